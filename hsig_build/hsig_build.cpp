@@ -1,0 +1,590 @@
+// Host-side HSIG builder: produces the serialised index that the search reads.
+//
+// Implements the construction of Section 4.1 of "UNIFY: Unified Index for Range
+// Filtered Approximate Nearest Neighbors Search":
+//   * equi-depth attribute segmentation (Section 3.1),
+//   * ANNSearch (Algorithm 1) restricted to one segment's sub-graph,
+//   * the Prune heuristic (Section 2.2),
+//   * BackboneConnectionsBuild (Algorithm 4),
+//   * HSIGInsert (Algorithm 6): per-segment descent and layer-wise insertion,
+//   * skip-list connections in attribute order (Section 4.1),
+//   * GlobalEdgeMasking (Algorithm 5).
+//
+// Readings taken where the paper is silent:
+//   * Segment bounds use all n attributes: b_j = sorted_attr[floor(j*n/S)] for
+//     j = 1..S-1, b_0 = -inf, b_S = +inf, segments half-open [b_j, b_{j+1}).
+//   * Node levels are floor(-ln(U) * mL) with mL = 1/ln(M), U in (0,1] drawn from
+//     a counter-based hash of (seed, id) (the printed formula is garbled).
+//   * Every chunk is kept sorted by (distance to its owner, id).
+//   * Empty segments are skipped; only a node's own segment can take it as entry.
+//   * Nodes are inserted in id order in batches: every node of a batch searches the
+//     graph as it stood at the start of the batch, then the batch's edges are
+//     applied in id order. The first 1024 nodes go one at a time. This makes the
+//     result independent of the thread count.
+//   * The skip list and the global-edge bitmaps are derived once all chunks are
+//     final: the skip-list level-l chain links the nodes of level >= l in
+//     attribute order (ties by id); Algorithm 5 runs per node in id order over the
+//     final chunks, so every stored bit position names the slot it was set for.
+//
+// Distances are float32 squared L2 with a fixed 8-way accumulation order
+// (compiled with -ffp-contract=off), so the graph is the same on every host.
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <queue>
+#include <string>
+#include <utility>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+using Key = std::pair<float, int32_t>;  // (distance, id), compared lexicographically
+
+inline float l2sq(const float* a, const float* b, int d) {
+  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int t = 0;
+  for (; t + 8 <= d; t += 8) {
+    for (int u = 0; u < 8; ++u) {
+      float df = a[t + u] - b[t + u];
+      acc[u] += df * df;
+    }
+  }
+  for (int u = 0; t < d; ++t, ++u) {
+    float df = a[t] - b[t];
+    acc[u] += df * df;
+  }
+  return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+}
+
+inline uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+struct Visited {
+  std::vector<uint32_t> stamp;
+  uint32_t cur = 0;
+  void reset(size_t n) {
+    if (stamp.size() != n) { stamp.assign(n, 0); cur = 0; }
+    if (++cur == 0) { std::fill(stamp.begin(), stamp.end(), 0); cur = 1; }
+  }
+  bool test_set(int32_t v) {
+    if (stamp[v] == cur) return true;
+    stamp[v] = cur;
+    return false;
+  }
+};
+
+struct Builder {
+  int64_t n = 0;
+  int d = 0, S = 0, M = 0, efc = 0;
+  uint64_t seed = 0;
+  const float* X = nullptr;
+  const int64_t* A = nullptr;
+
+  std::vector<int64_t> bounds;     // S+1
+  std::vector<int64_t> seg_count;  // S
+  std::vector<int32_t> seg;        // n
+  std::vector<int32_t> level;      // n
+  std::vector<int64_t> row0;       // n: first row (layer 0) of node v; rows of v are row0[v] + l
+  int64_t nrows = 0;
+  // Per row: S chunks of M slots (ids, distances to owner), counts per chunk.
+  std::vector<int32_t> adj;
+  std::vector<float> adjd;
+  std::vector<uint8_t> cnt;
+  std::vector<int32_t> entry_seg;  // S, -1 when the segment holds no node yet
+  std::vector<int32_t> top_seg;    // S, level of entry_seg
+  std::vector<int32_t> order;      // attribute order (ties by id)
+
+  const float* vec(int64_t v) const { return X + v * (int64_t)d; }
+  int64_t row(int32_t v, int l) const { return row0[v] + l; }
+  int32_t* chunk(int64_t r, int j) { return adj.data() + (r * S + j) * (int64_t)M; }
+  float* chunkd(int64_t r, int j) { return adjd.data() + (r * S + j) * (int64_t)M; }
+  uint8_t& chunkn(int64_t r, int j) { return cnt[r * S + j]; }
+
+  // ---- segmentation (Section 3.1) ----
+  void segment() {
+    order.resize(n);
+    for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return A[a] != A[b] ? A[a] < A[b] : a < b;
+    });
+    bounds.assign(S + 1, 0);
+    bounds[0] = std::numeric_limits<int64_t>::min();
+    bounds[S] = std::numeric_limits<int64_t>::max();
+    for (int j = 1; j < S; ++j) bounds[j] = A[order[(int64_t)j * n / S]];
+    seg.resize(n);
+    seg_count.assign(S, 0);
+    for (int64_t v = 0; v < n; ++v) {
+      // segment j with bounds[j] <= a < bounds[j+1]
+      int j = (int)(std::upper_bound(bounds.begin() + 1, bounds.begin() + S, A[v]) - (bounds.begin() + 1));
+      seg[v] = j;
+      seg_count[j]++;
+    }
+  }
+
+  // ---- levels (Algorithm 6, line 2) ----
+  void assign_levels() {
+    level.resize(n);
+    row0.resize(n);
+    double mL = 1.0 / std::log((double)M);
+    int64_t r = 0;
+    for (int64_t v = 0; v < n; ++v) {
+      uint64_t h = splitmix64(seed * 0x632BE59BD9B4E019ull + (uint64_t)v);
+      double u = ((double)(h >> 11) + 1.0) * (1.0 / 9007199254740992.0);  // (0, 1]
+      int lv = (int)std::floor(-std::log(u) * mL);
+      if (lv > 30) lv = 30;
+      level[v] = lv;
+      row0[v] = r;
+      r += lv + 1;
+    }
+    nrows = r;
+    adj.assign((size_t)nrows * S * M, -1);
+    adjd.assign((size_t)nrows * S * M, 0.f);
+    cnt.assign((size_t)nrows * S, 0);
+    entry_seg.assign(S, -1);
+    top_seg.assign(S, -1);
+  }
+
+  // ---- Algorithm 1 on the sub-graph of segment j at layer l ----
+  void ann_search(const float* q, int32_t ep, int l, int j, int ef, Visited& vis,
+                  std::vector<Key>& out) const {
+    std::priority_queue<Key, std::vector<Key>, std::greater<Key>> cand;
+    std::priority_queue<Key> ann;
+    Key e{l2sq(q, vec(ep), d), ep};
+    cand.push(e);
+    ann.push(e);
+    vis.test_set(ep);
+    while (!cand.empty()) {
+      Key o = cand.top();
+      cand.pop();
+      if (o > ann.top()) break;
+      int64_t r = row0[o.second] + l;
+      const int32_t* ch = adj.data() + (r * S + j) * (int64_t)M;
+      int c = cnt[r * S + j];
+      for (int s = 0; s < c; ++s) {
+        int32_t v = ch[s];
+        if (vis.test_set(v)) continue;
+        Key kv{l2sq(q, vec(v), d), v};
+        if ((int)ann.size() < ef || kv < ann.top()) {
+          cand.push(kv);
+          ann.push(kv);
+          if ((int)ann.size() > ef) ann.pop();
+        }
+      }
+    }
+    out.clear();
+    while (!ann.empty()) { out.push_back(ann.top()); ann.pop(); }
+    std::reverse(out.begin(), out.end());
+  }
+
+  // ---- Prune heuristic (Section 2.2) ----
+  // cands: (distance to owner, id); returns at most M survivors in ascending order.
+  void prune(std::vector<Key>& cands, int Mmax, std::vector<Key>& kept) const {
+    std::sort(cands.begin(), cands.end());
+    kept.clear();
+    for (const Key& r : cands) {
+      if ((int)kept.size() >= Mmax) break;
+      bool drop = false;
+      for (const Key& e : kept) {
+        if (r.first > l2sq(vec(e.second), vec(r.second), d)) { drop = true; break; }
+      }
+      if (!drop) kept.push_back(r);
+    }
+  }
+
+  struct Proposal {  // forward edges of one node: per layer, per segment
+    std::vector<std::vector<Key>> fwd;  // index l*S + j
+  };
+
+  // Searches of Algorithm 6 for node v against the current (read-only) graph.
+  void propose(int32_t v, Visited& vis, Proposal& P, std::vector<Key>& ann,
+               std::vector<Key>& tmp) const {
+    const float* q = vec(v);
+    int lv = level[v];
+    P.fwd.assign((size_t)(lv + 1) * S, {});
+    for (int j = 0; j < S; ++j) {
+      int32_t ep = entry_seg[j];
+      if (ep < 0) continue;  // empty segment
+      int L = top_seg[j];
+      for (int l = L; l > lv; --l) {
+        vis.reset(n);
+        ann_search(q, ep, l, j, 1, vis, ann);
+        ep = ann[0].second;
+      }
+      for (int l = std::min(lv, L); l >= 0; --l) {
+        vis.reset(n);
+        ann_search(q, ep, l, j, efc, vis, ann);
+        tmp = ann;
+        prune(tmp, M, P.fwd[(size_t)l * S + j]);
+        ep = ann[0].second;
+      }
+    }
+  }
+
+  void set_chunk(int64_t r, int j, const std::vector<Key>& ks) {
+    int32_t* ch = chunk(r, j);
+    float* cd = chunkd(r, j);
+    int c = (int)ks.size();
+    for (int s = 0; s < M; ++s) {
+      ch[s] = s < c ? ks[s].second : -1;
+      cd[s] = s < c ? ks[s].first : 0.f;
+    }
+    chunkn(r, j) = (uint8_t)c;
+  }
+
+  // Algorithm 4, lines 4-6: add (o -> v) to G[o][i], re-prune on overflow.
+  void add_reverse(int32_t o, int l, int i, Key kv, std::vector<Key>& cands, std::vector<Key>& kept) {
+    int64_t r = row(o, l);
+    int c = chunkn(r, i);
+    const int32_t* ch = chunk(r, i);
+    const float* cd = chunkd(r, i);
+    cands.clear();
+    for (int s = 0; s < c; ++s) {
+      if (ch[s] == kv.second) return;  // already present
+      cands.push_back({cd[s], ch[s]});
+    }
+    cands.push_back(kv);
+    if ((int)cands.size() <= M) {
+      std::sort(cands.begin(), cands.end());
+      set_chunk(r, i, cands);
+    } else {
+      prune(cands, M, kept);
+      set_chunk(r, i, kept);
+    }
+  }
+
+  void build(int threads) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+    int nth = omp_get_max_threads();
+#else
+    (void)threads;
+    int nth = 1;
+#endif
+    segment();
+    assign_levels();
+    std::vector<Visited> vis(nth);
+    std::vector<std::vector<Key>> ann(nth), tmp(nth), kept(nth);
+    std::vector<Proposal> props;
+    struct Rev { int32_t o; int32_t l; int32_t i; int32_t v; float dist; };
+    std::vector<Rev> revs;
+    int64_t done = 0;
+    while (done < n) {
+      int64_t bs = done < 1024 ? 1 : std::min<int64_t>(4096, done / 64);
+      int64_t end = std::min<int64_t>(n, done + bs);
+      int64_t cntb = end - done;
+      props.assign(cntb, {});
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+      for (int64_t t = 0; t < cntb; ++t) {
+#ifdef _OPENMP
+        int th = omp_get_thread_num();
+#else
+        int th = 0;
+#endif
+        propose((int32_t)(done + t), vis[th], props[t], ann[th], tmp[th]);
+      }
+      // forward edges (batch nodes' own rows) and the reverse-edge list, in id order
+      revs.clear();
+      for (int64_t t = 0; t < cntb; ++t) {
+        int32_t v = (int32_t)(done + t);
+        int i = seg[v];
+        const Proposal& P = props[t];
+        for (int l = 0; l <= level[v]; ++l)
+          for (int j = 0; j < S; ++j) {
+            const std::vector<Key>& f = P.fwd[(size_t)l * S + j];
+            if (f.empty()) continue;
+            set_chunk(row(v, l), j, f);
+            for (const Key& o : f) revs.push_back({o.second, l, i, v, o.first});
+          }
+      }
+      // reverse edges grouped by target chunk, applied in source-id order
+      std::stable_sort(revs.begin(), revs.end(), [](const Rev& a, const Rev& b) {
+        if (a.o != b.o) return a.o < b.o;
+        if (a.l != b.l) return a.l < b.l;
+        return a.i < b.i;
+      });
+      std::vector<size_t> starts;
+      for (size_t e = 0; e < revs.size(); ++e)
+        if (e == 0 || revs[e].o != revs[e - 1].o || revs[e].l != revs[e - 1].l || revs[e].i != revs[e - 1].i)
+          starts.push_back(e);
+      starts.push_back(revs.size());
+      const int64_t ngroups = (int64_t)starts.size() - 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+      for (int64_t g = 0; g < ngroups; ++g) {
+#ifdef _OPENMP
+        int th = omp_get_thread_num();
+#else
+        int th = 0;
+#endif
+        for (size_t e = starts[g]; e < starts[g + 1]; ++e)
+          add_reverse(revs[e].o, revs[e].l, revs[e].i, {revs[e].dist, revs[e].v}, tmp[th], kept[th]);
+      }
+      // entry points (Algorithm 6, line 11): only the node's own segment
+      for (int64_t t = 0; t < cntb; ++t) {
+        int32_t v = (int32_t)(done + t);
+        int i = seg[v];
+        if (entry_seg[i] < 0 || level[v] > top_seg[i]) {
+          entry_seg[i] = v;
+          top_seg[i] = level[v];
+        }
+      }
+      done = end;
+    }
+  }
+
+  // ---- skip list (Section 4.1) and global edge masking (Algorithm 5) ----
+  int max_level = 0;
+  int32_t entry_global = -1;
+  std::vector<int32_t> skip_next;  // per row
+  std::vector<int32_t> skip_head;  // per layer
+  std::vector<uint32_t> gmask;     // per row, W words
+  int W = 0;
+
+  void finalize(int threads) {
+    (void)threads;
+    max_level = 0;
+    for (int64_t v = 0; v < n; ++v) max_level = std::max(max_level, level[v]);
+    entry_global = -1;
+    for (int64_t v = 0; v < n; ++v)
+      if (level[v] == max_level) { entry_global = (int32_t)v; break; }
+    // skip list: level-l chain over nodes of level >= l in attribute order
+    skip_next.assign(nrows, -1);
+    skip_head.assign(max_level + 1, -1);
+    std::vector<int32_t> last(max_level + 1, -1);
+    for (int64_t p = 0; p < n; ++p) {
+      int32_t v = order[p];
+      for (int l = 0; l <= level[v]; ++l) {
+        if (last[l] < 0) skip_head[l] = v;
+        else skip_next[row(last[l], l)] = v;
+        last[l] = v;
+      }
+    }
+    // Algorithm 5 over the final chunks.
+    W = (S * M + 31) / 32;
+    gmask.assign((size_t)nrows * W, 0u);
+    // Prune(x, G[x], M) depends only on the final chunks: compute it for every row.
+    std::vector<std::vector<int32_t>> keep_pos(nrows);
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+      std::vector<Key> cands, kept;
+      std::vector<int32_t> posv;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+      for (int64_t v = 0; v < n; ++v) {
+        for (int l = 0; l <= level[v]; ++l) {
+          int64_t r = row0[v] + l;
+          cands.clear();
+          for (int j = 0; j < S; ++j) {
+            int c = cnt[r * S + j];
+            for (int s = 0; s < c; ++s)
+              cands.push_back({adjd[(r * S + j) * M + s], adj[(r * S + j) * M + s]});
+          }
+          prune(cands, M, kept);
+          posv.clear();
+          for (const Key& k : kept) {
+            int32_t id = k.second;
+            int j = seg[id];
+            int c = cnt[r * S + j];
+            for (int s = 0; s < c; ++s)
+              if (adj[(r * S + j) * M + s] == id) { posv.push_back(j * M + s); break; }
+          }
+          keep_pos[r] = posv;
+        }
+      }
+    }
+    auto popc = [&](int64_t r) {
+      int c = 0;
+      for (int w = 0; w < W; ++w) c += __builtin_popcount(gmask[r * W + w]);
+      return c;
+    };
+    auto set_from = [&](int64_t r) {
+      for (int w = 0; w < W; ++w) gmask[r * W + w] = 0;
+      for (int32_t p : keep_pos[r]) gmask[r * W + (p >> 5)] |= 1u << (p & 31);
+    };
+    for (int64_t v = 0; v < n; ++v) {
+      for (int l = 0; l <= level[v]; ++l) {
+        int64_t r = row0[v] + l;
+        set_from(r);
+        for (int32_t p : keep_pos[r]) {
+          int32_t o = adj[r * S * (int64_t)M + p];
+          int64_t ro = row0[o] + l;
+          int i = seg[v];
+          int c = cnt[ro * S + i];
+          int pos = -1;
+          for (int s = 0; s < c; ++s)
+            if (adj[(ro * S + i) * M + s] == (int32_t)v) { pos = i * M + s; break; }
+          if (pos < 0) continue;
+          gmask[ro * W + (pos >> 5)] |= 1u << (pos & 31);
+          if (popc(ro) > M) set_from(ro);
+        }
+      }
+    }
+  }
+};
+
+// ---- index file writer ----
+// Layout: "UNIFYHSG", u32 version, u32 nsec, then nsec 96-byte entries
+// {char name[24]; u32 dtype; u32 ndim; u64 shape[4]; u64 offset; u64 nbytes;
+//  u64 checksum; u64 reserved}, then the section payloads at 64-byte aligned
+// offsets. dtype: 1 i8, 2 u8, 3 i32, 4 u32, 5 i64, 6 f32. checksum: FNV-1a 64
+// over little-endian 8-byte words (the last word zero-padded).
+struct Section {
+  std::string name;
+  uint32_t dtype;
+  std::vector<uint64_t> shape;
+  const void* data;
+  uint64_t nbytes;
+};
+
+uint64_t fnv1a_words(const void* p, uint64_t nbytes) {
+  const unsigned char* b = (const unsigned char*)p;
+  uint64_t h = 0xcbf29ce484222325ull;
+  uint64_t i = 0;
+  for (; i + 8 <= nbytes; i += 8) {
+    uint64_t w;
+    std::memcpy(&w, b + i, 8);
+    h = (h ^ w) * 0x100000001b3ull;
+  }
+  if (i < nbytes) {
+    uint64_t w = 0;
+    std::memcpy(&w, b + i, nbytes - i);
+    h = (h ^ w) * 0x100000001b3ull;
+  }
+  return h;
+}
+
+bool write_index(const char* path, const std::vector<Section>& secs, std::string& err) {
+  FILE* f = std::fopen(path, "wb");
+  if (!f) { err = std::string("cannot open ") + path; return false; }
+  const uint32_t version = 1, nsec = (uint32_t)secs.size();
+  uint64_t off = 16 + 96ull * nsec;
+  off = (off + 63) & ~63ull;
+  std::vector<unsigned char> table(96ull * nsec, 0);
+  std::vector<uint64_t> offs;
+  for (size_t s = 0; s < secs.size(); ++s) {
+    unsigned char* e = table.data() + 96 * s;
+    std::strncpy((char*)e, secs[s].name.c_str(), 23);
+    std::memcpy(e + 24, &secs[s].dtype, 4);
+    uint32_t nd = (uint32_t)secs[s].shape.size();
+    std::memcpy(e + 28, &nd, 4);
+    for (uint32_t k = 0; k < 4; ++k) {
+      uint64_t v = k < nd ? secs[s].shape[k] : 0;
+      std::memcpy(e + 32 + 8 * k, &v, 8);
+    }
+    std::memcpy(e + 64, &off, 8);
+    std::memcpy(e + 72, &secs[s].nbytes, 8);
+    uint64_t ck = fnv1a_words(secs[s].data, secs[s].nbytes);
+    std::memcpy(e + 80, &ck, 8);
+    offs.push_back(off);
+    off += secs[s].nbytes;
+    off = (off + 63) & ~63ull;
+  }
+  bool ok = std::fwrite("UNIFYHSG", 1, 8, f) == 8 && std::fwrite(&version, 4, 1, f) == 1 &&
+            std::fwrite(&nsec, 4, 1, f) == 1 && std::fwrite(table.data(), 1, table.size(), f) == table.size();
+  uint64_t pos = 16 + table.size();
+  static const unsigned char zeros[64] = {0};
+  for (size_t s = 0; ok && s < secs.size(); ++s) {
+    while (ok && pos < offs[s]) {
+      size_t z = (size_t)std::min<uint64_t>(64, offs[s] - pos);
+      ok = std::fwrite(zeros, 1, z, f) == z;
+      pos += z;
+    }
+    ok = ok && std::fwrite(secs[s].data, 1, secs[s].nbytes, f) == secs[s].nbytes;
+    pos += secs[s].nbytes;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) err = std::string("write failed: ") + path;
+  return ok;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Builds the HSIG over X (n x d float32, row-major) with integer attributes A and
+// writes it to out_path. Returns 0 on success, a negative code otherwise (message
+// in errbuf). threads <= 0 uses every available core.
+int hsig_build_index(const float* X, const int64_t* A, int64_t n, int d, int S, int M, int efc,
+                     uint64_t seed, int threads, const char* out_path, char* errbuf, int errlen) {
+  auto fail = [&](int code, const std::string& msg) {
+    if (errbuf && errlen > 0) {
+      std::strncpy(errbuf, msg.c_str(), errlen - 1);
+      errbuf[errlen - 1] = 0;
+    }
+    return code;
+  };
+  if (!X || !A || !out_path) return fail(-1, "null argument");
+  if (n < 1 || n >= (1ll << 30)) return fail(-1, "n must be in [1, 2^30)");
+  if (d < 1 || S < 1 || S > 32 || M < 1 || M > 255 || efc < 1) return fail(-1, "bad d/S/M/efc (S <= 32, M <= 255)");
+  Builder b;
+  b.n = n; b.d = d; b.S = S; b.M = M; b.efc = efc; b.seed = seed; b.X = X; b.A = A;
+  b.build(threads);
+  b.finalize(threads);
+
+  std::vector<int32_t> upper_base(n, -1);
+  int64_t n_upper = 0;
+  for (int64_t v = 0; v < n; ++v)
+    if (b.level[v] > 0) { upper_base[v] = (int32_t)n_upper; n_upper += b.level[v]; }
+  const int64_t SM = (int64_t)S * M;
+  const int W = b.W;
+  std::vector<int32_t> adj0((size_t)n * SM), adjU((size_t)std::max<int64_t>(1, n_upper) * SM, -1);
+  std::vector<uint32_t> gm0((size_t)n * W), gmU((size_t)std::max<int64_t>(1, n_upper) * W, 0);
+  std::vector<int32_t> next0(n), nextU((size_t)std::max<int64_t>(1, n_upper), -1);
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t r = b.row0[v];
+    std::memcpy(&adj0[(size_t)v * SM], &b.adj[(size_t)r * SM], SM * 4);
+    std::memcpy(&gm0[(size_t)v * W], &b.gmask[(size_t)r * W], W * 4);
+    next0[v] = b.skip_next[r];
+    for (int l = 1; l <= b.level[v]; ++l) {
+      int64_t u = upper_base[v] + l - 1;
+      std::memcpy(&adjU[(size_t)u * SM], &b.adj[(size_t)(r + l) * SM], SM * 4);
+      std::memcpy(&gmU[(size_t)u * W], &b.gmask[(size_t)(r + l) * W], W * 4);
+      nextU[u] = b.skip_next[r + l];
+    }
+  }
+  std::vector<int64_t> meta(16, 0);
+  meta[0] = n; meta[1] = d; meta[2] = S; meta[3] = M; meta[4] = b.max_level;
+  meta[5] = b.entry_global; meta[6] = n_upper; meta[7] = efc; meta[8] = (int64_t)seed; meta[9] = W;
+  uint64_t nu = (uint64_t)std::max<int64_t>(1, n_upper);
+  std::vector<Section> secs = {
+      {"meta", 5, {16}, meta.data(), 16 * 8},
+      {"vectors", 6, {(uint64_t)n, (uint64_t)d}, X, (uint64_t)n * d * 4},
+      {"attr", 5, {(uint64_t)n}, A, (uint64_t)n * 8},
+      {"level", 3, {(uint64_t)n}, b.level.data(), (uint64_t)n * 4},
+      {"upper_base", 3, {(uint64_t)n}, upper_base.data(), (uint64_t)n * 4},
+      {"seg_bounds", 5, {(uint64_t)S + 1}, b.bounds.data(), (uint64_t)(S + 1) * 8},
+      {"seg_count", 5, {(uint64_t)S}, b.seg_count.data(), (uint64_t)S * 8},
+      {"entry_seg", 3, {(uint64_t)S}, b.entry_seg.data(), (uint64_t)S * 4},
+      {"sorted_ids", 3, {(uint64_t)n}, b.order.data(), (uint64_t)n * 4},
+      {"skip_next0", 3, {(uint64_t)n}, next0.data(), (uint64_t)n * 4},
+      {"skip_head", 3, {(uint64_t)b.max_level + 1}, b.skip_head.data(), (uint64_t)(b.max_level + 1) * 4},
+      {"skip_nextU", 3, {nu}, nextU.data(), nu * 4},
+      {"adj0", 3, {(uint64_t)n, (uint64_t)S, (uint64_t)M}, adj0.data(), (uint64_t)n * SM * 4},
+      {"gmask0", 4, {(uint64_t)n, (uint64_t)W}, gm0.data(), (uint64_t)n * W * 4},
+      {"adjU", 3, {nu, (uint64_t)S, (uint64_t)M}, adjU.data(), nu * SM * 4},
+      {"gmaskU", 4, {nu, (uint64_t)W}, gmU.data(), nu * W * 4},
+  };
+  std::string err;
+  if (!write_index(out_path, secs, err)) return fail(-2, err);
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,341 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage it checks. None of them re-types the oracle's own
+formulas: they use brute force in plain Python, library routines (numpy sort and
+searchsorted, scipy graph components), hand-traced examples and properties
+(Lemma 1 / Theorem 1) that a wrong oracle would violate.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from index_writer import tiny_index_sections, write_index
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- O1 (Definition 1)
+
+def _py_bruteforce(X, A, q, lo, hi, k):
+    """Definition 1 by hand: integer data, exact Python integers."""
+    R = [i for i in range(len(A)) if lo <= A[i] <= hi]
+    d = [(sum((int(q[t]) - int(X[i][t])) ** 2 for t in range(len(q))), i) for i in R]
+    d.sort()
+    return d[:k]
+
+
+def test_exact_knn_equals_python_bruteforce():
+    rng = np.random.default_rng(5)
+    n, d = 60, 3
+    X = rng.integers(0, 6, size=(n, d)).astype(np.float32)  # many distance ties
+    A = rng.integers(0, 20, size=n).astype(np.int64)
+    Q = rng.integers(0, 6, size=(25, d)).astype(np.float32)
+    lo = rng.integers(-2, 15, size=25)
+    hi = lo + rng.integers(0, 10, size=25)
+    for k in (1, 4, 9):
+        ids, dist, cnt = oracle.exact_knn(X, A, Q, lo, hi, k)
+        for i in range(25):
+            ref = _py_bruteforce(X, A, Q[i], lo[i], hi[i], k)
+            assert cnt[i] == len(ref)
+            assert list(ids[i, :cnt[i]]) == [r[1] for r in ref]
+            assert list(dist[i, :cnt[i]]) == [float(r[0]) for r in ref]
+            assert np.all(ids[i, cnt[i]:] == -1) and np.all(np.isinf(dist[i, cnt[i]:]))
+
+
+def test_exact_knn_short_and_empty_ranges():
+    """|R| < k returns all of R (Definition 1); an empty range returns nothing."""
+    X = np.arange(10, dtype=np.float32).reshape(10, 1)
+    A = np.arange(10, dtype=np.int64) * 10
+    Q = np.array([[4.2], [4.2], [4.2], [0.0]], np.float32)
+    lo = np.array([30, 95, 50, 0])
+    hi = np.array([50, 99, 40, 1000])
+    ids, dist, cnt = oracle.exact_knn(X, A, Q, lo, hi, 5)
+    assert list(cnt) == [3, 0, 0, 5]
+    assert list(ids[0, :3]) == [4, 5, 3]
+    assert list(ids[3]) == [0, 1, 2, 3, 4]
+    assert np.all(ids[1] == -1) and np.all(ids[2] == -1)
+
+
+def test_exact_knn_self_query_is_first():
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((300, 8)).astype(np.float32)
+    A = rng.permutation(300).astype(np.int64)
+    v = np.arange(0, 300, 17)
+    ids, dist, cnt = oracle.exact_knn(X, A, X[v], A[v] - 5, A[v] + 5, 3)
+    assert np.all(ids[:, 0] == v) and np.all(dist[:, 0] == 0.0)
+    assert np.all(dist[:, 1] > 0.0)
+
+
+def test_theorem1_sig_knng_inclusive():
+    """Lemma 1 / Theorem 1 (Section 3.2): with per-segment kNN chunks (SIG-kNNG),
+    the kNN graph of every union of segments is a sub-graph. Built by brute force
+    with O1 on a small input; a wrong range filter or ranking breaks it."""
+    rng = np.random.default_rng(11)
+    n, d, S, k = 64, 4, 4, 3
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    A = rng.permutation(n).astype(np.int64)
+    seg_lo = [j * n // S for j in range(S)]
+    seg_hi = [(j + 1) * n // S - 1 for j in range(S)]
+    # chunk j of v = kNN(v, D_j \ {v}); ask k+1 and drop v itself (distance 0, unique)
+    chunks = {}
+    for j in range(S):
+        ids, _, cnt = oracle.exact_knn(X, A, X, np.full(n, seg_lo[j]), np.full(n, seg_hi[j]), k + 1)
+        for v in range(n):
+            chunks[(v, j)] = [int(o) for o in ids[v, :cnt[v]] if o != v][:k]
+    sig = {v: set(itertools.chain.from_iterable(chunks[(v, j)] for j in range(S))) for v in range(n)}
+    for a in range(S):
+        for b in range(a, S):
+            lo, hi = seg_lo[a], seg_hi[b]
+            members = [v for v in range(n) if lo <= A[v] <= hi]
+            ids, _, cnt = oracle.exact_knn(X, A, X[members], np.full(len(members), lo),
+                                           np.full(len(members), hi), k + 1)
+            for r, v in enumerate(members):
+                knn = [int(o) for o in ids[r, :cnt[r]] if o != v][:k]
+                assert all(lo <= A[o] <= hi for o in knn)
+                assert set(knn) <= sig[v], (v, a, b)
+
+
+# ---------------------------------------------------------------- Eq. 1
+
+def test_recall_formula():
+    ex = np.array([[1, 2, 3], [7, -1, -1], [-1, -1, -1]])
+    cnt = np.array([3, 1, 0])
+    fo = np.array([[3, 9, 1], [8, 7, -1], [-1, -1, -1]])
+    r = oracle.recall(fo, ex, cnt, 3)
+    assert r[0] == pytest.approx(2 / 3) and r[1] == 1.0 and r[2] == 1.0
+
+
+# ---------------------------------------------------------------- hand-traced (Alg. 1, 7)
+
+@pytest.fixture(scope="module")
+def tiny(tmp_path_factory):
+    with open(os.path.join(GOLDEN, "tiny_line_graph.json")) as f:
+        g = json.load(f)
+    path = str(tmp_path_factory.mktemp("tiny") / "tiny.idx")
+    write_index(path, tiny_index_sections(g))
+    return g, path
+
+
+def test_golden_tiny_line_graph(tiny):
+    g, path = tiny
+    oi = oracle.OracleIndex(path)
+    for case in g["cases"]:
+        r = oi.search(np.array([case["q"]], np.float32), [case["lo"]], [case["hi"]], case["k"],
+                      ef=case["ef"], m=case["m"], ef_post=case["ef"], strategy=case["strategy"])
+        want = case["expect_ids"]
+        assert list(r["ids"][0]) == want, case["name"]
+        for got, exp in zip(r["dist"][0], case["expect_dist"]):
+            if exp is None:
+                assert np.isinf(got)
+            else:
+                assert got == pytest.approx(exp, rel=1e-6, abs=1e-6), case["name"]
+        assert r["n_exp"][0] == case["expect_n_exp"], case["name"]
+        assert r["n_dist"][0] == case["expect_n_dist"], case["name"]
+
+
+def test_corrupt_index_is_rejected(tiny, tmp_path):
+    g, _ = tiny
+    path = str(tmp_path / "bad.idx")
+    write_index(path, tiny_index_sections(g), corrupt_section="adj0")
+    with pytest.raises(RuntimeError):
+        oracle.OracleIndex(path)
+
+
+# ---------------------------------------------------------------- routing (Section 4.2)
+
+def test_paper_segmentation_example(tmp_path):
+    """Section 3.2 example: attributes 1..8 in two segments [1,5) and [5,8]."""
+    with open(os.path.join(GOLDEN, "segmentation_example.json")) as f:
+        g = json.load(f)
+    import hsig_build
+    X = np.arange(8, dtype=np.float32).reshape(8, 1)
+    A = np.array(g["attributes"], np.int64)
+    path = str(tmp_path / "seg.idx")
+    hsig_build.build_index(X, A, path, S=g["S"], M=2, efc=4, seed=1)
+    ix = hsig_build.read_index(path)
+    assert list(ix["seg_bounds"][1:-1]) == g["expect_inner_bounds"]
+    oi = oracle.OracleIndex(path)
+    lo = np.array([c[0] for c in g["mask_cases"]])
+    hi = np.array([c[1] for c in g["mask_cases"]])
+    r = oi.route(lo, hi)
+    assert list(r["mask"]) == [c[2] for c in g["mask_cases"]]
+
+
+def test_route_bounds_masks_strategies(c1_index):
+    w, path = c1_index
+    import hsig_build
+    ix = hsig_build.read_index(path)
+    oi = oracle.OracleIndex(path)
+    rng = np.random.default_rng(3)
+    sa = np.sort(w.attrs)
+    lo = np.concatenate([rng.integers(-50, w.n + 50, 400), [0, 0, 5, -10, w.n - 1, 100]])
+    hi = np.concatenate([lo[:400] + rng.integers(-3, w.n // 2, 400), [w.n - 1, 99, 4, -1, w.n + 5, 199]])
+    tau_a, tau_b = 100, 5000
+    r = oi.route(lo, hi, tau_a, tau_b)
+    pa = np.searchsorted(sa, lo, side="left")
+    pb = np.maximum(np.searchsorted(sa, hi, side="right"), pa)
+    assert np.array_equal(r["pa"], pa) and np.array_equal(r["pb"], pb)
+    Y = pb - pa
+    want = np.where(Y <= tau_a, 0, np.where(Y >= tau_b, 2, 1))
+    assert np.array_equal(r["strategy"], want)
+    b = ix["seg_bounds"]
+    S = ix["S"]
+    seg_of = np.searchsorted(b[1:S], w.attrs, side="right")
+    for i in range(len(lo)):
+        m = int(r["mask"][i])
+        inr = (w.attrs >= lo[i]) & (w.attrs <= hi[i])
+        # every in-range object's segment is marked
+        for j in np.unique(seg_of[inr]):
+            assert (m >> int(j)) & 1
+        # every marked segment's interval overlaps [lo, hi] and holds objects
+        for j in range(S):
+            if (m >> j) & 1:
+                lo_j = -np.inf if j == 0 else b[j]
+                hi_j = np.inf if j == S - 1 else b[j + 1] - 1
+                assert max(lo_j, lo[i]) <= min(hi_j, hi[i])
+                assert (seg_of == j).any()
+        # skip-list descent lands on the first object with attribute >= lo
+        first = int(r["first"][i])
+        n_below = int(np.searchsorted(sa, lo[i], side="left"))
+        assert first == (int(ix["sorted_ids"][n_below]) if n_below < w.n else -1)
+
+
+def test_router_thresholds_at_exact_counts(c1_index):
+    """Y <= tau_A -> A, Y >= tau_B -> B, otherwise C, at the boundary counts (c1's
+    attribute is a permutation, so a width-w range holds exactly w objects)."""
+    w, path = c1_index
+    oi = oracle.OracleIndex(path)
+    tau_a, tau_b = 100, 5000
+    widths = np.array([0, 1, 99, 100, 101, 4999, 5000, 5001, w.n])
+    lo = np.full(len(widths), 0)
+    hi = widths - 1
+    r = oi.route(lo, hi, tau_a, tau_b)
+    assert list(r["pb"] - r["pa"]) == list(widths)
+    assert list(r["strategy"]) == [0, 0, 0, 0, 1, 1, 2, 2, 2]
+
+
+# ---------------------------------------------------------------- strategies vs O1
+
+def test_prefilter_equals_exact(c1_index):
+    """Strategy A is exact (Section 4.2): equal to Definition 1 id for id."""
+    w, path = c1_index
+    oi = oracle.OracleIndex(path)
+    ex = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, w.k)
+    r = oi.search(w.queries, w.lo, w.hi, w.k, strategy="pre")
+    assert np.array_equal(r["ids"], ex[0]) and np.array_equal(r["count"], ex[2])
+    assert np.array_equal(r["dist"], ex[1])
+
+
+def _flat_copy(path, out_path):
+    """The same layer-0 graph with the upper layers dropped, so that the search
+    starts at the stored entry point on layer 0."""
+    import hsig_build
+    ix = hsig_build.read_index(path)
+    n, S, M, W = ix["n"], ix["S"], ix["M"], ix["W"]
+    meta = np.array(ix["meta"], np.int64)
+    meta[4] = 0
+    meta[6] = 0
+    sec = {k: np.array(ix[k]) for k in ("vectors", "attr", "seg_bounds", "seg_count", "entry_seg",
+                                         "sorted_ids", "skip_next0", "adj0", "gmask0")}
+    sec.update(meta=meta, level=np.zeros(n, np.int32), upper_base=np.full(n, -1, np.int32),
+               skip_head=np.array([ix["sorted_ids"][0]], np.int32), skip_nextU=np.full(1, -1, np.int32),
+               adjU=np.full((1, S, M), -1, np.int32), gmaskU=np.zeros((1, W), np.uint32))
+    write_index(out_path, sec)
+    return ix
+
+
+def _closure(n, src, dst, start):
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import breadth_first_order
+    g = coo_matrix((np.ones(len(src)), (src, dst)), shape=(n, n)).tocsr()
+    return breadth_first_order(g, start, directed=True, return_predecessors=False)
+
+
+def _topk_fp64(X, q, ids, k):
+    d = ((X[ids].astype(np.float64) - q.astype(np.float64)) ** 2).sum(1)
+    o = np.lexsort((ids, d))[:k]
+    return ids[o]
+
+
+def test_hybrid_unbounded_beam_is_exact(c1_index, tmp_path):
+    """With ef above |R| the ann never fills, Algorithm 7 never breaks and expands
+    every node reachable from the entry point over the selected chunk slots (S2).
+    The result must then be the exact top-k of the in-range part of that closure
+    (scipy BFS + numpy sort)."""
+    w, path = c1_index
+    flat = str(tmp_path / "flat.idx")
+    ix = _flat_copy(path, flat)
+    n, S, M = ix["n"], ix["S"], ix["M"]
+    oi = oracle.OracleIndex(flat)
+    sel = np.flatnonzero(w.fractions <= 0.10)[:40]
+    Q, lo, hi = w.queries[sel], w.lo[sel], w.hi[sel]
+    m = 16
+    r = oi.search(Q, lo, hi, w.k, ef=n, m=m, strategy="hybrid")
+    rt = oi.route(lo, hi)
+    ep = ix["entry_global"]
+    nonempty = 0
+    for i in range(len(sel)):
+        mask = int(rt["mask"][i])
+        segs = [j for j in range(S) if (mask >> j) & 1]
+        per = min(M, -(-m // len(segs)))
+        src, dst = [], []
+        for j in segs:
+            ch = ix["adj0"][:, j, :per]
+            vv, ss = np.nonzero(ch >= 0)
+            src.append(vv)
+            dst.append(ch[vv, ss])
+        reach = _closure(n, np.concatenate(src), np.concatenate(dst), ep)
+        inr = reach[(w.attrs[reach] >= lo[i]) & (w.attrs[reach] <= hi[i])]
+        want = _topk_fp64(w.vectors, Q[i], inr, w.k)
+        nonempty += len(want) > 0
+        assert int(r["count"][i]) == len(want)
+        assert np.array_equal(r["ids"][i, :len(want)], want), i
+    assert nonempty >= 30
+
+
+def test_post_unbounded_beam_is_exact(c1_index, tmp_path):
+    """Strategy B with ef_post >= n keeps every node reachable from the entry point
+    over the bitmap-marked slots; after the range filter the result must be the
+    exact top-k of the in-range part of that closure."""
+    w, path = c1_index
+    flat = str(tmp_path / "flat.idx")
+    ix = _flat_copy(path, flat)
+    n, S, M = ix["n"], ix["S"], ix["M"]
+    bits = np.unpackbits(ix["gmask0"].view(np.uint8), axis=1, bitorder="little")[:, :S * M].astype(bool)
+    adj = ix["adj0"].reshape(n, S * M)
+    vv, pp = np.nonzero(bits & (adj >= 0))
+    reach = _closure(n, vv, adj[vv, pp], ix["entry_global"])
+    assert len(reach) > 0.9 * n
+    oi = oracle.OracleIndex(flat)
+    sel = np.arange(0, len(w.lo), 5)
+    Q, lo, hi = w.queries[sel], w.lo[sel], w.hi[sel]
+    r = oi.search(Q, lo, hi, w.k, ef=100, ef_post=n, strategy="post")
+    for i in range(len(sel)):
+        inr = reach[(w.attrs[reach] >= lo[i]) & (w.attrs[reach] <= hi[i])]
+        want = _topk_fp64(w.vectors, Q[i], inr, w.k)
+        assert np.array_equal(r["ids"][i, :len(want)], want) and int(r["count"][i]) == len(want)
+
+
+def test_results_are_valid(c1_index):
+    """Invariants of every strategy: ids in [lo, hi], sorted by (distance, id), no
+    duplicates, padding after count (Definition 1)."""
+    w, path = c1_index
+    oi = oracle.OracleIndex(path)
+    for st in ("pre", "hybrid", "post", "auto"):
+        r = oi.search(w.queries, w.lo, w.hi, w.k, ef=40, strategy=st, tau_a=100, tau_b=5000)
+        for i in range(len(w.lo)):
+            c = int(r["count"][i])
+            ids, dist = r["ids"][i, :c], r["dist"][i, :c]
+            assert np.all((w.attrs[ids] >= w.lo[i]) & (w.attrs[ids] <= w.hi[i]))
+            assert len(set(ids.tolist())) == c
+            keys = list(zip(dist.tolist(), ids.tolist()))
+            assert keys == sorted(keys)
+            assert np.all(r["ids"][i, c:] == -1)
+        if st in ("pre", "hybrid"):
+            ex_cnt = np.minimum(w.k, np.array([((w.attrs >= a) & (w.attrs <= b)).sum() for a, b in zip(w.lo, w.hi)]))
+            if st == "pre":
+                assert np.array_equal(r["count"], ex_cnt)
