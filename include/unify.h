@@ -1,0 +1,163 @@
+/*
+ * unify.h - C ABI of the GB300 range-filtered k-NN search over an HSIG.
+ *
+ * The operation (Definition 1, Section 2.1 of "UNIFY: Unified Index for Range
+ * Filtered Approximate Nearest Neighbors Search"): for each query (q, [lo, hi], k)
+ * return the k objects v with lo <= v[A] <= hi nearest to q, or all of them when
+ * fewer than k exist. Distances are squared L2 (the paper's Euclidean distance,
+ * Section 5.1, ranks identically). Ties in distance are broken by id.
+ *
+ * Search strategies (Section 4.2):
+ *   UNIFY_PRE     Strategy A, pre-filtering: exhaustive scan of the in-range
+ *                 objects, located through the attribute order. Exact.
+ *   UNIFY_HYBRID  Strategy C, hybrid filtering: Algorithm 2's layer scheme with
+ *                 Algorithm 7 per layer; only chunks of intersected segments are
+ *                 followed, the first ceil(m / S') slots of each (selection S2).
+ *   UNIFY_POST    Strategy B, post-filtering: Algorithm 2 with Algorithm 1 over
+ *                 the bitmap-marked (global) edges, beam ef_post, then the range
+ *                 filter and the first k.
+ *   UNIFY_AUTO    Range-aware selection: Y = |{v : lo <= v[A] <= hi}|;
+ *                 A if Y <= tau_A, B if Y >= tau_B, otherwise C.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: UNIFY_OK (0) or a negative UNIFY_E_* code; the message of the
+ *     last failure on the calling thread is returned by unify_last_error().
+ *   - Device pointers are CUDA device (or managed) memory on the index's device
+ *     and stay owned by the caller. Work is enqueued on `stream` (a cudaStream_t,
+ *     NULL = the legacy default stream) and is asynchronous unless stated.
+ *   - Output rows hold min(k, found) results sorted by (distance, id); the rest of
+ *     the row is padded with id -1 and distance +inf. lo > hi is an empty range
+ *     (count 0), not an error.
+ *   - Attributes are int64; lo and hi are inclusive.
+ *   - One index may serve one search at a time: concurrent searches on the same
+ *     index from different streams race on its scratch buffers.
+ */
+#ifndef UNIFY_H
+#define UNIFY_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define UNIFY_API __attribute__((visibility("default")))
+#else
+#define UNIFY_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct unify_index unify_index_t; /* opaque, library-owned */
+
+typedef enum {
+  UNIFY_AUTO = -1,
+  UNIFY_PRE = 0,
+  UNIFY_HYBRID = 1,
+  UNIFY_POST = 2
+} unify_strategy_t;
+
+typedef enum {
+  UNIFY_FP32 = 0,    /* traversal and scan read the float32 vectors */
+  UNIFY_BF16 = 1,    /* read a bfloat16 copy (RNE), FP32 accumulate, FP32 re-rank */
+  UNIFY_FP8E4M3 = 2  /* read an FP8 E4M3 copy with a per-vector float32 scale
+                        s = max|x| / 448, FP32 accumulate, FP32 re-rank */
+} unify_dtype_t;
+
+/* Return codes. */
+#define UNIFY_OK 0
+#define UNIFY_E_ARG (-1)     /* invalid argument (null pointer, bad size, k < 1, ...) */
+#define UNIFY_E_IO (-2)      /* index file missing or unreadable */
+#define UNIFY_E_FORMAT (-3)  /* index file malformed or checksum mismatch */
+#define UNIFY_E_NOMEM (-4)   /* host or device allocation failed */
+#define UNIFY_E_CUDA (-5)    /* a CUDA call failed (message has the CUDA error) */
+#define UNIFY_E_LIMIT (-6)   /* a size exceeds a compiled limit (message says which) */
+
+/* Per-query status bits written to out_status. */
+#define UNIFY_Q_LIMIT 1u      /* the expansion bound (max_expansions) stopped a layer */
+#define UNIFY_Q_TRUNCATED 2u  /* the candidate buffer overflowed and dropped its worst
+                                 entries; the result is valid but may differ from the
+                                 unbounded algorithm */
+
+/* Search parameters. unify_default_params() fills the defaults shown. */
+typedef struct {
+  int ef;              /* Algorithm 7 layer-0 beam (ann capacity), default 100 */
+  int m;               /* neighbours visited per expanded object (S2), default 16 */
+  int ef_post;         /* Algorithm 1 layer-0 beam of Strategy B; <= 0 means ef */
+  int rerank_mult;     /* BF16/FP8: re-rank rerank_mult * k candidates in FP32, default 4 */
+  unify_dtype_t dtype; /* storage read by traversal and scan, default UNIFY_FP32 */
+  int64_t tau_a;       /* Strategy A when Y <= tau_a; < 0 means floor(0.01 n) */
+  int64_t tau_b;       /* Strategy B when Y >= tau_b; < 0 means floor(0.5 n) */
+  int cand_cap;        /* candidate buffer entries per query, default 512 (<= 4096) */
+  int visited_cap;     /* visited-filter slots per query, power of two, default 2048 */
+  int max_expansions;  /* expansions per layer before UNIFY_Q_LIMIT, default 100000 */
+  int warps_per_block; /* graph-search warps per CTA, default 4 */
+  int scan_rows;       /* pre-filter rows per scan work item, default 8192 */
+} unify_params_t;
+
+/* Fills *p with the defaults above. */
+UNIFY_API void unify_default_params(unify_params_t* p);
+
+/* Reads the serialised HSIG at `path` (written by the host builder), verifies its
+ * section checksums and copies it to `device`; the attribute-sorted vector copy
+ * and the positions are derived on the device. On success *out owns the device
+ * memory until unify_free_index. Synchronous. Errors: UNIFY_E_ARG, UNIFY_E_IO,
+ * UNIFY_E_FORMAT, UNIFY_E_NOMEM, UNIFY_E_CUDA. */
+UNIFY_API int unify_load_index(const char* path, int device, unify_index_t** out);
+
+/* Releases every device and host buffer of the index (NULL is ignored). The caller
+ * must make sure no search on the index is still running. */
+UNIFY_API void unify_free_index(unify_index_t* idx);
+
+/* Index sizes; any output pointer may be NULL. */
+UNIFY_API int unify_index_info(const unify_index_t* idx, int64_t* n, int* d, int* S, int* M, int* max_level);
+
+/* Range resolution and range-aware selection for nq queries (device pointers):
+ *   out_pa[i] = #{v : v[A] < lo[i]}, out_pb[i] = max(pa, #{v : v[A] <= hi[i]})
+ *       (the in-range objects are positions [pa, pb) of the attribute order, so
+ *        Y = pb - pa; the skip-list descent of Strategy A lands on position pa);
+ *   out_mask[i] bit j: segment j holds objects, b_j <= hi and lo < b_{j+1}
+ *       (segments are half-open [b_j, b_{j+1}) with b_0 = -inf, b_S = +inf);
+ *   out_strategy[i] = UNIFY_PRE / UNIFY_HYBRID / UNIFY_POST by Y vs tau_a, tau_b
+ *       (tau < 0 selects the default).
+ * Any output may be NULL. Asynchronous on `stream`. */
+UNIFY_API int unify_route(unify_index_t* idx, const int64_t* lo, const int64_t* hi, int64_t nq, int64_t tau_a,
+                int64_t tau_b, int32_t* out_pa, int32_t* out_pb, uint32_t* out_mask,
+                int32_t* out_strategy, void* stream);
+
+/* Searches nq queries with one strategy (UNIFY_AUTO routes per query).
+ *   q          nq x d float32, row-major, device
+ *   lo, hi     nq int64, device, inclusive ranges
+ *   k          results per query, 1 <= k <= 256
+ *   ef         overrides p->ef (and ef_post when p->ef_post <= 0); ef >= 1
+ *   p          parameters, NULL = defaults
+ *   out_ids    nq x k int64, device;  out_dist nq x k float32 (squared L2), device
+ *   out_count  nq int32, device: number of valid results in the row
+ *   out_status nq uint32 bit set of UNIFY_Q_*, device, may be NULL
+ *   out_counters nq x 2 int32 (distance evaluations, expansions), device, may be NULL
+ * The first call with a larger nq grows the index's scratch buffers (a device
+ * allocation); make that call before capturing the stream into a CUDA graph. */
+UNIFY_API int unify_search(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi, int64_t nq,
+                 int k, int ef, unify_strategy_t strategy, const unify_params_t* p, int64_t* out_ids,
+                 float* out_dist, int32_t* out_count, uint32_t* out_status, int32_t* out_counters,
+                 void* stream);
+
+/* unify_search with strategy UNIFY_AUTO (range-aware selection). */
+UNIFY_API int unify_search_auto(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,
+                      int64_t nq, int k, int ef, const unify_params_t* p, int64_t* out_ids,
+                      float* out_dist, int32_t* out_count, uint32_t* out_status, void* stream);
+
+/* unify_search_auto on HOST buffers (pinned memory is fastest): the inputs are
+ * copied to index-owned device staging buffers on `stream`, searched, and the
+ * results copied back; returns after the stream has finished that work. */
+UNIFY_API int unify_search_auto_host(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,
+                           int64_t nq, int k, int ef, const unify_params_t* p, int64_t* out_ids,
+                           float* out_dist, int32_t* out_count, uint32_t* out_status, void* stream);
+
+/* Message of the last failed call on this thread ("" when none). */
+UNIFY_API const char* unify_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UNIFY_H */

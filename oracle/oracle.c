@@ -466,7 +466,9 @@ static int alg7(const orc_index* ix, const float* q, int32_t ep, int l, int k, i
 /* Strategy B (R7). */
 static int64_t strategy_post(const orc_index* ix, const float* q, int64_t lo, int64_t hi, int k,
                              int ef_post, scratch_t* s, key_t_* out) {
-  if (lo > hi) return 0;
+  int64_t pa, pb;
+  orc_range_bounds(ix, lo, hi, &pa, &pb);
+  if (pb <= pa) return 0; /* no object in range: the filter would leave nothing */
   int32_t ep = ix->entry_global;
   for (int l = ix->max_level; l >= 1; --l) {
     if (alg1_global(ix, q, ep, l, 1, s)) return -1;

@@ -1,0 +1,192 @@
+"""GB300 range-filtered k-NN search over an HSIG (UNIFY, Section 4.2).
+
+Thin ctypes binding of ``libunify.so`` (the C ABI in ``include/unify.h``).
+Every step of the search runs in the library's CUDA kernels; PyTorch is used
+only to own device memory and streams. The binding refuses to work when the
+compiled library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libunify.so")
+
+PRE, HYBRID, POST, AUTO = 0, 1, 2, -1
+STRATEGIES = {"pre": PRE, "hybrid": HYBRID, "post": POST, "auto": AUTO}
+FP32, BF16, FP8E4M3 = 0, 1, 2
+Q_LIMIT, Q_TRUNCATED = 1, 2
+
+_P = ctypes.c_void_p
+_lock = threading.Lock()
+_lib = None
+
+
+class UnifyError(RuntimeError):
+    pass
+
+
+class Params(ctypes.Structure):
+    """Mirror of unify_params_t."""
+    _fields_ = [("ef", ctypes.c_int), ("m", ctypes.c_int), ("ef_post", ctypes.c_int),
+                ("rerank_mult", ctypes.c_int), ("dtype", ctypes.c_int), ("tau_a", ctypes.c_int64),
+                ("tau_b", ctypes.c_int64), ("cand_cap", ctypes.c_int), ("visited_cap", ctypes.c_int),
+                ("max_expansions", ctypes.c_int), ("warps_per_block", ctypes.c_int),
+                ("scan_rows", ctypes.c_int)]
+
+    @classmethod
+    def defaults(cls, **kw) -> "Params":
+        p = cls()
+        lib().unify_default_params(ctypes.byref(p))
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        return p
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def lib():
+    """The loaded CUDA library; raises when it was not built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise UnifyError(f"CUDA library not built: {LIB_PATH} is missing (run build())")
+            L = ctypes.CDLL(LIB_PATH)
+            L.unify_default_params.argtypes = [_P]
+            L.unify_default_params.restype = None
+            L.unify_load_index.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(_P)]
+            L.unify_load_index.restype = ctypes.c_int
+            L.unify_free_index.argtypes = [_P]
+            L.unify_free_index.restype = None
+            L.unify_index_info.argtypes = [_P, _P, _P, _P, _P, _P]
+            L.unify_index_info.restype = ctypes.c_int
+            L.unify_route.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                      _P, _P, _P, _P, _P]
+            L.unify_route.restype = ctypes.c_int
+            L.unify_search.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]
+            L.unify_search.restype = ctypes.c_int
+            L.unify_search_auto.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                            _P, _P, _P, _P, _P, _P]
+            L.unify_search_auto.restype = ctypes.c_int
+            L.unify_search_auto_host.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int,
+                                                 ctypes.c_int, _P, _P, _P, _P, _P, _P]
+            L.unify_search_auto_host.restype = ctypes.c_int
+            L.unify_last_error.argtypes = []
+            L.unify_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise UnifyError(f"{what} failed ({rc}): {lib().unify_last_error().decode()}")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(torch, device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Index:
+    """An HSIG index resident on one GPU."""
+
+    def __init__(self, path: str, device: int = 0):
+        import torch
+        self._torch = torch
+        self.device = torch.device("cuda", device)
+        h = _P()
+        _check(lib().unify_load_index(path.encode(), device, ctypes.byref(h)), "unify_load_index")
+        self._h = h
+        n, d, S, M, L = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().unify_index_info(h, ctypes.byref(n), ctypes.byref(d), ctypes.byref(S), ctypes.byref(M),
+                                      ctypes.byref(L)), "unify_index_info")
+        self.n, self.d, self.S, self.M, self.max_level = n.value, d.value, S.value, M.value, L.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().unify_free_index(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers
+    def _dev(self, x, dtype):
+        t = self._torch.as_tensor(x)
+        return t.to(device=self.device, dtype=dtype).contiguous()
+
+    def route(self, lo, hi, tau_a: int = -1, tau_b: int = -1):
+        torch = self._torch
+        lo, hi = self._dev(lo, torch.int64), self._dev(hi, torch.int64)
+        nq = lo.numel()
+        out = {k: torch.empty(nq, dtype=torch.int32, device=self.device) for k in ("pa", "pb", "mask", "strategy")}
+        _check(lib().unify_route(self._h, _ptr(lo), _ptr(hi), nq, tau_a, tau_b, _ptr(out["pa"]), _ptr(out["pb"]),
+                                 _ptr(out["mask"]), _ptr(out["strategy"]), _stream_handle(torch, self.device)),
+               "unify_route")
+        return out
+
+    def search(self, q, lo, hi, k: int, ef: int = 0, strategy="auto", params: Params | None = None,
+               out=None, counters: bool = False):
+        """Returns dict(ids int64 [nq,k], dist float32 [nq,k], count int32 [nq], status int32 [nq]
+        [, counters int32 [nq,2]]) as device tensors. ``out`` may pass preallocated tensors."""
+        torch = self._torch
+        q = self._dev(q, torch.float32).reshape(-1, self.d)
+        lo, hi = self._dev(lo, torch.int64), self._dev(hi, torch.int64)
+        nq = q.shape[0]
+        if lo.numel() != nq or hi.numel() != nq:
+            raise ValueError("q, lo and hi must have the same number of queries")
+        st = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        if out is None:
+            out = dict(ids=torch.empty((nq, k), dtype=torch.int64, device=self.device),
+                       dist=torch.empty((nq, k), dtype=torch.float32, device=self.device),
+                       count=torch.empty(nq, dtype=torch.int32, device=self.device),
+                       status=torch.empty(nq, dtype=torch.int32, device=self.device))
+            if counters:
+                out["counters"] = torch.empty((nq, 2), dtype=torch.int32, device=self.device)
+        p = ctypes.byref(params) if params is not None else None
+        _check(lib().unify_search(self._h, _ptr(q), _ptr(lo), _ptr(hi), nq, k, ef, st, p, _ptr(out["ids"]),
+                                  _ptr(out["dist"]), _ptr(out["count"]), _ptr(out.get("status")),
+                                  _ptr(out.get("counters")), _stream_handle(torch, self.device)),
+               "unify_search")
+        return out
+
+    def search_auto(self, q, lo, hi, k: int, ef: int = 0, params: Params | None = None, out=None):
+        return self.search(q, lo, hi, k, ef=ef, strategy=AUTO, params=params, out=out)
+
+    def search_auto_host(self, q: np.ndarray, lo: np.ndarray, hi: np.ndarray, k: int, ef: int = 0,
+                         params: Params | None = None, out=None):
+        """Host buffers in and out (numpy arrays or pinned CPU tensors); synchronous."""
+        q = np.ascontiguousarray(q, dtype=np.float32) if isinstance(q, np.ndarray) else q
+        lo = np.ascontiguousarray(lo, dtype=np.int64) if isinstance(lo, np.ndarray) else lo
+        hi = np.ascontiguousarray(hi, dtype=np.int64) if isinstance(hi, np.ndarray) else hi
+        nq = lo.shape[0]
+        if out is None:
+            out = dict(ids=np.empty((nq, k), np.int64), dist=np.empty((nq, k), np.float32),
+                       count=np.empty(nq, np.int32), status=np.empty(nq, np.uint32))
+
+        def hp(a):
+            return ctypes.c_void_p(a.ctypes.data) if isinstance(a, np.ndarray) else ctypes.c_void_p(a.data_ptr())
+
+        p = ctypes.byref(params) if params is not None else None
+        _check(lib().unify_search_auto_host(self._h, hp(q), hp(lo), hp(hi), nq, k, ef, p, hp(out["ids"]),
+                                            hp(out["dist"]), hp(out["count"]), hp(out["status"]),
+                                            _stream_handle(self._torch, self.device)),
+               "unify_search_auto_host")
+        return out

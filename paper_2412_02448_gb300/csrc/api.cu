@@ -1,0 +1,278 @@
+// C ABI entry points: argument checks, parameters, scratch, and the launch
+// sequence route -> pre-filter scan (+ merge) -> hybrid search -> post search.
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace unify {
+
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(e == cudaErrorMemoryAllocation ? UNIFY_E_NOMEM : UNIFY_E_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+void release(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_core(Scratch& sc) {
+  release(sc.pa);
+  release(sc.pb);
+  release(sc.mask);
+  release(sc.strat);
+  release(sc.nblk);
+  release(sc.qbase);
+  release(sc.queues);
+  release(sc.items);
+  release(sc.part);
+  release(sc.counters);
+  sc.cap_nq = 0;
+  sc.cap_k = 0;
+}
+
+void free_stage(Scratch& sc) {
+  release(sc.s_q);
+  release(sc.s_lo);
+  release(sc.s_hi);
+  release(sc.s_ids);
+  release(sc.s_dist);
+  release(sc.s_count);
+  release(sc.s_status);
+  sc.stage_nq = 0;
+  sc.stage_k = 0;
+  sc.stage_d = 0;
+}
+
+template <typename T>
+cudaError_t alloc(T*& p, size_t elems) {
+  return cudaMalloc(reinterpret_cast<void**>(&p), (elems > 0 ? elems : 1) * sizeof(T));
+}
+
+// Grows the scratch to hold nq queries with k results (device allocation).
+cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k) {
+  if (sc.counters && nq <= sc.cap_nq && k <= sc.cap_k) return cudaSuccess;
+  int64_t cap = nq > sc.cap_nq ? nq : sc.cap_nq;
+  if (cap < 256) cap = 256;
+  int kc = k > sc.cap_k ? k : sc.cap_k;
+  if (kc < 16) kc = 16;
+  free_core(sc);
+  cudaError_t e = alloc(sc.pa, cap);
+  if (e == cudaSuccess) e = alloc(sc.pb, cap);
+  if (e == cudaSuccess) e = alloc(sc.mask, cap);
+  if (e == cudaSuccess) e = alloc(sc.strat, cap);
+  if (e == cudaSuccess) e = alloc(sc.nblk, cap);
+  if (e == cudaSuccess) e = alloc(sc.qbase, cap);
+  if (e == cudaSuccess) e = alloc(sc.queues, 3 * cap);
+  if (e == cudaSuccess) e = alloc(sc.items, cap * kMaxScanBlocks);
+  if (e == cudaSuccess) e = alloc(sc.part, (size_t)cap * kMaxScanBlocks * kc);
+  if (e == cudaSuccess) e = alloc(sc.counters, kNumCounters);
+  if (e != cudaSuccess) {
+    free_core(sc);
+    return e;
+  }
+  sc.cap_nq = cap;
+  sc.cap_k = kc;
+  return cudaSuccess;
+}
+
+cudaError_t ensure_stage(Scratch& sc, int64_t nq, int k, int d) {
+  if (sc.s_q && nq <= sc.stage_nq && k <= sc.stage_k && d == sc.stage_d) return cudaSuccess;
+  int64_t cap = nq > sc.stage_nq ? nq : sc.stage_nq;
+  int kc = k > sc.stage_k ? k : sc.stage_k;
+  free_stage(sc);
+  cudaError_t e = alloc(sc.s_q, (size_t)cap * d);
+  if (e == cudaSuccess) e = alloc(sc.s_lo, cap);
+  if (e == cudaSuccess) e = alloc(sc.s_hi, cap);
+  if (e == cudaSuccess) e = alloc(sc.s_ids, (size_t)cap * kc);
+  if (e == cudaSuccess) e = alloc(sc.s_dist, (size_t)cap * kc);
+  if (e == cudaSuccess) e = alloc(sc.s_count, cap);
+  if (e == cudaSuccess) e = alloc(sc.s_status, cap);
+  if (e != cudaSuccess) {
+    free_stage(sc);
+    return e;
+  }
+  sc.stage_nq = cap;
+  sc.stage_k = kc;
+  sc.stage_d = d;
+  return cudaSuccess;
+}
+
+int graph_warp_bytes(int cand_cap, int ann_cap, int vis_log2) {
+  int b = cand_cap * 8 + ann_cap * 8 + (4 << vis_log2);
+  b += (cand_cap + 15) & ~15;
+  b += 32 * 4 + 32 * 4 + 64 * 4;
+  return (b + 15) & ~15;
+}
+
+int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Params& p) {
+  unify_params_t d;
+  unify_default_params(&d);
+  if (up) d = *up;
+  if (k < 1 || k > kMaxK) return fail(UNIFY_E_ARG, "k must be in [1, 256]");
+  p.k = k;
+  p.ef = ef > 0 ? ef : d.ef;
+  p.ef_post = d.ef_post > 0 ? d.ef_post : p.ef;
+  p.m = d.m;
+  p.cand_cap = d.cand_cap;
+  p.max_exp = d.max_expansions;
+  p.warps_per_block = d.warps_per_block;
+  p.scan_rows = d.scan_rows;
+  p.dtype = d.dtype;
+  p.tau_a = d.tau_a >= 0 ? d.tau_a : ix.n / 100;
+  p.tau_b = d.tau_b >= 0 ? d.tau_b : ix.n / 2;
+  if (p.ef < 1 || p.ef > 2048 || p.ef_post < 1 || p.ef_post > 2048) return fail(UNIFY_E_ARG, "ef and ef_post must be in [1, 2048]");
+  if (p.m < 1 || p.m > 1024) return fail(UNIFY_E_ARG, "m must be in [1, 1024]");
+  if (p.cand_cap < 32 || p.cand_cap > kMaxCand) return fail(UNIFY_E_ARG, "cand_cap must be in [32, 4096]");
+  if (d.visited_cap < 64 || d.visited_cap > 65536 || (d.visited_cap & (d.visited_cap - 1)))
+    return fail(UNIFY_E_ARG, "visited_cap must be a power of two in [64, 65536]");
+  p.vis_log2 = 0;
+  while ((1 << p.vis_log2) < d.visited_cap) ++p.vis_log2;
+  if (p.max_exp < 1) return fail(UNIFY_E_ARG, "max_expansions must be >= 1");
+  if (p.warps_per_block < 1 || p.warps_per_block > 8) return fail(UNIFY_E_ARG, "warps_per_block must be in [1, 8]");
+  if (p.scan_rows < 32) return fail(UNIFY_E_ARG, "scan_rows must be >= 32");
+  if (p.dtype != UNIFY_FP32) return fail(UNIFY_E_ARG, "dtype: only UNIFY_FP32 is available in this build");
+  const int annc = (p.ef > p.ef_post ? p.ef : p.ef_post) > k ? (p.ef > p.ef_post ? p.ef : p.ef_post) : k;
+  const long smem = (long)p.warps_per_block * graph_warp_bytes(p.cand_cap, annc, p.vis_log2);
+  if (smem > 227 * 1024) return fail(UNIFY_E_LIMIT, "graph search shared memory per CTA exceeds 227 KB; lower warps_per_block, cand_cap, visited_cap or ef");
+  return UNIFY_OK;
+}
+
+int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi, int64_t nq, int k,
+               int ef, int strategy, const unify_params_t* up, int64_t* out_ids, float* out_dist,
+               int32_t* out_count, uint32_t* out_status, int32_t* out_counters, cudaStream_t st) {
+  if (!idx) return fail(UNIFY_E_ARG, "null index");
+  if (nq < 0 || nq >= (1ll << 31) / kMaxScanBlocks) return fail(UNIFY_E_ARG, "nq out of range");
+  if (strategy < -1 || strategy > 2) return fail(UNIFY_E_ARG, "bad strategy");
+  Params p;
+  int rc = resolve(idx->ix, up, k, ef, p);
+  if (rc != UNIFY_OK) return rc;
+  if (nq == 0) return UNIFY_OK;
+  if (!q || !lo || !hi || !out_ids || !out_dist || !out_count) return fail(UNIFY_E_ARG, "null query or output pointer");
+  DeviceGuard guard(idx->ix.device);
+  cudaError_t e = ensure_scratch(idx->sc, nq, k);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+  Scratch& sc = idx->sc;
+  e = cudaMemsetAsync(sc.counters, 0, kNumCounters * sizeof(int32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "counter reset");
+  Outputs o{out_ids, out_dist, out_count, out_status, out_counters};
+  e = launch_route(idx->ix, sc, lo, hi, nq, p.tau_a, p.tau_b, strategy, p.scan_rows, 1, sc.pa, sc.pb, sc.mask,
+                   sc.strat, &o, st);
+  if (e != cudaSuccess) return cuda_fail(e, "route kernel");
+  if (strategy == UNIFY_PRE || strategy == UNIFY_AUTO) {
+    e = launch_scan(idx->ix, sc, q, nq, p, o, st);
+    if (e != cudaSuccess) return cuda_fail(e, "pre-filter scan");
+  }
+  if (strategy == UNIFY_HYBRID || strategy == UNIFY_AUTO) {
+    e = launch_graph(idx->ix, sc, q, nq, UNIFY_HYBRID, p, o, st);
+    if (e != cudaSuccess) return cuda_fail(e, "hybrid search");
+  }
+  if (strategy == UNIFY_POST || strategy == UNIFY_AUTO) {
+    e = launch_graph(idx->ix, sc, q, nq, UNIFY_POST, p, o, st);
+    if (e != cudaSuccess) return cuda_fail(e, "post-filter search");
+  }
+  return UNIFY_OK;
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+void free_scratch(Scratch& sc) {
+  free_core(sc);
+  free_stage(sc);
+}
+
+}  // namespace unify
+
+using namespace unify;
+
+extern "C" void unify_default_params(unify_params_t* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->ef = 100;
+  p->m = 16;
+  p->ef_post = 0;
+  p->rerank_mult = 4;
+  p->dtype = UNIFY_FP32;
+  p->tau_a = -1;
+  p->tau_b = -1;
+  p->cand_cap = 512;
+  p->visited_cap = 2048;
+  p->max_expansions = 100000;
+  p->warps_per_block = 4;
+  p->scan_rows = 8192;
+}
+
+extern "C" const char* unify_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int unify_route(unify_index_t* idx, const int64_t* lo, const int64_t* hi, int64_t nq, int64_t tau_a,
+                           int64_t tau_b, int32_t* out_pa, int32_t* out_pb, uint32_t* out_mask,
+                           int32_t* out_strategy, void* stream) {
+  if (!idx) return fail(UNIFY_E_ARG, "unify_route: null index");
+  if (nq < 0) return fail(UNIFY_E_ARG, "unify_route: nq < 0");
+  if (nq == 0) return UNIFY_OK;
+  if (!lo || !hi) return fail(UNIFY_E_ARG, "unify_route: null range pointer");
+  DeviceGuard guard(idx->ix.device);
+  const int64_t ta = tau_a >= 0 ? tau_a : idx->ix.n / 100;
+  const int64_t tb = tau_b >= 0 ? tau_b : idx->ix.n / 2;
+  cudaError_t e = launch_route(idx->ix, idx->sc, lo, hi, nq, ta, tb, -1, 8192, 0, out_pa, out_pb, out_mask,
+                               out_strategy, nullptr, (cudaStream_t)stream);
+  return e == cudaSuccess ? UNIFY_OK : cuda_fail(e, "unify_route");
+}
+
+extern "C" int unify_search(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi, int64_t nq,
+                            int k, int ef, unify_strategy_t strategy, const unify_params_t* p, int64_t* out_ids,
+                            float* out_dist, int32_t* out_count, uint32_t* out_status, int32_t* out_counters,
+                            void* stream) {
+  return run_search(idx, q, lo, hi, nq, k, ef, (int)strategy, p, out_ids, out_dist, out_count, out_status,
+                    out_counters, (cudaStream_t)stream);
+}
+
+extern "C" int unify_search_auto(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,
+                                 int64_t nq, int k, int ef, const unify_params_t* p, int64_t* out_ids,
+                                 float* out_dist, int32_t* out_count, uint32_t* out_status, void* stream) {
+  return run_search(idx, q, lo, hi, nq, k, ef, UNIFY_AUTO, p, out_ids, out_dist, out_count, out_status, nullptr,
+                    (cudaStream_t)stream);
+}
+
+extern "C" int unify_search_auto_host(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,
+                                      int64_t nq, int k, int ef, const unify_params_t* p, int64_t* out_ids,
+                                      float* out_dist, int32_t* out_count, uint32_t* out_status, void* stream) {
+  if (!idx) return fail(UNIFY_E_ARG, "null index");
+  if (nq < 0) return fail(UNIFY_E_ARG, "nq < 0");
+  if (k < 1 || k > kMaxK) return fail(UNIFY_E_ARG, "k must be in [1, 256]");
+  if (nq == 0) return UNIFY_OK;
+  if (!q || !lo || !hi || !out_ids || !out_dist || !out_count) return fail(UNIFY_E_ARG, "null query or output pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  DeviceGuard guard(idx->ix.device);
+  Scratch& sc = idx->sc;
+  const int d = idx->ix.d;
+  cudaError_t e = ensure_stage(sc, nq, k, d);
+  if (e != cudaSuccess) return cuda_fail(e, "staging allocation");
+  e = cudaMemcpyAsync(sc.s_q, q, (size_t)nq * d * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sc.s_lo, lo, (size_t)nq * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sc.s_hi, hi, (size_t)nq * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  int rc = run_search(idx, sc.s_q, sc.s_lo, sc.s_hi, nq, k, ef, UNIFY_AUTO, p, sc.s_ids, sc.s_dist, sc.s_count,
+                      sc.s_status, nullptr, st);
+  if (rc != UNIFY_OK) return rc;
+  e = cudaMemcpyAsync(out_ids, sc.s_ids, (size_t)nq * k * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_dist, sc.s_dist, (size_t)nq * k * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_count, sc.s_count, (size_t)nq * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && out_status)
+    e = cudaMemcpyAsync(out_status, sc.s_status, (size_t)nq * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? UNIFY_OK : cuda_fail(e, "device-to-host copy");
+}

@@ -1,0 +1,178 @@
+// Warp-level device primitives shared by the search kernels.
+//
+// Keys: a candidate (distance, id) is packed into one uint64 as
+// (bits of the non-negative float32 distance) << 32 | id. For non-negative
+// floats the IEEE bit pattern orders like the value, so comparing keys compares
+// (distance, id) lexicographically: the tie rule "equal distance -> smaller id".
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace unify {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint64_t kKeyMax = ~0ull;
+
+__device__ __forceinline__ uint64_t make_key(float d, int32_t id) {
+  return ((uint64_t)__float_as_uint(d) << 32) | (uint32_t)id;
+}
+__device__ __forceinline__ float key_dist(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
+__device__ __forceinline__ int32_t key_id(uint64_t k) { return (int32_t)(uint32_t)(k & 0xffffffffu); }
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+// Bitonic sort of one key per lane, ascending across lanes 0..31.
+__device__ __forceinline__ uint64_t warp_sort_asc(uint64_t x) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      uint64_t y = __shfl_xor_sync(kFull, x, j);
+      bool up = (lane & k) == 0;
+      bool lower = (lane & j) == 0;
+      x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
+    }
+  }
+  return x;
+}
+
+// First index i in a[0, n) with a[i] >= x (per lane).
+__device__ __forceinline__ int lower_bound_u64(const uint64_t* a, int n, uint64_t x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// First index i in a[0, n) with a[i] > x (per lane).
+__device__ __forceinline__ int upper_bound_u64(const uint64_t* a, int n, uint64_t x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool contains_u64(const uint64_t* a, int n, uint64_t x) {
+  int i = lower_bound_u64(a, n, x);
+  return i < n && a[i] == x;
+}
+
+// Merges a sorted batch into the sorted array arr[0, n) of capacity cap, in place.
+// Every lane of the warp calls it. Lane i < nb holds the i-th smallest batch key
+// (distinct from every arr entry); the other lanes hold kKeyMax. Entries that fall
+// beyond cap are dropped (the largest ones). flags (may be null) move with their
+// keys; new entries get flag 0. R is 32 ints of per-warp shared scratch.
+// Returns the new size; *r0 = rank of the smallest batch key in the old array
+// (entries below r0 did not move); *dropped = some entry fell beyond cap.
+__device__ __forceinline__ int warp_merge(uint64_t* arr, uint8_t* flags, int n, int cap, uint64_t bk,
+                                          int nb, int* R, int* r0_out, bool* dropped) {
+  const int lane = lane_id();
+  int r = (lane < nb) ? lower_bound_u64(arr, n, bk) : n;
+  R[lane] = r;
+  __syncwarp();
+  const int r0 = __shfl_sync(kFull, r, 0);
+  if (n > 0 && nb > 0) {
+    for (int base = (n - 1) & ~31; base >= (r0 & ~31); base -= 32) {
+      int j = base + lane;
+      bool act = j >= r0 && j < n;
+      uint64_t v = 0;
+      uint8_t f = 0;
+      int dst = 0;
+      if (act) {
+        int a = 0, b = nb;  // number of batch keys with rank <= j
+        while (a < b) {
+          int mid = (a + b) >> 1;
+          if (R[mid] <= j) a = mid + 1; else b = mid;
+        }
+        dst = j + a;
+        v = arr[j];
+        if (flags) f = flags[j];
+      }
+      __syncwarp();
+      if (act && dst < cap) {
+        arr[dst] = v;
+        if (flags) flags[dst] = f;
+      }
+      __syncwarp();
+    }
+  }
+  if (lane < nb) {
+    int dst = r + lane;
+    if (dst < cap) {
+      arr[dst] = bk;
+      if (flags) flags[dst] = 0;
+    }
+  }
+  __syncwarp();
+  *r0_out = r0;
+  *dropped = (n + nb) > cap;
+  return (n + nb) < cap ? (n + nb) : cap;
+}
+
+// Transposed warp reduction of V partial values per lane (V in {8, 16, 32}).
+// Afterwards the lanes whose index >> log2(32/V) equals u hold the sum over all
+// 32 lanes of value u. Every value is summed by the same tree (pairs across lane
+// bit 4, then bit 3, ..., bit 0), so a vector's distance does not depend on the
+// slot it was computed in.
+template <int V>
+__device__ __forceinline__ float warp_transpose_reduce(float (&v)[V]) {
+  const int lane = lane_id();
+  int off = 16;
+#pragma unroll
+  for (int cnt = V; cnt > 1; cnt >>= 1, off >>= 1) {
+    const int half = cnt >> 1;
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      float send = up ? v[i] : v[i + half];
+      float keep = up ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, off);
+    }
+  }
+#pragma unroll
+  for (; off >= 1; off >>= 1) v[0] += __shfl_xor_sync(kFull, v[0], off);
+  return v[0];
+}
+
+// Squared-L2 partial of one lane over its float4 chunks c = lane + 32 t.
+template <int CH>
+__device__ __forceinline__ float l2_partial(const float4 (&q)[CH], const float* row, int nchunks) {
+  const int lane = lane_id();
+  float s = 0.f;
+#pragma unroll
+  for (int t = 0; t < CH; ++t) {
+    int c = lane + 32 * t;
+    if (c < nchunks) {
+      float4 x = __ldg(reinterpret_cast<const float4*>(row) + c);
+      float a = q[t].x - x.x, b = q[t].y - x.y, e = q[t].z - x.z, f = q[t].w - x.w;
+      s = fmaf(a, a, s);
+      s = fmaf(b, b, s);
+      s = fmaf(e, e, s);
+      s = fmaf(f, f, s);
+    }
+  }
+  return s;
+}
+
+// Loads the query into the per-lane chunks (zero beyond d).
+template <int CH>
+__device__ __forceinline__ void load_query(float4 (&q)[CH], const float* qrow, int d) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int t = 0; t < CH; ++t) {
+    int c = (lane + 32 * t) * 4;
+    q[t].x = c + 0 < d ? qrow[c + 0] : 0.f;
+    q[t].y = c + 1 < d ? qrow[c + 1] : 0.f;
+    q[t].z = c + 2 < d ? qrow[c + 2] : 0.f;
+    q[t].w = c + 3 < d ? qrow[c + 3] : 0.f;
+  }
+}
+
+}  // namespace unify

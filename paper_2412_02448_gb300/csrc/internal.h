@@ -1,0 +1,124 @@
+// Internal declarations of the CUDA search library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/unify.h"
+
+namespace unify {
+
+constexpr int kMaxS = 32;      // segments (one bit each in a 32-bit mask)
+constexpr int kMaxK = 256;     // results per query
+constexpr int kMaxCand = 4096; // candidate buffer entries per query
+constexpr int kMaxScanBlocks = 64;  // scan work items per pre-filter query
+
+// Device-resident index. Arrays marked (n) are indexed by object id unless noted.
+struct DeviceIndex {
+  int device = 0;
+  int64_t n = 0, n_upper = 0;
+  int d = 0, dp = 0;           // dimension and padded row stride (multiple of 4 floats)
+  int S = 0, M = 0, W = 0;     // segments, chunk width, bitmap words per row
+  int max_level = 0, entry_global = 0;
+  int64_t h_seg_bounds[kMaxS + 1];
+  int32_t h_seg_start[kMaxS + 1];  // first attribute-order position of each segment
+  // device memory
+  float* vec = nullptr;         // (n, dp) float32 by id
+  float* vec_sorted = nullptr;  // (n, dp) float32 in attribute order
+  int32_t* sorted_ids = nullptr;   // attribute order (ties by id)
+  int64_t* sorted_attr = nullptr;  // attribute values in attribute order
+  int32_t* pos = nullptr;       // (n) position of each id in attribute order
+  int32_t* upper_base = nullptr;
+  int32_t* adj0 = nullptr;      // (n, S, M), -1 padded
+  uint32_t* gmask0 = nullptr;   // (n, W)
+  int32_t* adjU = nullptr;      // (n_upper, S, M)
+  uint32_t* gmaskU = nullptr;   // (n_upper, W)
+  int64_t* seg_bounds = nullptr;  // (S+1)
+  int32_t* seg_start = nullptr;   // (S+1)
+  int num_sms = 0;
+};
+
+// Per-index scratch, grown on demand.
+struct Scratch {
+  int64_t cap_nq = 0;
+  int cap_k = 0;
+  int32_t* pa = nullptr;
+  int32_t* pb = nullptr;
+  uint32_t* mask = nullptr;
+  int32_t* strat = nullptr;
+  int32_t* nblk = nullptr;     // scan work items of each pre-filter query
+  int32_t* qbase = nullptr;    // index of its first work item
+  int32_t* queues = nullptr;   // 3 x cap_nq: query ids per strategy (A, C, B)
+  int2* items = nullptr;       // cap_nq * kMaxScanBlocks scan work items (query, block)
+  uint64_t* part = nullptr;    // cap_nq * kMaxScanBlocks * cap_k partial top-k keys
+  int32_t* counters = nullptr; // kNumCounters ints, zeroed per call
+  // host-buffer staging
+  int64_t stage_nq = 0;
+  int stage_k = 0, stage_d = 0;
+  float* s_q = nullptr;
+  int64_t* s_lo = nullptr;
+  int64_t* s_hi = nullptr;
+  int64_t* s_ids = nullptr;
+  float* s_dist = nullptr;
+  int32_t* s_count = nullptr;
+  uint32_t* s_status = nullptr;
+};
+
+// counters[] layout
+enum {
+  CNT_QA = 0, CNT_QC = 1, CNT_QB = 2,  // queue lengths
+  CNT_ITEMS = 3,                       // scan work items
+  CNT_TAKE_ITEMS = 4,                  // scan work-queue head
+  CNT_TAKE_C = 5, CNT_TAKE_B = 6,      // graph work-queue heads
+  CNT_TAKE_MERGE = 7,
+  kNumCounters = 16
+};
+
+struct Params {
+  int k, ef, m, ef_post, cand_cap, vis_log2, max_exp, warps_per_block, scan_rows;
+  int64_t tau_a, tau_b;
+  unify_dtype_t dtype;
+};
+
+struct Outputs {
+  int64_t* ids;
+  float* dist;
+  int32_t* count;
+  uint32_t* status;
+  int32_t* counters;
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_route(const DeviceIndex& ix, const Scratch& sc, const int64_t* lo, const int64_t* hi,
+                         int64_t nq, int64_t tau_a, int64_t tau_b, int forced, int scan_rows,
+                         int build_queues, int32_t* out_pa, int32_t* out_pb, uint32_t* out_mask,
+                         int32_t* out_strat, const Outputs* outs, cudaStream_t st);
+cudaError_t launch_scan(const DeviceIndex& ix, const Scratch& sc, const float* q, int64_t nq,
+                        const Params& p, const Outputs& o, cudaStream_t st);
+cudaError_t launch_graph(const DeviceIndex& ix, const Scratch& sc, const float* q, int64_t nq,
+                         int strategy, const Params& p, const Outputs& o, cudaStream_t st);
+cudaError_t derive_sorted(DeviceIndex& ix, cudaStream_t st);
+
+void set_error(const std::string& msg);
+void free_scratch(Scratch& sc);
+
+// Makes `dev` current for the lifetime of the guard.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace unify
+
+struct unify_index {
+  unify::DeviceIndex ix;
+  unify::Scratch sc;
+};

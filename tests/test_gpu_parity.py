@@ -1,0 +1,228 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer-valued vectors (the c2 shape: coordinates in [0, 255], d = 128) make
+every float32 squared distance an exact integer below 2**24, so the GPU's
+float32 arithmetic equals the oracle's FP64 exactly and the approximate
+strategies must follow the very same traversal: ids and expansion counts are
+compared bit for bit. On real-valued data (c1) the pre-filter ids may only
+differ by swaps of items whose FP64 distances lie within 2e-5 relative, and
+distances must be within 1e-5 relative of FP64.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EXACT_BITS = 3  # UNIFY_Q_LIMIT | UNIFY_Q_TRUNCATED
+
+
+@pytest.fixture(scope="module")
+def U():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2412_02448_gb300 as U
+    assert torch.cuda.is_available()
+    return U
+
+
+def _np(r):
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in r.items()}
+
+
+def _edge_ranges(w):
+    lo = np.array([-5, 10**9, 7, 500, 0, -(2**62), 123456], np.int64)
+    hi = np.array([-1, 10**9 + 5, 6, 500, 10**7, 2**62, 123456 + 1000], np.int64)
+    q = w.queries[: len(lo)]
+    return q, lo, hi
+
+
+def test_route_parity(U, c2_small_index, c1_index):
+    for w, path in (c2_small_index, c1_index):
+        ix = U.Index(path)
+        oi = oracle.OracleIndex(path)
+        q, elo, ehi = _edge_ranges(w)
+        lo = np.concatenate([w.lo, elo])
+        hi = np.concatenate([w.hi, ehi])
+        ta, tb = w.n // 100, w.n // 2
+        g = _np(ix.route(lo, hi, ta, tb))
+        o = oi.route(lo, hi, ta, tb)
+        assert np.array_equal(g["pa"], o["pa"]) and np.array_equal(g["pb"], o["pb"])
+        assert np.array_equal(g["mask"].astype(np.uint32), o["mask"])
+        assert np.array_equal(g["strategy"], o["strategy"])
+
+
+def test_prefilter_exact_integer_data(U, c2_small_index):
+    w, path = c2_small_index
+    ix = U.Index(path)
+    q, elo, ehi = _edge_ranges(w)
+    Q = np.concatenate([w.queries, q])
+    lo = np.concatenate([w.lo, elo])
+    hi = np.concatenate([w.hi, ehi])
+    ex_ids, ex_d, ex_c = oracle.exact_knn(w.vectors, w.attrs, Q, lo, hi, w.k)
+    for scan_rows in (8192, 96):  # one work item, and a ragged split merged by the second kernel
+        r = _np(ix.search(Q, lo, hi, w.k, strategy="pre", params=U.Params.defaults(scan_rows=scan_rows),
+                          counters=True))
+        assert np.array_equal(r["count"], ex_c)
+        assert np.array_equal(r["ids"], ex_ids)
+        fin = np.isfinite(ex_d)
+        assert np.array_equal(r["dist"][fin].astype(np.float64), ex_d[fin])
+        assert np.all(np.isinf(r["dist"][~fin]))
+
+
+def test_prefilter_tie_band_real_data(U, c1_index):
+    w, path = c1_index
+    ix = U.Index(path)
+    for k in (1, 10, 100):
+        ex_ids, ex_d, ex_c = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, k)
+        r = _np(ix.search(w.queries, w.lo, w.hi, k, strategy="pre"))
+        assert np.array_equal(r["count"], ex_c)
+        for i in range(len(w.lo)):
+            c = ex_c[i]
+            g, e = r["ids"][i, :c], ex_ids[i, :c]
+            gd = r["dist"][i, :c].astype(np.float64)
+            assert np.all(np.abs(gd - ex_d[i, :c]) <= 1e-5 * np.maximum(ex_d[i, :c], 1e-30))
+            if not np.array_equal(g, e):
+                # only swaps inside the FP64 tie band, including at the k-th boundary
+                X = w.vectors.astype(np.float64)
+                dg = ((X[g] - w.queries[i].astype(np.float64)) ** 2).sum(1)
+                kth = ex_d[i, c - 1]
+                assert np.all(dg <= kth * (1 + 2e-5))
+                diff = set(g.tolist()) ^ set(e.tolist())
+                X_d = {j: ((X[j] - w.queries[i].astype(np.float64)) ** 2).sum() for j in diff}
+                assert all(abs(X_d[j] - kth) <= 2e-5 * kth for j in diff)
+
+
+@pytest.mark.parametrize("strategy", ["hybrid", "post"])
+@pytest.mark.parametrize("ef", [10, 64, 200])
+def test_graph_strategies_match_oracle(U, c2_small_index, strategy, ef):
+    """Same traversal as the oracle's literal Algorithms 1/2/7: ids and expansion
+    counts identical wherever the GPU reports no truncation or expansion limit."""
+    w, path = c2_small_index
+    ix = U.Index(path)
+    oi = oracle.OracleIndex(path)
+    r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=ef, strategy=strategy, counters=True))
+    o = oi.search(w.queries, w.lo, w.hi, w.k, ef=ef, m=16, strategy=strategy)
+    ok = (r["status"] & EXACT_BITS) == 0
+    assert ok.mean() > 0.9
+    assert np.array_equal(r["ids"][ok], o["ids"][ok])
+    assert np.array_equal(r["count"][ok], o["count"][ok])
+    assert np.array_equal(r["counters"][ok, 1], o["n_exp"][ok])
+    fin = np.isfinite(o["dist"][ok])
+    assert np.array_equal(r["dist"][ok][fin].astype(np.float64), o["dist"][ok][fin])
+
+
+@pytest.mark.parametrize("m", [4, 16, 40])
+def test_hybrid_selection_width(U, c2_small_index, m):
+    w, path = c2_small_index
+    ix = U.Index(path)
+    oi = oracle.OracleIndex(path)
+    r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=50, strategy="hybrid",
+                      params=U.Params.defaults(m=m), counters=True))
+    o = oi.search(w.queries, w.lo, w.hi, w.k, ef=50, m=m, strategy="hybrid")
+    ok = (r["status"] & EXACT_BITS) == 0
+    assert ok.mean() > 0.9
+    assert np.array_equal(r["ids"][ok], o["ids"][ok])
+    assert np.array_equal(r["counters"][ok, 1], o["n_exp"][ok])
+
+
+def test_auto_routing_matches_oracle(U, c2_small_index):
+    w, path = c2_small_index
+    ix = U.Index(path)
+    oi = oracle.OracleIndex(path)
+    ta, tb = w.n // 100, w.n // 2
+    p = U.Params.defaults(tau_a=ta, tau_b=tb)
+    r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=80, strategy="auto", params=p))
+    o = oi.search(w.queries, w.lo, w.hi, w.k, ef=80, m=16, strategy="auto", tau_a=ta, tau_b=tb)
+    assert set(np.unique(o["strategy"]).tolist()) == {0, 1, 2}
+    ok = (r["status"] & EXACT_BITS) == 0
+    assert np.array_equal(r["ids"][ok], o["ids"][ok])
+    ex = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, w.k)
+    rec = oracle.recall(r["ids"], ex[0], ex[2], w.k)
+    assert rec.mean() > 0.9
+
+
+def test_golden_tiny_line_graph_gpu(U, tmp_path):
+    from index_writer import tiny_index_sections, write_index
+    with open(os.path.join(GOLDEN, "tiny_line_graph.json")) as f:
+        g = json.load(f)
+    path = str(tmp_path / "tiny.idx")
+    write_index(path, tiny_index_sections(g))
+    ix = U.Index(path)
+    for case in g["cases"]:
+        p = U.Params.defaults(m=case["m"], ef_post=case["ef"])
+        r = _np(ix.search(np.array([case["q"]], np.float32), [case["lo"]], [case["hi"]], case["k"],
+                          ef=case["ef"], strategy=case["strategy"], params=p, counters=True))
+        assert list(r["ids"][0]) == case["expect_ids"], case["name"]
+        for got, exp in zip(r["dist"][0], case["expect_dist"]):
+            if exp is None:
+                assert np.isinf(got)
+            else:
+                assert got == pytest.approx(exp, rel=1e-5, abs=1e-6)
+        if case["strategy"] != "pre":
+            assert r["counters"][0, 1] == case["expect_n_exp"], case["name"]
+        assert r["counters"][0, 0] >= case["expect_n_dist"] or case["strategy"] == "pre"
+
+
+def test_edge_cases(U, c2_small_index):
+    w, path = c2_small_index
+    ix = U.Index(path)
+    # empty batch
+    r = ix.search(np.zeros((0, w.d), np.float32), np.zeros(0, np.int64), np.zeros(0, np.int64), 5)
+    assert r["ids"].shape == (0, 5)
+    # k = 1 and k = 256 (the maximum), k above |R|
+    lo = np.array([w.lo[0], 5, 100], np.int64)
+    hi = np.array([w.hi[0], 4, 160], np.int64)  # second is lo > hi
+    for k in (1, 256):
+        for st in ("pre", "hybrid", "post"):
+            r = _np(ix.search(w.queries[:3], lo, hi, k, ef=300, strategy=st))
+            assert r["count"][1] == 0 and np.all(r["ids"][1] == -1)
+            for i in (0, 2):
+                c = r["count"][i]
+                ids = r["ids"][i, :c]
+                assert np.all((w.attrs[ids] >= lo[i]) & (w.attrs[ids] <= hi[i]))
+                assert len(set(ids.tolist())) == c and np.all(r["ids"][i, c:] == -1)
+    # invalid arguments are reported, not run
+    with pytest.raises(U.UnifyError):
+        ix.search(w.queries[:2], w.lo[:2], w.hi[:2], 0)
+    with pytest.raises(U.UnifyError):
+        ix.search(w.queries[:2], w.lo[:2], w.hi[:2], 257)
+    with pytest.raises(U.UnifyError):
+        ix.search(w.queries[:2], w.lo[:2], w.hi[:2], 10, params=U.Params.defaults(visited_cap=1000))
+
+
+def test_host_buffers_equal_device(U, c2_small_index):
+    w, path = c2_small_index
+    ix = U.Index(path)
+    ta, tb = w.n // 100, w.n // 2
+    p = U.Params.defaults(tau_a=ta, tau_b=tb)
+    d = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy="auto", params=p))
+    h = ix.search_auto_host(w.queries, w.lo, w.hi, w.k, ef=64, params=p)
+    assert np.array_equal(d["ids"], h["ids"]) and np.array_equal(d["count"], h["count"])
+
+
+def test_bad_index_files_rejected(U, tmp_path):
+    from index_writer import tiny_index_sections, write_index
+    with open(os.path.join(GOLDEN, "tiny_line_graph.json")) as f:
+        g = json.load(f)
+    sec = tiny_index_sections(g)
+    bad = str(tmp_path / "bad.idx")
+    write_index(bad, sec, corrupt_section="vectors")
+    with pytest.raises(U.UnifyError, match="checksum"):
+        U.Index(bad)
+    sec2 = dict(sec)
+    adj = sec["adj0"].copy()
+    adj[0, 0, 0] = 10**6  # neighbour id out of range
+    sec2["adj0"] = adj
+    write_index(bad, sec2)
+    with pytest.raises(U.UnifyError, match="out of range"):
+        U.Index(bad)
+    with pytest.raises(U.UnifyError):
+        U.Index(str(tmp_path / "missing.idx"))
