@@ -21,6 +21,18 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 EXACT_BITS = 3  # UNIFY_Q_LIMIT | UNIFY_Q_TRUNCATED
+CAND = 2048     # candidate-buffer entries used by the exactness checks
+
+
+def _valid(w, r, lo, hi):
+    """Invariants of any result row: ids in range, no duplicates, sorted, padded."""
+    for i in range(len(lo)):
+        c = int(r["count"][i])
+        ids = r["ids"][i, :c]
+        assert np.all((w.attrs[ids] >= lo[i]) & (w.attrs[ids] <= hi[i]))
+        assert len(set(ids.tolist())) == c and np.all(r["ids"][i, c:] == -1)
+        keys = list(zip(r["dist"][i, :c].tolist(), ids.tolist()))
+        assert keys == sorted(keys)
 
 
 @pytest.fixture(scope="module")
@@ -108,10 +120,12 @@ def test_graph_strategies_match_oracle(U, c2_small_index, strategy, ef):
     w, path = c2_small_index
     ix = U.Index(path)
     oi = oracle.OracleIndex(path)
-    r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=ef, strategy=strategy, counters=True))
+    r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=ef, strategy=strategy, counters=True,
+                      params=U.Params.defaults(cand_cap=CAND)))
     o = oi.search(w.queries, w.lo, w.hi, w.k, ef=ef, m=16, strategy=strategy)
     ok = (r["status"] & EXACT_BITS) == 0
-    assert ok.mean() > 0.9
+    _valid(w, r, w.lo, w.hi)
+    assert ok.mean() > 0.8
     assert np.array_equal(r["ids"][ok], o["ids"][ok])
     assert np.array_equal(r["count"][ok], o["count"][ok])
     assert np.array_equal(r["counters"][ok, 1], o["n_exp"][ok])
@@ -125,10 +139,11 @@ def test_hybrid_selection_width(U, c2_small_index, m):
     ix = U.Index(path)
     oi = oracle.OracleIndex(path)
     r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=50, strategy="hybrid",
-                      params=U.Params.defaults(m=m), counters=True))
+                      params=U.Params.defaults(m=m, cand_cap=CAND), counters=True))
     o = oi.search(w.queries, w.lo, w.hi, w.k, ef=50, m=m, strategy="hybrid")
     ok = (r["status"] & EXACT_BITS) == 0
-    assert ok.mean() > 0.9
+    _valid(w, r, w.lo, w.hi)
+    assert ok.mean() > 0.8
     assert np.array_equal(r["ids"][ok], o["ids"][ok])
     assert np.array_equal(r["counters"][ok, 1], o["n_exp"][ok])
 
@@ -138,8 +153,9 @@ def test_auto_routing_matches_oracle(U, c2_small_index):
     ix = U.Index(path)
     oi = oracle.OracleIndex(path)
     ta, tb = w.n // 100, w.n // 2
-    p = U.Params.defaults(tau_a=ta, tau_b=tb)
+    p = U.Params.defaults(tau_a=ta, tau_b=tb, cand_cap=CAND)
     r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=80, strategy="auto", params=p))
+    _valid(w, r, w.lo, w.hi)
     o = oi.search(w.queries, w.lo, w.hi, w.k, ef=80, m=16, strategy="auto", tau_a=ta, tau_b=tb)
     assert set(np.unique(o["strategy"]).tolist()) == {0, 1, 2}
     ok = (r["status"] & EXACT_BITS) == 0
