@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark of batched range-filtered k-NN search (UNIFY / HSIG) on GB300.
+
+Workload (SIFT1M shape, seeded synthetic stand-in): n = 1,000,000 integer-valued
+vectors, d = 128, uniform integer attributes in [0, 1e6), HSIG with S = 16
+segments and M = 16; a batch of 10,000 queries from the same mixture with range
+fractions 0.1 / 1 / 10 / 50 / 100 % (2,000 each), k = 10, range-aware routing.
+
+One step = one search of the whole batch through the C ABI (route, pre-filter
+scan + merge, hybrid search, post-filter search, result writing). The metric is
+queries per second at recall@10 >= 0.95 in every range-fraction group; the beam
+widths are picked by the autotuner against the exact answers before timing.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank holds a replica of the index and searches its
+own batch (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QPS at recall@10>=0.95 by range fraction; FP32 vs BF16/FP8 path; % HBM peak"
+UNIT = "queries/s"
+WORKLOAD = "c2: n=1,000,000 d=128 int-valued mixture, 10,000 queries, ranges 0.1/1/10/50/100%, k=10, auto-routed"
+FALLBACK_HBM_GBS = 6800.0
+
+# ncu DRAM traffic per launch of the dominant kernel, keyed by the digest of the
+# kernel source it was taken on (stale digests are ignored, so the value is null
+# again once the kernel changes).
+NCU_TRAFFIC = {}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def src_digest(*names):
+    h = hashlib.sha1()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2412_02448_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def cache_dir():
+    d = os.environ.get("UNIFY_CACHE_DIR", os.path.join(ROOT, "_cache"))
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def get_index(w, rank, world, barrier):
+    import hsig_build
+    path = os.path.join(cache_dir(), f"{w.name}_n{w.n}_s{w.seed}_{hsig_build.source_digest()}.idx")
+    if rank == 0 and not os.path.exists(path):
+        t = time.time()
+        hsig_build.build_index(w.vectors, w.attrs, path, w.S, w.M, w.efc, seed=w.seed)
+        log(f"built index {path} in {time.time() - t:.1f} s")
+    barrier()
+    return path
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(cache_dir(), f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(path, w, params, k, budget_s, per_fraction):
+    """The oracle's literal HSIG search on the host cores, on a stratified sample."""
+    import oracle
+    oi = oracle.OracleIndex(path)
+    cores = oracle.default_threads()
+    fr = np.unique(w.fractions)
+    idx = np.concatenate([np.flatnonzero(w.fractions == f)[:per_fraction] for f in fr])
+    kw = dict(ef=params.ef, m=params.m, ef_post=params.ef_post, strategy="auto",
+              tau_a=params.tau_a, tau_b=params.tau_b, threads=cores)
+    t = time.perf_counter()
+    oi.search(w.queries[idx], w.lo[idx], w.hi[idx], k, **kw)
+    dt = time.perf_counter() - t
+    # grow the sample towards the time budget
+    if dt < budget_s / 4 and per_fraction * len(fr) < len(w.lo):
+        scale = min(len(w.lo) // len(fr), int(per_fraction * budget_s / max(dt, 1e-3) / 2))
+        idx = np.concatenate([np.flatnonzero(w.fractions == f)[:scale] for f in fr])
+        t = time.perf_counter()
+        oi.search(w.queries[idx], w.lo[idx], w.hi[idx], k, **kw)
+        dt = time.perf_counter() - t
+    oi.close()
+    return {"value": len(idx) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(idx)} queries stratified over the range fractions of the same batch "
+                      f"(literal HSIG search, FP64, same ef/m/tau), {dt:.1f} s"}
+
+
+def reference_arm(args, rank, world):
+    """The oracle (the CPU reference of this build) timed on the host cores."""
+    from workloads import make_workload
+    import oracle
+    if rank != 0:
+        return
+    w = make_workload("c2", seed=args.seed)
+    path = get_index(w, 0, 1, lambda: None)
+    import paper_2412_02448_gb300 as U  # parameters only; no GPU work on this arm
+    params = U.Params.defaults(ef=args.ef, ef_post=args.ef_post or args.ef, tau_a=w.n // 100, tau_b=w.n // 2)
+    oi = oracle.OracleIndex(path)
+    cores = oracle.default_threads()
+    fr = np.unique(w.fractions)
+    # calibrate the per-query time, then size every step to fit the run in ~2 minutes
+    cal = np.concatenate([np.flatnonzero(w.fractions == f)[:4] for f in fr])
+    kw = dict(ef=params.ef, m=params.m, ef_post=params.ef_post, strategy="auto",
+              tau_a=params.tau_a, tau_b=params.tau_b, threads=cores)
+    t = time.perf_counter()
+    oi.search(w.queries[cal], w.lo[cal], w.hi[cal], 10, **kw)
+    tq = (time.perf_counter() - t) / len(cal)
+    per_step = int(np.clip(120.0 / (args.steps + args.warmup) / max(tq, 1e-6), len(fr), 2000))
+    per_f = max(1, per_step // len(fr))
+    rng = np.random.default_rng(args.seed)
+    steps_t = []
+    for s in range(args.warmup + args.steps):
+        idx = np.concatenate([rng.choice(np.flatnonzero(w.fractions == f), per_f, replace=False) for f in fr])
+        t = time.perf_counter()
+        oi.search(w.queries[idx], w.lo[idx], w.hi[idx], 10, **kw)
+        if s >= args.warmup:
+            steps_t.append((time.perf_counter() - t, len(idx)))
+    tot = sum(x for x, _ in steps_t)
+    nqs = sum(n for _, n in steps_t)
+    value = nqs / tot
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * tot / len(steps_t), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "queries_per_step": per_f * len(fr)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_f * len(fr)} queries per step, stratified over the fractions"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--target", type=float, default=0.95)
+    ap.add_argument("--ef", type=int, default=100, help="reference arm / no-tune beam width")
+    ap.add_argument("--ef-post", type=int, default=0)
+    ap.add_argument("--m", type=int, default=16)
+    ap.add_argument("--cand-cap", type=int, default=512)
+    ap.add_argument("--visited-cap", type=int, default=2048)
+    ap.add_argument("--warps-per-block", type=int, default=4)
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--n", type=int, default=0, help="smaller base set (profiling captures only)")
+    ap.add_argument("--nq", type=int, default=0, help="smaller batch (profiling captures only)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier()
+    import paper_2412_02448_gb300 as U
+    from paper_2412_02448_gb300 import autotune
+    from workloads import make_workload
+
+    over = {}
+    if args.n:
+        over["n"] = args.n
+    if args.nq:
+        over["nq"] = args.nq
+    w0 = make_workload("c2", seed=args.seed, **over)
+    path = get_index(w0, rank, world, barrier)
+    # weak scaling: every rank searches its own batch of the same shape
+    if rank == 0:
+        w = w0
+    else:
+        w = make_workload("c2", seed=args.seed, **over)
+        rng = np.random.default_rng([args.seed, 100 + rank])
+        perm = rng.permutation(len(w.lo))
+        w.queries, w.lo, w.hi, w.fractions = w.queries[perm], w.lo[perm], w.hi[perm], w.fractions[perm]
+    ix = U.Index(path, device=local)
+    dev = torch.device("cuda", local)
+    q = torch.from_numpy(w.queries).to(dev)
+    lo = torch.from_numpy(w.lo).to(dev)
+    hi = torch.from_numpy(w.hi).to(dev)
+    k = w.k
+    nq = len(w.lo)
+    tau_a, tau_b = w.n // 100, w.n // 2
+
+    # exact answers: Strategy A on every query (exact; bit-identical to the FP64
+    # oracle on this integer-valued workload)
+    truth = ix.search(q, lo, hi, k, strategy="pre")
+    torch.cuda.synchronize()
+    t_ids, t_cnt = truth["ids"].cpu().numpy(), truth["count"].cpu().numpy()
+
+    base = U.Params.defaults(tau_a=tau_a, tau_b=tau_b, ef=args.ef, ef_post=args.ef_post or args.ef, m=args.m,
+                             cand_cap=args.cand_cap, visited_cap=args.visited_cap,
+                             warps_per_block=args.warps_per_block)
+    if args.no_tune:
+        params, report = base, {}
+    else:
+        params, report = autotune.tune(ix, q, lo, hi, k, t_ids, t_cnt, w.fractions, target=args.target,
+                                       base=base, log=log if rank == 0 else None)
+    out = ix.search(q, lo, hi, k, strategy="auto", params=params, counters=True)
+    torch.cuda.synchronize()
+    rec = autotune.recall_rows(out["ids"].cpu().numpy(), t_ids, t_cnt, k)
+    per_frac = autotune.group_recall(rec, w.fractions)
+    counters = out["counters"].cpu().numpy().astype(np.int64)
+    status = out["status"].cpu().numpy()
+    route = ix.route(lo, hi, tau_a, tau_b)
+    strat = route["strategy"].cpu().numpy()
+    pa, pb = route["pa"].cpu().numpy().astype(np.int64), route["pb"].cpu().numpy().astype(np.int64)
+    mask = route["mask"].cpu().numpy().astype(np.uint32)
+
+    # timed region: W warm-up steps, then K steps; L2 flushed (256 MiB write)
+    # between steps, outside the per-step events.
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    clocks = Clocks(local)
+    clocks.start()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        out = ix.search(q, lo, hi, k, strategy="auto", params=params, out=out)
+    ix.collect_timing()
+    ix.timing(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        evs[s][0].record(stream)
+        out = ix.search(q, lo, hi, k, strategy="auto", params=params, out=out)
+        evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    ix.timing(False)
+    phases = ix.collect_timing()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = float(np.mean(step_ms))
+    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * nq / (ms_max / 1000.0)
+
+    # end to end through the host-buffer entry point (pinned memory)
+    hq = torch.from_numpy(w.queries).pin_memory()
+    hlo = torch.from_numpy(w.lo).pin_memory()
+    hhi = torch.from_numpy(w.hi).pin_memory()
+    hout = dict(ids=torch.empty((nq, k), dtype=torch.int64).pin_memory(),
+                dist=torch.empty((nq, k), dtype=torch.float32).pin_memory(),
+                count=torch.empty(nq, dtype=torch.int32).pin_memory(),
+                status=torch.empty(nq, dtype=torch.int32).pin_memory())
+    for _ in range(max(3, args.warmup // 2)):
+        ix.search_auto_host(hq, hlo, hhi, k, params=params, out=hout)
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ix.search_auto_host(hq, hlo, hhi, k, params=params, out=hout)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    t_e2e = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_value = world * nq / float(t_e2e.item())
+    h2d = nq * w.d * 4 + 2 * nq * 8
+    d2h = nq * k * (8 + 4) + nq * 4 + nq * 4
+
+    # roofline of the dominant phase (algorithmic bytes per launch / event time)
+    hbm, peak_kind = peaks()
+    d = w.d
+    per_phase_ms = {ph: (v[0] / v[1] if v[1] else 0.0) for ph, v in phases.items()}
+    Sp = np.array([bin(int(m_)).count("1") for m_ in mask])
+    per = np.minimum(ix.M, -(-params.m // np.maximum(Sp, 1)))
+    isA, isC, isB = strat == 0, strat == 1, strat == 2
+    bytes_phase = {
+        # scan: every in-range row once (vector + its id)
+        "scan": float(((pb - pa) * (d * 4 + 4))[isA].sum()),
+        # graph: gathered vectors + the adjacency slots read per expansion
+        "hybrid": float((counters[isC, 0] * d * 4 + counters[isC, 1] * Sp[isC] * per[isC] * 4).sum()),
+        "post": float((counters[isB, 0] * d * 4 + counters[isB, 1] * (ix.M + (ix.S * ix.M + 31) // 32) * 4).sum()),
+    }
+    dom = max(("scan", "hybrid", "post"), key=lambda p_: per_phase_ms[p_])
+    achieved = bytes_phase[dom] / (per_phase_ms[dom] / 1000.0) / 1e9 if per_phase_ms[dom] > 0 else 0.0
+    digest = src_digest("graph.cu", "common.cuh") if dom != "scan" else src_digest("scan.cu", "common.cuh")
+    traffic = NCU_TRAFFIC.get((dom, digest))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "kernel": dom, "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": bytes_phase[dom]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(path, w, params, k, args.cpu_budget, per_fraction=20)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": w.n, "d": w.d, "queries_per_step": nq, "k": k,
+                       "S": w.S, "M": w.M, "efc": w.efc, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MiB write), inputs 1.6 GB > L2",
+                       "params": {"ef": params.ef, "ef_post": params.ef_post, "m": params.m,
+                                  "cand_cap": params.cand_cap, "visited_cap": params.visited_cap,
+                                  "warps_per_block": params.warps_per_block, "tau_a": tau_a, "tau_b": tau_b}},
+            "recall_by_fraction": {f"{100 * f_:g}%": round(r_, 4) for f_, r_ in per_frac.items()},
+            "routed": {"pre": int(isA.sum()), "hybrid": int(isC.sum()), "post": int(isB.sum())},
+            "status_flagged": int(((status & 3) != 0).sum()),
+            "phase_ms_per_step": {ph: round(v, 4) for ph, v in per_phase_ms.items()},
+            "wall_s_timed_region": wall,
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 5 * args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        if report:
+            line["tune"] = {"chosen_ms": report.get("ms"), "trials": len(report.get("trials", []))}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

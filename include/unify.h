@@ -153,6 +153,17 @@ UNIFY_API int unify_search_auto_host(unify_index_t* idx, const float* q, const i
                            int64_t nq, int k, int ef, const unify_params_t* p, int64_t* out_ids,
                            float* out_dist, int32_t* out_count, uint32_t* out_status, void* stream);
 
+/* Per-phase timing of searches with CUDA events recorded on the search stream.
+ * While enabled, every search records one event pair around each phase it runs:
+ * 0 = route (range bounds, masks, queues), 1 = pre-filter scan and merge,
+ * 2 = hybrid search, 3 = post-filter search. */
+UNIFY_API int unify_timing_enable(unify_index_t* idx, int enable);
+
+/* Waits for the recorded events, writes per phase the summed milliseconds
+ * (total_ms[4]) and the number of recorded spans (spans[4]), and clears the
+ * records. Either output may be NULL. */
+UNIFY_API int unify_timing_collect(unify_index_t* idx, double* total_ms, int64_t* spans);
+
 /* Message of the last failed call on this thread ("" when none). */
 UNIFY_API const char* unify_last_error(void);
 

@@ -82,6 +82,10 @@ def lib():
             L.unify_search_auto_host.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int,
                                                  ctypes.c_int, _P, _P, _P, _P, _P, _P]
             L.unify_search_auto_host.restype = ctypes.c_int
+            L.unify_timing_enable.argtypes = [_P, ctypes.c_int]
+            L.unify_timing_enable.restype = ctypes.c_int
+            L.unify_timing_collect.argtypes = [_P, _P, _P]
+            L.unify_timing_collect.restype = ctypes.c_int
             L.unify_last_error.argtypes = []
             L.unify_last_error.restype = ctypes.c_char_p
             _lib = L
@@ -166,6 +170,18 @@ class Index:
                                   _ptr(out.get("counters")), _stream_handle(torch, self.device)),
                "unify_search")
         return out
+
+    PHASES = ("route", "scan", "hybrid", "post")
+
+    def timing(self, enable: bool = True):
+        _check(lib().unify_timing_enable(self._h, 1 if enable else 0), "unify_timing_enable")
+
+    def collect_timing(self) -> dict:
+        """{phase: (summed milliseconds, spans)} of the searches since the last collect."""
+        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_int64 * 4)()
+        _check(lib().unify_timing_collect(self._h, ms, cnt), "unify_timing_collect")
+        return {ph: (ms[i], cnt[i]) for i, ph in enumerate(self.PHASES)}
 
     def search_auto(self, q, lo, hi, k: int, ef: int = 0, params: Params | None = None, out=None):
         return self.search(q, lo, hi, k, ef=ef, strategy=AUTO, params=params, out=out)

@@ -1,0 +1,125 @@
+"""Autotuner: picks the search parameters that give the highest throughput while
+every range-fraction group keeps recall@k at or above a target.
+
+Recall follows Eq. 1 of the paper: |found ∩ exact| / min(k, |R|). The exact
+answers come from the caller (for instance the exact pre-filter strategy run on
+every query). Beam widths are tuned per strategy, because the hybrid (C) and
+post-filter (B) queries of a batch are disjoint: C is tuned on the C-routed
+queries of each group, B on the B-routed ones; pre-filtered queries (A) are exact.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def recall_rows(ids: np.ndarray, truth_ids: np.ndarray, truth_count: np.ndarray, k: int) -> np.ndarray:
+    """Per-query recall (Eq. 1); a query whose range holds nothing scores 1."""
+    ids = np.asarray(ids)[:, :k]
+    truth = np.asarray(truth_ids)[:, :k]
+    c = np.minimum(k, np.asarray(truth_count))
+    valid_t = np.arange(k)[None, :] < c[:, None]
+    t = np.where(valid_t, truth, -2)
+    hit = (ids[:, :, None] == t[:, None, :]) & (ids[:, :, None] >= 0)
+    got = hit.any(axis=2).sum(axis=1)
+    return np.where(c > 0, got / np.maximum(c, 1), 1.0)
+
+
+def group_recall(rec: np.ndarray, groups: np.ndarray, sel: np.ndarray | None = None) -> dict:
+    out = {}
+    for g in np.unique(groups):
+        m = groups == g
+        if sel is not None:
+            m = m & sel
+        if m.any():
+            out[float(g)] = float(rec[m].mean())
+    return out
+
+
+def _time_search(index, q, lo, hi, k, params, reps, torch, strategy="auto"):
+    out = None
+    for _ in range(2):
+        out = index.search(q, lo, hi, k, strategy=strategy, params=params, out=out)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(reps):
+        out = index.search(q, lo, hi, k, strategy=strategy, params=params, out=out)
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps, out
+
+
+def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=None,
+         efs=(16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512), ms_=(16, 24, 32, 48, 64), reps=3, log=None):
+    """Returns (Params, report). q/lo/hi are device tensors; truth_* and groups numpy.
+
+    Hybrid (C): for every selection width m (Section 4.2, the paper's m), the
+    smallest ef meeting the target on the C-routed queries of every group; the
+    fastest (m, ef) pair wins. Post-filter (B): the smallest ef_post meeting the
+    target on the B-routed queries. Then the CTA shape and buffer sizes."""
+    import torch
+
+    import paper_2412_02448_gb300 as U
+
+    base = base or U.Params.defaults()
+    strat = index.route(lo, hi, base.tau_a, base.tau_b)["strategy"].cpu().numpy()
+    report = {"trials": []}
+
+    def run(extra):
+        p = U.Params.defaults(**{f: getattr(base, f) for f, _ in U.Params._fields_})
+        for kk, v in extra.items():
+            setattr(p, kk, v)
+        if max(p.ef, p.ef_post) > p.cand_cap // 2:
+            p.cand_cap = min(4096, 2 * max(p.ef, p.ef_post))
+        ms, out = _time_search(index, q, lo, hi, k, p, reps, torch)
+        ids = out["ids"].cpu().numpy()
+        return p, ms, recall_rows(ids, truth_ids, truth_count, k)
+
+    def smallest_ef(sel, fixed, field):
+        for ef in efs:
+            if ef < k:
+                continue
+            p, ms, rec = run(dict(fixed, **{field: ef}))
+            gr = group_recall(rec, groups, sel)
+            report["trials"].append({"params": dict(fixed, **{field: ef}), "ms": ms, "recall": gr})
+            if log:
+                log(f"tune {dict(fixed, **{field: ef})}: {ms:.3f} ms/batch, recall {gr}")
+            if min(gr.values()) >= target:
+                return ef, ms
+        return None, None
+
+    chosen = {"ef": efs[0], "ef_post": efs[0], "m": base.m}
+    selB, selC = strat == U.POST, strat == U.HYBRID
+    if selB.any():
+        ef, _ = smallest_ef(selB, {"ef": efs[0]}, "ef_post")
+        chosen["ef_post"] = ef if ef is not None else efs[-1]
+    if selC.any():
+        best_c = None
+        for m in ms_:
+            ef, ms = smallest_ef(selC, {"m": m, "ef_post": chosen["ef_post"]}, "ef")
+            if ef is not None and (best_c is None or ms < best_c[2]):
+                best_c = (m, ef, ms)
+        if best_c is None:
+            best_c = (ms_[-1], efs[-1], None)
+        chosen["m"], chosen["ef"] = best_c[0], best_c[1]
+    best = None
+    for extra in ({"warps_per_block": 4}, {"warps_per_block": 2}, {"warps_per_block": 8},
+                  {"warps_per_block": 4, "cand_cap": 256}, {"warps_per_block": 4, "cand_cap": 1024},
+                  {"warps_per_block": 4, "visited_cap": 1024}, {"warps_per_block": 4, "visited_cap": 4096}):
+        try:
+            p, ms, rec = run(dict(chosen, **extra))
+        except U.UnifyError:
+            continue
+        gr = group_recall(rec, groups)
+        report["trials"].append({"params": dict(chosen, **extra), "ms": ms, "recall": gr})
+        if log:
+            log(f"tune shape {dict(chosen, **extra)}: {ms:.3f} ms/batch, recall {gr}")
+        if min(gr.values()) >= target and (best is None or ms < best[1]):
+            best = (p, ms, gr)
+    if best is None:
+        p, ms, rec = run(chosen)
+        best = (p, ms, group_recall(rec, groups))
+    report["chosen"] = {f: getattr(best[0], f) for f, _ in U.Params._fields_}
+    report["ms"] = best[1]
+    report["recall"] = best[2]
+    return best[0], report

@@ -149,6 +149,38 @@ int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Para
   return UNIFY_OK;
 }
 
+cudaEvent_t take_event(Timing& t) {
+  if (!t.pool.empty()) {
+    cudaEvent_t e = t.pool.back();
+    t.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records an event pair around one phase when timing is on.
+struct PhaseTimer {
+  Timing& t;
+  int phase;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  PhaseTimer(Timing& t_, int ph, cudaStream_t s) : t(t_), phase(ph), st(s) {
+    if (t.on) {
+      a = take_event(t);
+      cudaEventRecord(a, st);
+    }
+  }
+  ~PhaseTimer() {
+    if (t.on && a) {
+      cudaEvent_t b = take_event(t);
+      cudaEventRecord(b, st);
+      t.rec[phase].push_back({a, b});
+    }
+  }
+};
+
 int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi, int64_t nq, int k,
                int ef, int strategy, const unify_params_t* up, int64_t* out_ids, float* out_dist,
                int32_t* out_count, uint32_t* out_status, int32_t* out_counters, cudaStream_t st) {
@@ -167,18 +199,24 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
   e = cudaMemsetAsync(sc.counters, 0, kNumCounters * sizeof(int32_t), st);
   if (e != cudaSuccess) return cuda_fail(e, "counter reset");
   Outputs o{out_ids, out_dist, out_count, out_status, out_counters};
-  e = launch_route(idx->ix, sc, lo, hi, nq, p.tau_a, p.tau_b, strategy, p.scan_rows, 1, sc.pa, sc.pb, sc.mask,
-                   sc.strat, &o, st);
+  {
+    PhaseTimer t(idx->tm, 0, st);
+    e = launch_route(idx->ix, sc, lo, hi, nq, p.tau_a, p.tau_b, strategy, p.scan_rows, 1, sc.pa, sc.pb, sc.mask,
+                     sc.strat, &o, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "route kernel");
   if (strategy == UNIFY_PRE || strategy == UNIFY_AUTO) {
+    PhaseTimer t(idx->tm, 1, st);
     e = launch_scan(idx->ix, sc, q, nq, p, o, st);
     if (e != cudaSuccess) return cuda_fail(e, "pre-filter scan");
   }
   if (strategy == UNIFY_HYBRID || strategy == UNIFY_AUTO) {
+    PhaseTimer t(idx->tm, 2, st);
     e = launch_graph(idx->ix, sc, q, nq, UNIFY_HYBRID, p, o, st);
     if (e != cudaSuccess) return cuda_fail(e, "hybrid search");
   }
   if (strategy == UNIFY_POST || strategy == UNIFY_AUTO) {
+    PhaseTimer t(idx->tm, 3, st);
     e = launch_graph(idx->ix, sc, q, nq, UNIFY_POST, p, o, st);
     if (e != cudaSuccess) return cuda_fail(e, "post-filter search");
   }
@@ -216,6 +254,35 @@ extern "C" void unify_default_params(unify_params_t* p) {
 }
 
 extern "C" const char* unify_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int unify_timing_enable(unify_index_t* idx, int enable) {
+  if (!idx) return fail(UNIFY_E_ARG, "unify_timing_enable: null index");
+  idx->tm.on = enable != 0;
+  return UNIFY_OK;
+}
+
+extern "C" int unify_timing_collect(unify_index_t* idx, double* total_ms, int64_t* spans) {
+  if (!idx) return fail(UNIFY_E_ARG, "unify_timing_collect: null index");
+  DeviceGuard guard(idx->ix.device);
+  for (int ph = 0; ph < kPhases; ++ph) {
+    double sum = 0.0;
+    int64_t cnt = 0;
+    for (auto& pr : idx->tm.rec[ph]) {
+      cudaError_t e = cudaEventSynchronize(pr.second);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+      if (e != cudaSuccess) return cuda_fail(e, "unify_timing_collect");
+      sum += ms;
+      ++cnt;
+      idx->tm.pool.push_back(pr.first);
+      idx->tm.pool.push_back(pr.second);
+    }
+    idx->tm.rec[ph].clear();
+    if (total_ms) total_ms[ph] = sum;
+    if (spans) spans[ph] = cnt;
+  }
+  return UNIFY_OK;
+}
 
 extern "C" int unify_route(unify_index_t* idx, const int64_t* lo, const int64_t* hi, int64_t nq, int64_t tau_a,
                            int64_t tau_b, int32_t* out_pa, int32_t* out_pb, uint32_t* out_mask,

@@ -303,6 +303,12 @@ extern "C" void unify_free_index(unify_index_t* idx) {
     DeviceGuard guard(idx->ix.device);
     free_device(idx->ix);
     free_scratch(idx->sc);
+    for (int ph = 0; ph < kPhases; ++ph)
+      for (auto& pr : idx->tm.rec[ph]) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+      }
+    for (cudaEvent_t e : idx->tm.pool) cudaEventDestroy(e);
   }
   delete idx;
 }

@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/unify.h"
 
@@ -118,7 +120,18 @@ struct DeviceGuard {
 
 }  // namespace unify
 
+namespace unify {
+// Optional per-phase CUDA-event timing of searches (route, scan, hybrid, post).
+constexpr int kPhases = 4;
+struct Timing {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rec[kPhases];
+};
+}  // namespace unify
+
 struct unify_index {
   unify::DeviceIndex ix;
   unify::Scratch sc;
+  unify::Timing tm;
 };
