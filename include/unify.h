@@ -153,6 +153,25 @@ UNIFY_API int unify_search_auto_host(unify_index_t* idx, const float* q, const i
                            int64_t nq, int k, int ef, const unify_params_t* p, int64_t* out_ids,
                            float* out_dist, int32_t* out_count, uint32_t* out_status, void* stream);
 
+/* unify_search without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc while searching
+ * (a fixed device-memory budget, a latency-critical loop that cannot take
+ * cudaMalloc's implicit device-wide synchronisation or its failure, a host that
+ * must not allocate once running). Arguments are those of unify_search minus
+ * out_counters; inputs and outputs are still the caller's device buffers.
+ * Scratch comes from one fixed device array of about 8.6 MiB compiled into the
+ * library, present on every GPU that loads it until the process exits. Limits:
+ * nq <= 1024 and k <= 16 per call; larger sizes return UNIFY_E_LIMIT without
+ * running. The first call on a device looks up the array's device address (keep
+ * that first call outside any stream capture). All calls share the array and it
+ * keeps the last call's contents; each call clears its work counters on `stream`
+ * first. Calls whose GPU work overlaps (different streams or threads, or another
+ * index on the same device) race on the array and must be serialised. */
+UNIFY_API int unify_search_noalloc(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,
+                                   int64_t nq, int k, int ef, unify_strategy_t strategy,
+                                   const unify_params_t* p, int64_t* out_ids, float* out_dist,
+                                   int32_t* out_count, uint32_t* out_status, void* stream);
+
 /* Per-phase timing of searches with CUDA events recorded on the search stream.
  * While enabled, every search records one event pair around each phase it runs:
  * 0 = route (range bounds, masks, queues), 1 = pre-filter scan and merge,

@@ -227,6 +227,10 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+int resolve_search_params(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Params& p) {
+  return resolve(ix, up, k, ef, p);
+}
+
 void free_scratch(Scratch& sc) {
   free_core(sc);
   free_stage(sc);

@@ -104,6 +104,7 @@ cudaError_t launch_graph(const DeviceIndex& ix, const Scratch& sc, const float* 
 cudaError_t derive_sorted(DeviceIndex& ix, cudaStream_t st);
 
 void set_error(const std::string& msg);
+int resolve_search_params(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Params& p);
 void free_scratch(Scratch& sc);
 
 // Makes `dev` current for the lifetime of the guard.
