@@ -156,42 +156,63 @@ struct Builder {
     top_seg.assign(S, -1);
   }
 
+  void prefetch_vec(int32_t v) const {
+    const char* p = reinterpret_cast<const char*>(vec(v));
+    for (int b = 0; b < d * 4; b += 64) __builtin_prefetch(p + b);
+  }
+
   // ---- Algorithm 1 on the sub-graph of segment j at layer l ----
+  // cand_buf / ann_buf are reusable heap storage (min-heap and max-heap).
   void ann_search(const float* q, int32_t ep, int l, int j, int ef, Visited& vis,
-                  std::vector<Key>& out) const {
-    std::priority_queue<Key, std::vector<Key>, std::greater<Key>> cand;
-    std::priority_queue<Key> ann;
+                  std::vector<Key>& out, std::vector<Key>& cand_buf, std::vector<Key>& ann_buf) const {
+    std::vector<Key>& cand = cand_buf;
+    std::vector<Key>& ann = ann_buf;
+    cand.clear();
+    ann.clear();
+    auto cand_push = [&](Key k) { cand.push_back(k); std::push_heap(cand.begin(), cand.end(), std::greater<Key>()); };
+    auto ann_push = [&](Key k) { ann.push_back(k); std::push_heap(ann.begin(), ann.end()); };
     Key e{l2sq(q, vec(ep), d), ep};
-    cand.push(e);
-    ann.push(e);
+    cand_push(e);
+    ann_push(e);
     vis.test_set(ep);
+    int32_t fresh[256];
     while (!cand.empty()) {
-      Key o = cand.top();
-      cand.pop();
-      if (o > ann.top()) break;
+      std::pop_heap(cand.begin(), cand.end(), std::greater<Key>());
+      Key o = cand.back();
+      cand.pop_back();
+      if (o > ann.front()) break;
       int64_t r = row0[o.second] + l;
       const int32_t* ch = adj.data() + (r * S + j) * (int64_t)M;
       int c = cnt[r * S + j];
+      int nf = 0;
       for (int s = 0; s < c; ++s) {
         int32_t v = ch[s];
         if (vis.test_set(v)) continue;
+        fresh[nf++] = v;
+        prefetch_vec(v);
+      }
+      for (int t = 0; t < nf; ++t) {
+        int32_t v = fresh[t];
         Key kv{l2sq(q, vec(v), d), v};
-        if ((int)ann.size() < ef || kv < ann.top()) {
-          cand.push(kv);
-          ann.push(kv);
-          if ((int)ann.size() > ef) ann.pop();
+        if ((int)ann.size() < ef || kv < ann.front()) {
+          cand_push(kv);
+          ann_push(kv);
+          if ((int)ann.size() > ef) {
+            std::pop_heap(ann.begin(), ann.end());
+            ann.pop_back();
+          }
         }
       }
     }
-    out.clear();
-    while (!ann.empty()) { out.push_back(ann.top()); ann.pop(); }
-    std::reverse(out.begin(), out.end());
+    out.assign(ann.begin(), ann.end());
+    std::sort(out.begin(), out.end());
   }
 
   // ---- Prune heuristic (Section 2.2) ----
   // cands: (distance to owner, id); returns at most M survivors in ascending order.
   void prune(std::vector<Key>& cands, int Mmax, std::vector<Key>& kept) const {
     std::sort(cands.begin(), cands.end());
+    for (size_t t = 0; t < cands.size() && t < 64; ++t) prefetch_vec(cands[t].second);
     kept.clear();
     for (const Key& r : cands) {
       if ((int)kept.size() >= Mmax) break;
@@ -210,6 +231,7 @@ struct Builder {
   // Searches of Algorithm 6 for node v against the current (read-only) graph.
   void propose(int32_t v, Visited& vis, Proposal& P, std::vector<Key>& ann,
                std::vector<Key>& tmp) const {
+    thread_local std::vector<Key> cand_buf, ann_buf;
     const float* q = vec(v);
     int lv = level[v];
     P.fwd.assign((size_t)(lv + 1) * S, {});
@@ -219,12 +241,12 @@ struct Builder {
       int L = top_seg[j];
       for (int l = L; l > lv; --l) {
         vis.reset(n);
-        ann_search(q, ep, l, j, 1, vis, ann);
+        ann_search(q, ep, l, j, 1, vis, ann, cand_buf, ann_buf);
         ep = ann[0].second;
       }
       for (int l = std::min(lv, L); l >= 0; --l) {
         vis.reset(n);
-        ann_search(q, ep, l, j, efc, vis, ann);
+        ann_search(q, ep, l, j, efc, vis, ann, cand_buf, ann_buf);
         tmp = ann;
         prune(tmp, M, P.fwd[(size_t)l * S + j]);
         ep = ann[0].second;

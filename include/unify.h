@@ -174,8 +174,8 @@ UNIFY_API int unify_search_noalloc(unify_index_t* idx, const float* q, const int
 
 /* Per-phase timing of searches with CUDA events recorded on the search stream.
  * While enabled, every search records one event pair around each phase it runs:
- * 0 = route (range bounds, masks, queues), 1 = pre-filter scan and merge,
- * 2 = hybrid search, 3 = post-filter search. */
+ * 0 = route (range bounds, masks, work queues), 1 = the search kernel (hybrid,
+ * post-filter and pre-filter work of the batch); 2 and 3 are reserved (zero). */
 UNIFY_API int unify_timing_enable(unify_index_t* idx, int enable);
 
 /* Waits for the recorded events, writes per phase the summed milliseconds

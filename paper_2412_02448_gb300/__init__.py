@@ -171,7 +171,7 @@ class Index:
                "unify_search")
         return out
 
-    PHASES = ("route", "scan", "hybrid", "post")
+    PHASES = ("route", "search", "unused2", "unused3")
 
     def timing(self, enable: bool = True):
         _check(lib().unify_timing_enable(self._h, 1 if enable else 0), "unify_timing_enable")

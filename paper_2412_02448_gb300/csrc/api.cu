@@ -34,6 +34,7 @@ void free_core(Scratch& sc) {
   release(sc.strat);
   release(sc.nblk);
   release(sc.qbase);
+  release(sc.done);
   release(sc.queues);
   release(sc.items);
   release(sc.part);
@@ -74,6 +75,7 @@ cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k) {
   if (e == cudaSuccess) e = alloc(sc.strat, cap);
   if (e == cudaSuccess) e = alloc(sc.nblk, cap);
   if (e == cudaSuccess) e = alloc(sc.qbase, cap);
+  if (e == cudaSuccess) e = alloc(sc.done, cap);
   if (e == cudaSuccess) e = alloc(sc.queues, 3 * cap);
   if (e == cudaSuccess) e = alloc(sc.items, cap * kMaxScanBlocks);
   if (e == cudaSuccess) e = alloc(sc.part, (size_t)cap * kMaxScanBlocks * kc);
@@ -109,13 +111,6 @@ cudaError_t ensure_stage(Scratch& sc, int64_t nq, int k, int d) {
   return cudaSuccess;
 }
 
-int graph_warp_bytes(int cand_cap, int ann_cap, int vis_log2) {
-  int b = cand_cap * 8 + ann_cap * 8 + (4 << vis_log2);
-  b += (cand_cap + 15) & ~15;
-  b += 32 * 4 + 32 * 4 + 64 * 4;
-  return (b + 15) & ~15;
-}
-
 int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Params& p) {
   unify_params_t d;
   unify_default_params(&d);
@@ -143,8 +138,7 @@ int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Para
   if (p.warps_per_block < 1 || p.warps_per_block > 8) return fail(UNIFY_E_ARG, "warps_per_block must be in [1, 8]");
   if (p.scan_rows < 32) return fail(UNIFY_E_ARG, "scan_rows must be >= 32");
   if (p.dtype != UNIFY_FP32) return fail(UNIFY_E_ARG, "dtype: only UNIFY_FP32 is available in this build");
-  const int annc = (p.ef > p.ef_post ? p.ef : p.ef_post) > k ? (p.ef > p.ef_post ? p.ef : p.ef_post) : k;
-  const long smem = (long)p.warps_per_block * graph_warp_bytes(p.cand_cap, annc, p.vis_log2);
+  const long smem = (long)p.warps_per_block * batch_smem_per_warp(p);
   if (smem > 227 * 1024) return fail(UNIFY_E_LIMIT, "graph search shared memory per CTA exceeds 227 KB; lower warps_per_block, cand_cap, visited_cap or ef");
   return UNIFY_OK;
 }
@@ -205,21 +199,11 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
                      sc.strat, &o, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "route kernel");
-  if (strategy == UNIFY_PRE || strategy == UNIFY_AUTO) {
+  {
     PhaseTimer t(idx->tm, 1, st);
-    e = launch_scan(idx->ix, sc, q, nq, p, o, st);
-    if (e != cudaSuccess) return cuda_fail(e, "pre-filter scan");
+    e = launch_batch(idx->ix, sc, q, p, o, st);
   }
-  if (strategy == UNIFY_HYBRID || strategy == UNIFY_AUTO) {
-    PhaseTimer t(idx->tm, 2, st);
-    e = launch_graph(idx->ix, sc, q, nq, UNIFY_HYBRID, p, o, st);
-    if (e != cudaSuccess) return cuda_fail(e, "hybrid search");
-  }
-  if (strategy == UNIFY_POST || strategy == UNIFY_AUTO) {
-    PhaseTimer t(idx->tm, 3, st);
-    e = launch_graph(idx->ix, sc, q, nq, UNIFY_POST, p, o, st);
-    if (e != cudaSuccess) return cuda_fail(e, "post-filter search");
-  }
+  if (e != cudaSuccess) return cuda_fail(e, "search kernel");
   return UNIFY_OK;
 }
 

@@ -52,6 +52,7 @@ struct Scratch {
   int32_t* strat = nullptr;
   int32_t* nblk = nullptr;     // scan work items of each pre-filter query
   int32_t* qbase = nullptr;    // index of its first work item
+  int32_t* done = nullptr;     // completed scan work items of each pre-filter query
   int32_t* queues = nullptr;   // 3 x cap_nq: query ids per strategy (A, C, B)
   int2* items = nullptr;       // cap_nq * kMaxScanBlocks scan work items (query, block)
   uint64_t* part = nullptr;    // cap_nq * kMaxScanBlocks * cap_k partial top-k keys
@@ -72,9 +73,7 @@ struct Scratch {
 enum {
   CNT_QA = 0, CNT_QC = 1, CNT_QB = 2,  // queue lengths
   CNT_ITEMS = 3,                       // scan work items
-  CNT_TAKE_ITEMS = 4,                  // scan work-queue head
-  CNT_TAKE_C = 5, CNT_TAKE_B = 6,      // graph work-queue heads
-  CNT_TAKE_MERGE = 7,
+  CNT_TAKE = 4,                        // head of the combined work queue
   kNumCounters = 16
 };
 
@@ -97,11 +96,9 @@ cudaError_t launch_route(const DeviceIndex& ix, const Scratch& sc, const int64_t
                          int64_t nq, int64_t tau_a, int64_t tau_b, int forced, int scan_rows,
                          int build_queues, int32_t* out_pa, int32_t* out_pb, uint32_t* out_mask,
                          int32_t* out_strat, const Outputs* outs, cudaStream_t st);
-cudaError_t launch_scan(const DeviceIndex& ix, const Scratch& sc, const float* q, int64_t nq,
-                        const Params& p, const Outputs& o, cudaStream_t st);
-cudaError_t launch_graph(const DeviceIndex& ix, const Scratch& sc, const float* q, int64_t nq,
-                         int strategy, const Params& p, const Outputs& o, cudaStream_t st);
-cudaError_t derive_sorted(DeviceIndex& ix, cudaStream_t st);
+cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
+                         const Outputs& o, cudaStream_t st);
+int batch_smem_per_warp(const Params& p);
 
 void set_error(const std::string& msg);
 int resolve_search_params(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Params& p);
@@ -123,7 +120,7 @@ struct DeviceGuard {
 
 namespace unify {
 // Optional per-phase CUDA-event timing of searches (route, scan, hybrid, post).
-constexpr int kPhases = 4;
+constexpr int kPhases = 4;  // 0 route, 1 search kernel, 2 and 3 unused
 struct Timing {
   bool on = false;
   std::vector<cudaEvent_t> pool;

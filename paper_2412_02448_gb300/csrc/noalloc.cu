@@ -35,7 +35,8 @@ constexpr size_t kOffMask = kOffPb + kI32;
 constexpr size_t kOffStrat = kOffMask + kI32;
 constexpr size_t kOffNblk = kOffStrat + kI32;
 constexpr size_t kOffQbase = kOffNblk + kI32;
-constexpr size_t kOffQueues = kOffQbase + kI32;
+constexpr size_t kOffDone = kOffQbase + kI32;
+constexpr size_t kOffQueues = kOffDone + kI32;
 constexpr size_t kOffItems = kOffQueues + al256(3 * kNoAllocMaxQueries * sizeof(int32_t));
 constexpr size_t kOffPart = kOffItems + al256(kNoAllocMaxQueries * kMaxScanBlocks * sizeof(int2));
 constexpr size_t kOffCounters =
@@ -115,6 +116,7 @@ extern "C" int unify_search_noalloc(unify_index_t* idx, const float* q, const in
   sc.strat = reinterpret_cast<int32_t*>(base + kOffStrat);
   sc.nblk = reinterpret_cast<int32_t*>(base + kOffNblk);
   sc.qbase = reinterpret_cast<int32_t*>(base + kOffQbase);
+  sc.done = reinterpret_cast<int32_t*>(base + kOffDone);
   sc.queues = reinterpret_cast<int32_t*>(base + kOffQueues);
   sc.items = reinterpret_cast<int2*>(base + kOffItems);
   sc.part = reinterpret_cast<uint64_t*>(base + kOffPart);
@@ -125,17 +127,7 @@ extern "C" int unify_search_noalloc(unify_index_t* idx, const float* q, const in
   e = launch_route(idx->ix, sc, lo, hi, nq, prm.tau_a, prm.tau_b, st_code, prm.scan_rows, 1, sc.pa, sc.pb,
                    sc.mask, sc.strat, &o, st);
   if (e != cudaSuccess) return cuda_fail(e, "route kernel");
-  if (st_code == UNIFY_PRE || st_code == UNIFY_AUTO) {
-    e = launch_scan(idx->ix, sc, q, nq, prm, o, st);
-    if (e != cudaSuccess) return cuda_fail(e, "pre-filter scan");
-  }
-  if (st_code == UNIFY_HYBRID || st_code == UNIFY_AUTO) {
-    e = launch_graph(idx->ix, sc, q, nq, UNIFY_HYBRID, prm, o, st);
-    if (e != cudaSuccess) return cuda_fail(e, "hybrid search");
-  }
-  if (st_code == UNIFY_POST || st_code == UNIFY_AUTO) {
-    e = launch_graph(idx->ix, sc, q, nq, UNIFY_POST, prm, o, st);
-    if (e != cudaSuccess) return cuda_fail(e, "post-filter search");
-  }
+  e = launch_batch(idx->ix, sc, q, prm, o, st);
+  if (e != cudaSuccess) return cuda_fail(e, "search kernel");
   return UNIFY_OK;
 }

@@ -46,6 +46,7 @@ struct RouteArgs {
   int32_t* strat;
   int32_t* nblk;
   int32_t* qbase;
+  int32_t* done;
   int32_t* queues;
   int64_t cap_nq;
   int2* items;
@@ -96,6 +97,7 @@ __global__ void route_kernel(RouteArgs a, const int64_t* __restrict__ seg_bounds
     int base = atomicAdd(&a.counters[CNT_ITEMS], (int)nb);
     a.nblk[i] = (int)nb;
     a.qbase[i] = base;
+    a.done[i] = 0;
     for (int t = 0; t < nb; ++t) a.items[base + t] = make_int2((int)i, t);
     if (a.out_counters) {
       a.out_counters[2 * i] = (int32_t)Y;
@@ -126,6 +128,7 @@ cudaError_t launch_route(const DeviceIndex& ix, const Scratch& sc, const int64_t
   a.strat = out_strat;
   a.nblk = sc.nblk;
   a.qbase = sc.qbase;
+  a.done = sc.done;
   a.queues = sc.queues;
   a.cap_nq = sc.cap_nq;
   a.items = sc.items;

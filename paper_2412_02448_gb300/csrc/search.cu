@@ -1,0 +1,580 @@
+// The search of one batch in one persistent kernel: hybrid filtering (Strategy
+// C), post-filtering (Strategy B) and pre-filtering (Strategy A) of Section 4.2.
+//
+// Work queue. The router appends every query to a queue per strategy and splits
+// each pre-filter query into scan items. One warp takes one work unit at a time
+// from a single device counter, in the order: hybrid queries, post-filter queries,
+// scan items. The long graph searches start first and the short scan items fill
+// the tail, so the batch has one tail instead of one per strategy. A pre-filter
+// query split into several items is merged by the warp that completes its last
+// item (release/acquire through a per-query counter).
+//
+// Graph search (Algorithm 2's scheme; Algorithm 1 for B over bitmap-marked
+// slots; Algorithm 7 for C over the first ceil(m/S') slots of each intersected
+// chunk). One warp per query. Per-warp shared memory holds
+//   E    the candidate buffer: every visited object that can still matter, sorted
+//        by key (distance, id), with an "expanded" flag; popping the nearest
+//        candidate is taking the first unexpanded entry;
+//   ann  the result heap of Algorithms 1/7 as a sorted array of capacity ef;
+//   vis  a direct-mapped visited filter (ids; a slot may be overwritten).
+// Equivalence with the heap formulation: once ann holds ef entries its worst key
+// w only decreases, and an object with key > w can neither enter cand or ann nor
+// be expanded (the loop stops first), so E keeps exactly the visited objects with
+// key <= w (all visited objects while ann is not full). An object the filter
+// forgot is re-checked against E and ann by key, which is exact because its
+// distance is recomputed bit-identically (fixed per-lane order and a fixed
+// reduction tree). The neighbours of one expansion are processed as one batch
+// against the ann of the start of the batch; objects the sequential loop would
+// have rejected after an earlier insertion of the same batch end above the final
+// w and are dropped from E, so the outcome is the same. The visible differences
+// are the capacity of E (UNIFY_Q_TRUNCATED) and the expansion bound
+// (UNIFY_Q_LIMIT). While an expansion is processed, the adjacency of the next
+// candidate is prefetched into L2.
+//
+// Scan (Strategy A): rows [pa, pb) of the attribute-ordered vectors; a warp
+// computes 32 rows per step with coalesced 16-byte loads issued in batches of
+// 64 registers and a transposed shuffle reduction that leaves row r's distance
+// in lane r; keys beating the current k-th are merged into a sorted top-k.
+//
+// Bounds (checked by reading, against the buffers the launch receives):
+// E[< cand_cap], ann[< ann_cap], vis[< 2^vis_log2], clist[< 32], slots[< 64];
+// ids come from validated adjacency (0 <= id < n); upper-layer rows exist for
+// every object reached on that layer (validated levels); scan rows lie in
+// [pa, pb) and loads clamp to the last valid row.
+#include "common.cuh"
+#include "internal.h"
+
+namespace unify {
+
+struct BatchArgs {
+  const float* vec;
+  const float* vec_sorted;
+  const int32_t* sorted_ids;
+  int dp4, d;
+  int S, M, W, max_level, entry_global;
+  const int32_t* adj0;
+  const uint32_t* gmask0;
+  const int32_t* adjU;
+  const uint32_t* gmaskU;
+  const int32_t* upper_base;
+  const int32_t* pos;
+  const int32_t* seg_start;
+  const float* q;
+  const int32_t* pa;
+  const int32_t* pb;
+  const uint32_t* mask;
+  const int32_t* queues;
+  int64_t cap_nq;
+  const int32_t* nblk;
+  const int32_t* qbase;
+  int32_t* done;
+  const int2* items;
+  uint64_t* part;
+  int32_t* counters;
+  int k, ef_h, ef_p, m, cand_cap, ann_cap, vis_log2, max_exp;
+  int warp_bytes;
+  Outputs o;
+};
+
+struct WarpMem {
+  uint64_t* E;
+  uint64_t* ann;
+  int32_t* vis;
+  uint8_t* Ef;
+  int* R;
+  int* clist;
+  int* slots;
+};
+
+__host__ __device__ inline int batch_warp_bytes(int cand_cap, int ann_cap, int vis_log2) {
+  int b = cand_cap * 8 + ann_cap * 8 + (4 << vis_log2);
+  b += (cand_cap + 15) & ~15;
+  b += 32 * 4 + 32 * 4 + 64 * 4;
+  return (b + 15) & ~15;
+}
+
+__device__ __forceinline__ WarpMem carve(unsigned char* base, const BatchArgs& a) {
+  WarpMem w;
+  w.E = reinterpret_cast<uint64_t*>(base);
+  w.ann = w.E + a.cand_cap;
+  w.vis = reinterpret_cast<int32_t*>(w.ann + a.ann_cap);
+  w.Ef = reinterpret_cast<uint8_t*>(w.vis + (1 << a.vis_log2));
+  w.R = reinterpret_cast<int*>(w.Ef + ((a.cand_cap + 15) & ~15));
+  w.clist = w.R + 32;
+  w.slots = w.clist + 32;
+  return w;
+}
+
+__device__ __forceinline__ uint32_t vis_hash(int id, int log2) {
+  return ((uint32_t)id * 0x9E3779B1u) >> (32 - log2);
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void write_row(const uint64_t* keys, int cnt, int k, int64_t qi, const Outputs& o) {
+  const int lane = lane_id();
+  for (int t = lane; t < k; t += 32) {
+    const bool v = t < cnt;
+    const uint64_t key = v ? keys[t] : kKeyMax;
+    o.ids[qi * k + t] = v ? (int64_t)key_id(key) : (int64_t)-1;
+    o.dist[qi * k + t] = v ? key_dist(key) : __int_as_float(0x7f800000);
+  }
+}
+
+// Distances of the candidates held by the lanes (cid >= 0), G at a time.
+template <int CH, int G>
+__device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, const float* vec, int dp4,
+                                            int* clist) {
+  const unsigned vm = __ballot_sync(kFull, cid >= 0);
+  const int nv = __popc(vm);
+  const int my = __popc(vm & lanemask_lt());
+  if (cid >= 0) clist[my] = cid;
+  __syncwarp();
+  constexpr int SH = (G == 8) ? 2 : (G == 16 ? 1 : 0);
+  float result = 0.f;
+  for (int g = 0; g * G < nv; ++g) {
+    float part[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int c = g * G + u;
+      part[u] = (c < nv) ? l2_partial<CH>(q, vec + (int64_t)clist[c] * dp4 * 4, dp4) : 0.f;
+    }
+    const float red = warp_transpose_reduce<G>(part);
+    const int u = my - g * G;
+    const bool mine = cid >= 0 && u >= 0 && u < G;
+    const float v = __shfl_sync(kFull, red, mine ? (u << SH) : 0);
+    if (mine) result = v;
+  }
+  __syncwarp();
+  return result;
+}
+
+// Slot (segment * M + s) of the ci-th selected neighbour (hybrid, S2 selection).
+__device__ __forceinline__ int hybrid_slot(int ci, int per, uint32_t mask, int M, int* seg) {
+  const int kseg = ci / per;
+  const int s = ci - kseg * per;
+  *seg = (int)__fns(mask, 0, kseg + 1);
+  return *seg * M + s;
+}
+
+// One layer of Algorithm 1 (post) or Algorithm 7 (hybrid). Returns |ann|.
+template <int CH, int G>
+__device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (&q)[CH], bool hybrid, int l,
+                            int efl, uint64_t ep_key, bool ep_in, uint32_t mask, uint32_t full_mask, int per,
+                            int pa, int pb, int& n_dist, int& n_exp, uint32_t& status) {
+  const int lane = lane_id();
+  const int H = 1 << a.vis_log2;
+  for (int t = lane; t < H; t += 32) w.vis[t] = -1;
+  __syncwarp();
+  const int ep = key_id(ep_key);
+  if (lane == 0) {
+    w.E[0] = ep_key;
+    w.Ef[0] = 0;
+    if (ep_in) w.ann[0] = ep_key;
+    w.vis[vis_hash(ep, a.vis_log2)] = ep;
+  }
+  __syncwarp();
+  int nE = 1, nA = ep_in ? 1 : 0, cursor = 0, exp_l = 0;
+  const int Sp = __popc(mask);
+  const int SM = a.S * a.M;
+  for (;;) {
+    // the nearest unexpanded candidate
+    while (cursor < nE) {
+      const int j = cursor + lane;
+      const bool un = j < nE && w.Ef[j] == 0;
+      const unsigned bal = __ballot_sync(kFull, un);
+      if (bal) {
+        cursor += __ffs(bal) - 1;
+        break;
+      }
+      cursor += 32;
+    }
+    if (cursor >= nE) break;
+    if (exp_l >= a.max_exp) {
+      status |= UNIFY_Q_LIMIT;
+      break;
+    }
+    const int o = key_id(w.E[cursor]);
+    __syncwarp();
+    if (lane == 0) w.Ef[cursor] = 1;
+    __syncwarp();
+    ++exp_l;
+    ++n_exp;
+    const int64_t row = (l == 0) ? (int64_t)o : ((int64_t)__ldg(a.upper_base + o) + (l - 1));
+    const int32_t* adj = (l == 0 ? a.adj0 : a.adjU) + row * SM;
+    int ncand;
+    if (hybrid) {
+      ncand = Sp * per;
+    } else {
+      // all bitmap words in one round trip, then compaction by ballots
+      const uint32_t* gm = (l == 0 ? a.gmask0 : a.gmaskU) + row * a.W;
+      int cnt = 0;
+      for (int wb = 0; wb < a.W; wb += 32) {
+        const uint32_t myword = wb + lane < a.W ? __ldg(gm + wb + lane) : 0u;
+        const int nw = a.W - wb < 32 ? a.W - wb : 32;
+        for (int wd = 0; wd < nw; ++wd) {
+          const uint32_t word = __shfl_sync(kFull, myword, wd);
+          const bool has = (word >> lane) & 1u;
+          const unsigned bal = __ballot_sync(kFull, has);
+          if (has) {
+            const int p = cnt + __popc(bal & lanemask_lt());
+            if (p < 64) w.slots[p] = (wb + wd) * 32 + lane;
+          }
+          cnt += __popc(bal);
+        }
+      }
+      __syncwarp();
+      ncand = cnt < 64 ? cnt : 64;
+    }
+    // prefetch the adjacency of the next candidate (layer 0) into L2
+    if (l == 0) {
+      const int j = cursor + 1 + lane;
+      const unsigned bal = __ballot_sync(kFull, j < nE && w.Ef[j] == 0);
+      if (bal) {
+        const int o2 = key_id(w.E[cursor + __ffs(bal)]);
+        const int32_t* adj2 = a.adj0 + (int64_t)o2 * SM;
+        if (hybrid) {
+          if (lane < ncand) {
+            int sg;
+            prefetch_l2(adj2 + hybrid_slot(lane, per, mask, a.M, &sg));
+          }
+        } else {
+          if (lane * 32 < SM) prefetch_l2(adj2 + lane * 32);
+          if (lane == 31) prefetch_l2(a.gmask0 + (int64_t)o2 * a.W);
+        }
+      }
+    }
+    for (int rb = 0; rb < ncand; rb += 32) {
+      const int ci = rb + lane;
+      int cid = -1, cseg = 0;
+      if (ci < ncand) {
+        int slot;
+        if (hybrid) {
+          slot = hybrid_slot(ci, per, mask, a.M, &cseg);
+        } else {
+          slot = w.slots[ci];
+          cseg = slot / a.M;
+        }
+        if (slot < SM) cid = __ldg(adj + slot);
+      }
+      if (cid >= 0) {
+        const uint32_t h = vis_hash(cid, a.vis_log2);
+        if (w.vis[h] == cid) cid = -1;
+        else w.vis[h] = cid;
+      }
+      __syncwarp();
+      bool need = false;
+      int pv = 0;
+      if (hybrid && l == 0 && cid >= 0 && !((full_mask >> cseg) & 1u)) {
+        need = true;
+        pv = __ldg(a.pos + cid);
+      }
+      const float dist = batch_dist<CH, G>(q, cid, a.vec, a.dp4, w.clist);
+      const bool inr = need ? (pv >= pa && pv < pb) : true;
+      n_dist += __popc(__ballot_sync(kFull, cid >= 0));
+      const uint64_t key = cid >= 0 ? make_key(dist, cid) : kKeyMax;
+      const uint64_t thr = nA >= efl ? w.ann[efl - 1] : kKeyMax;
+      bool keep = cid >= 0 && key < thr;
+      if (keep && (contains_u64(w.E, nE, key) || contains_u64(w.ann, nA, key))) keep = false;
+      const unsigned kb = __ballot_sync(kFull, keep);
+      if (kb == 0) continue;
+      int r0;
+      bool dropped;
+      const uint64_t sk = warp_sort_asc(keep ? key : kKeyMax);
+      nE = warp_merge(w.E, w.Ef, nE, a.cand_cap, sk, __popc(kb), w.R, &r0, &dropped);
+      if (dropped) status |= UNIFY_Q_TRUNCATED;
+      if (r0 < cursor) cursor = r0;
+      const bool ka = keep && inr;
+      const unsigned ab = __ballot_sync(kFull, ka);
+      if (ab) {
+        const uint64_t sa = warp_sort_asc(ka ? key : kKeyMax);
+        nA = warp_merge(w.ann, nullptr, nA, efl, sa, __popc(ab), w.R, &r0, &dropped);
+      }
+      if (nA >= efl) {
+        nE = upper_bound_u64(w.E, nE, w.ann[efl - 1]);
+        if (cursor > nE) cursor = nE;
+      }
+    }
+  }
+  return nA;
+}
+
+template <int CH, int G>
+__device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool hybrid) {
+  const int lane = lane_id();
+  const uint32_t mask = a.mask[qi];
+  const int pa = a.pa[qi], pb = a.pb[qi];
+  uint32_t status = 0;
+  int n_dist = 0, n_exp = 0, cnt = 0;
+  if (hybrid ? mask != 0 : pb > pa) {  // nothing can be in range otherwise
+    float4 q[CH];
+    load_query<CH>(q, a.q + (int64_t)qi * a.d, a.d);
+    uint32_t full_mask = 0;
+    for (int j = 0; j < a.S; ++j)
+      if (((mask >> j) & 1u) && __ldg(a.seg_start + j) >= pa && __ldg(a.seg_start + j + 1) <= pb)
+        full_mask |= 1u << j;
+    const int Sp = __popc(mask);
+    int per = Sp > 0 ? (a.m + Sp - 1) / Sp : 0;
+    if (per > a.M) per = a.M;
+    const int efl0 = hybrid ? (a.ef_h > a.k ? a.ef_h : a.k) : (a.ef_p > a.k ? a.ef_p : a.k);
+    // entry point: the first object on the top layer
+    const int ep0 = a.entry_global;
+    const float d0 = batch_dist<CH, G>(q, lane == 0 ? ep0 : -1, a.vec, a.dp4, w.clist);
+    uint64_t ep_key = make_key(__shfl_sync(kFull, d0, 0), ep0);
+    n_dist = 1;
+    int nA = 0;
+    for (int l = a.max_level; l >= 0; --l) {
+      const int ep = key_id(ep_key);
+      bool ep_in = true;
+      if (hybrid) {
+        const int p = __ldg(a.pos + ep);
+        if (l == 0) {
+          ep_in = p >= pa && p < pb;
+        } else {
+          int seg = 0;
+          for (int j = 1; j < a.S; ++j)
+            if (__ldg(a.seg_start + j) <= p) seg = j;
+          ep_in = (mask >> seg) & 1u;
+        }
+      }
+      nA = search_layer<CH, G>(a, w, q, hybrid, l, l > 0 ? 1 : efl0, ep_key, ep_in, mask, full_mask, per, pa, pb,
+                               n_dist, n_exp, status);
+      if (l > 0 && nA > 0) ep_key = w.ann[0];
+    }
+    if (hybrid) {
+      cnt = nA < a.k ? nA : a.k;
+      write_row(w.ann, cnt, a.k, qi, a.o);
+    } else {
+      // Strategy B: filter ann by the range, keep the first k
+      for (int base = 0; base < nA && cnt < a.k; base += 32) {
+        const int t = base + lane;
+        bool inr = false;
+        uint64_t key = kKeyMax;
+        if (t < nA) {
+          key = w.ann[t];
+          const int p = __ldg(a.pos + key_id(key));
+          inr = p >= pa && p < pb;
+        }
+        const unsigned bal = __ballot_sync(kFull, inr);
+        const int dst = cnt + __popc(bal & lanemask_lt());
+        if (inr && dst < a.k) {
+          a.o.ids[(int64_t)qi * a.k + dst] = key_id(key);
+          a.o.dist[(int64_t)qi * a.k + dst] = key_dist(key);
+        }
+        cnt += __popc(bal);
+      }
+      if (cnt > a.k) cnt = a.k;
+      for (int t = cnt + lane; t < a.k; t += 32) {
+        a.o.ids[(int64_t)qi * a.k + t] = -1;
+        a.o.dist[(int64_t)qi * a.k + t] = __int_as_float(0x7f800000);
+      }
+    }
+  } else {
+    write_row(w.ann, 0, a.k, qi, a.o);
+  }
+  if (lane == 0) {
+    a.o.count[qi] = cnt;
+    if (a.o.status) a.o.status[qi] = status;
+    if (a.o.counters) {
+      a.o.counters[2 * (int64_t)qi] = n_dist;
+      a.o.counters[2 * (int64_t)qi + 1] = n_exp;
+    }
+  }
+  __syncwarp();
+}
+
+// Keeps the k smallest keys: merges the lanes' keys that beat the current k-th.
+__device__ __forceinline__ int topk_offer(uint64_t* topk, int nt, int k, uint64_t key, int* R) {
+  const uint64_t thr = (nt >= k) ? topk[k - 1] : kKeyMax;
+  const bool pass = key < thr;
+  const unsigned bal = __ballot_sync(kFull, pass);
+  if (bal == 0) return nt;
+  uint64_t s = warp_sort_asc(pass ? key : kKeyMax);
+  int r0;
+  bool dropped;
+  return warp_merge(topk, nullptr, nt, k, s, __popc(bal), R, &r0, &dropped);
+}
+
+template <int CH>
+__device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
+  const int lane = lane_id();
+  uint64_t* topk = w.ann;  // ann_cap >= k
+  const int2 item = a.items[it];
+  const int qi = item.x, b = item.y;
+  const int pa = a.pa[qi], pb = a.pb[qi], nb = a.nblk[qi];
+  const int Y = pb - pa;
+  const int rpb = (Y + nb - 1) / (nb > 0 ? nb : 1);
+  const int r0 = pa + b * rpb;
+  const int r1 = min(pb, r0 + rpb);
+  float4 q[CH];
+  load_query<CH>(q, a.q + (int64_t)qi * a.d, a.d);
+  constexpr int RB = (16 / CH) > 2 ? (16 / CH) : 2;  // rows per load batch (64 registers of loads)
+  int nt = 0;
+  for (int base = r0; base < r1; base += 32) {
+    float part[32];
+#pragma unroll
+    for (int h = 0; h < 32; h += RB) {
+      float4 x[RB][CH];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int row = min(base + h + r, r1 - 1);
+        const float4* src = reinterpret_cast<const float4*>(a.vec_sorted + (int64_t)row * a.dp4 * 4);
+#pragma unroll
+        for (int t = 0; t < CH; ++t) {
+          const int c = lane + 32 * t;
+          x[r][t] = c < a.dp4 ? __ldg(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        float s = 0.f;
+#pragma unroll
+        for (int t = 0; t < CH; ++t) {
+          const float e0 = q[t].x - x[r][t].x, e1 = q[t].y - x[r][t].y;
+          const float e2 = q[t].z - x[r][t].z, e3 = q[t].w - x[r][t].w;
+          s = fmaf(e0, e0, s);
+          s = fmaf(e1, e1, s);
+          s = fmaf(e2, e2, s);
+          s = fmaf(e3, e3, s);
+        }
+        part[h + r] = s;
+      }
+    }
+    const float dist = warp_transpose_reduce<32>(part);
+    const int row = base + lane;
+    uint64_t key = kKeyMax;
+    if (row < r1) key = make_key(dist, __ldg(a.sorted_ids + row));
+    nt = topk_offer(topk, nt, a.k, key, w.R);
+  }
+  if (nb == 1) {
+    write_row(topk, nt, a.k, qi, a.o);
+    if (lane == 0) {
+      a.o.count[qi] = nt;
+      if (a.o.status) a.o.status[qi] = 0u;
+    }
+    __syncwarp();
+    return;
+  }
+  // split query: publish the partial list; the warp finishing the last item merges
+  uint64_t* dst = a.part + (int64_t)it * a.k;
+  for (int t = lane; t < a.k; t += 32) dst[t] = t < nt ? topk[t] : kKeyMax;
+  __threadfence();
+  __syncwarp();
+  int prev = 0;
+  if (lane == 0) prev = atomicAdd(&a.done[qi], 1);
+  prev = __shfl_sync(kFull, prev, 0);
+  if (prev != nb - 1) return;
+  __threadfence();
+  const uint64_t* src = a.part + (int64_t)a.qbase[qi] * a.k;
+  const int total = nb * a.k;
+  nt = 0;
+  for (int off = 0; off < total; off += 32) {
+    const uint64_t key = (off + lane < total) ? __ldcg(reinterpret_cast<const unsigned long long*>(src) + off + lane)
+                                              : kKeyMax;
+    nt = topk_offer(topk, nt, a.k, key, w.R);
+  }
+  const int cnt = min(nt, min(Y, a.k));
+  write_row(topk, cnt, a.k, qi, a.o);
+  if (lane == 0) {
+    a.o.count[qi] = cnt;
+    if (a.o.status) a.o.status[qi] = 0u;
+  }
+  __syncwarp();
+}
+
+template <int CH, int G>
+__global__ void __launch_bounds__(256) batch_kernel(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  const WarpMem w = carve(smem_raw + (size_t)warp * a.warp_bytes, a);
+  const int nC = a.counters[CNT_QC], nB = a.counters[CNT_QB], nI = a.counters[CNT_ITEMS];
+  for (;;) {
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(&a.counters[CNT_TAKE], 1);
+    idx = __shfl_sync(kFull, idx, 0);
+    if (idx < nC) {
+      graph_query<CH, G>(a, w, a.queues[a.cap_nq + idx], true);
+    } else if (idx < nC + nB) {
+      graph_query<CH, G>(a, w, a.queues[2 * a.cap_nq + (idx - nC)], false);
+    } else if (idx < nC + nB + nI) {
+      scan_item<CH>(a, w, idx - nC - nB);
+    } else {
+      break;
+    }
+  }
+}
+
+template <int CH, int G>
+static cudaError_t launch_t(const BatchArgs& a, int wpb, int num_sms, cudaStream_t st) {
+  const int threads = 32 * wpb;
+  const size_t smem = (size_t)wpb * a.warp_bytes;
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<CH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<CH, G>, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  batch_kernel<CH, G><<<num_sms * per_sm, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+int batch_smem_per_warp(const Params& p) {
+  int annc = p.ef > p.ef_post ? p.ef : p.ef_post;
+  if (annc < p.k) annc = p.k;
+  return batch_warp_bytes(p.cand_cap, annc, p.vis_log2);
+}
+
+cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
+                         const Outputs& o, cudaStream_t st) {
+  BatchArgs a;
+  a.vec = ix.vec;
+  a.vec_sorted = ix.vec_sorted;
+  a.sorted_ids = ix.sorted_ids;
+  a.dp4 = ix.dp / 4;
+  a.d = ix.d;
+  a.S = ix.S;
+  a.M = ix.M;
+  a.W = ix.W;
+  a.max_level = ix.max_level;
+  a.entry_global = ix.entry_global;
+  a.adj0 = ix.adj0;
+  a.gmask0 = ix.gmask0;
+  a.adjU = ix.adjU;
+  a.gmaskU = ix.gmaskU;
+  a.upper_base = ix.upper_base;
+  a.pos = ix.pos;
+  a.seg_start = ix.seg_start;
+  a.q = q;
+  a.pa = sc.pa;
+  a.pb = sc.pb;
+  a.mask = sc.mask;
+  a.queues = sc.queues;
+  a.cap_nq = sc.cap_nq;
+  a.nblk = sc.nblk;
+  a.qbase = sc.qbase;
+  a.done = sc.done;
+  a.items = sc.items;
+  a.part = sc.part;
+  a.counters = sc.counters;
+  a.k = p.k;
+  a.ef_h = p.ef;
+  a.ef_p = p.ef_post;
+  a.m = p.m;
+  a.cand_cap = p.cand_cap;
+  a.ann_cap = p.ef > p.ef_post ? p.ef : p.ef_post;
+  if (a.ann_cap < p.k) a.ann_cap = p.k;
+  a.vis_log2 = p.vis_log2;
+  a.max_exp = p.max_exp;
+  a.warp_bytes = batch_warp_bytes(a.cand_cap, a.ann_cap, a.vis_log2);
+  a.o = o;
+  const int wpb = p.warps_per_block;
+  const int ch = (a.dp4 + 31) / 32;
+  if (ch <= 1) return launch_t<1, 16>(a, wpb, ix.num_sms, st);
+  if (ch <= 2) return launch_t<2, 16>(a, wpb, ix.num_sms, st);
+  if (ch <= 4) return launch_t<4, 8>(a, wpb, ix.num_sms, st);
+  return launch_t<8, 8>(a, wpb, ix.num_sms, st);
+}
+
+}  // namespace unify
