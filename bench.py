@@ -214,6 +214,7 @@ def main():
     ap.add_argument("--warps-per-block", type=int, default=4)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the BF16/FP8 lines")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--n", type=int, default=0, help="smaller base set (profiling captures only)")
     ap.add_argument("--nq", type=int, default=0, help="smaller batch (profiling captures only)")
@@ -279,55 +280,120 @@ def main():
     base = U.Params.defaults(tau_a=tau_a, tau_b=tau_b, ef=args.ef, ef_post=args.ef_post or args.ef, m=args.m,
                              cand_cap=args.cand_cap, visited_cap=args.visited_cap,
                              warps_per_block=args.warps_per_block)
-    if args.no_tune:
-        params, report = base, {}
-    else:
-        params, report = autotune.tune(ix, q, lo, hi, k, t_ids, t_cnt, w.fractions, target=args.target,
-                                       base=base, log=log if rank == 0 else None)
-    out = ix.search(q, lo, hi, k, strategy="auto", params=params, counters=True)
-    torch.cuda.synchronize()
-    rec = autotune.recall_rows(out["ids"].cpu().numpy(), t_ids, t_cnt, k)
-    per_frac = autotune.group_recall(rec, w.fractions)
-    counters = out["counters"].cpu().numpy().astype(np.int64)
-    status = out["status"].cpu().numpy()
     route = ix.route(lo, hi, tau_a, tau_b)
     strat = route["strategy"].cpu().numpy()
     pa, pb = route["pa"].cpu().numpy().astype(np.int64), route["pb"].cpu().numpy().astype(np.int64)
     mask = route["mask"].cpu().numpy().astype(np.uint32)
-
-    # timed region: W warm-up steps, then K steps; L2 flushed (256 MiB write)
-    # between steps, outside the per-step events.
+    isA, isC, isB = strat == 0, strat == 1, strat == 2
+    Sp = np.array([bin(int(m_)).count("1") for m_ in mask])
+    hbm, peak_kind = peaks()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    d = w.d
+
+    def algorithmic_bytes(params, counters):
+        """Bytes the search kernel must move per launch (kernels)."""
+        row = {U.FP32: 4 * d, U.BF16: 2 * d, U.FP8E4M3: d + 4}[params.dtype]
+        per = np.minimum(ix.M, -(-params.m // np.maximum(Sp, 1)))
+        rr = 0 if params.dtype == U.FP32 else params.rerank_mult * k * 4 * d
+        parts = {
+            "scan": float(((pb - pa) * (row + 4))[isA].sum() + rr * isA.sum()),
+            "hybrid": float((counters[isC, 0] * row + counters[isC, 1] * Sp[isC] * per[isC] * 4).sum() + rr * isC.sum()),
+            "post": float((counters[isB, 0] * row + counters[isB, 1] * (ix.M + (ix.S * ix.M + 31) // 32) * 4).sum()
+                          + rr * isB.sum()),
+        }
+        return parts
+
+    def measure(params, steps, warmup):
+        out = ix.search(q, lo, hi, k, strategy="auto", params=params, counters=True)
+        torch.cuda.synchronize()
+        rec = autotune.recall_rows(out["ids"].cpu().numpy(), t_ids, t_cnt, k)
+        counters = out["counters"].cpu().numpy().astype(np.int64)
+        status = out["status"].cpu().numpy()
+        out = ix.search(q, lo, hi, k, strategy="auto", params=params)
+        for _ in range(warmup):
+            flush.fill_(1)
+            out = ix.search(q, lo, hi, k, strategy="auto", params=params, out=out)
+        ix.collect_timing()
+        ix.timing(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for s_ in range(steps):
+            flush.fill_(s_ & 0xFF)
+            evs[s_][0].record(stream)
+            out = ix.search(q, lo, hi, k, strategy="auto", params=params, out=out)
+            evs[s_][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - wall0
+        ix.timing(False)
+        phases = ix.collect_timing()
+        ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in evs]))
+        t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        ms_max = float(t_local.item())
+        search_ms = phases["search"][0] / max(1, phases["search"][1])
+        parts = algorithmic_bytes(params, counters)
+        alg = sum(parts.values())
+        achieved = alg / (search_ms / 1000.0) / 1e9 if search_ms > 0 else 0.0
+        return dict(ms=ms_max, value=world * nq / (ms_max / 1000.0), out=out, wall=wall,
+                    recall=autotune.group_recall(rec, w.fractions), status=status,
+                    phases={ph: (v[0] / v[1] if v[1] else 0.0) for ph, v in phases.items()},
+                    achieved=achieved, alg=alg, parts=parts)
+
+    def tuned(extra):
+        b = U.Params.defaults(**{f: getattr(base, f) for f, _ in U.Params._fields_})
+        for kk, v in extra.items():
+            setattr(b, kk, v)
+        if args.no_tune:
+            return b, {}
+        return autotune.tune(ix, q, lo, hi, k, t_ids, t_cnt, w.fractions, target=args.target, base=b,
+                             log=log if rank == 0 else None)
+
+    # FP32 storage: the headline
     clocks = Clocks(local)
     clocks.start()
-    stream = torch.cuda.current_stream(dev)
+    params, report = tuned({})
+    m32 = measure(params, args.steps, args.warmup)
+    clk = clocks.stop()
+    value, ms_max, out = m32["value"], m32["ms"], m32["out"]
+    digest = src_digest("search.cu", "common.cuh")
+    roofline = {"bound": "hbm", "achieved": m32["achieved"], "peak": hbm, "unit": "GB/s",
+                "frac": m32["achieved"] / hbm, "traffic": NCU_TRAFFIC.get(("batch_kernel", digest)),
+                "kernel": "batch_kernel (route excluded)", "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": m32["alg"], "algorithmic_bytes_by_strategy": m32["parts"]}
+
+    # BF16 and FP8 (per-vector scale) storage with FP32 re-rank of 4k candidates
+    precision = {}
+    if not args.no_precision:
+        for name, dt in (("bf16", U.BF16), ("fp8e4m3", U.FP8E4M3)):
+            p_, _ = tuned({"dtype": dt, "rerank_mult": 4})
+            r_ = measure(p_, max(3, args.steps // 2), args.warmup)
+            precision[name] = {
+                "value": r_["value"], "ms_per_step": r_["ms"],
+                "recall_by_fraction": {f"{100 * f_:g}%": round(v_, 4) for f_, v_ in r_["recall"].items()},
+                "roofline_frac": r_["achieved"] / hbm, "achieved_gbs": r_["achieved"],
+                "params": {"ef": p_.ef, "ef_post": p_.ef_post, "m": p_.m, "rerank_mult": p_.rerank_mult}}
+
+    # the same step replayed as one CUDA graph (counter reset, route, search kernel)
+    plan = ix.plan(q, lo, hi, k, strategy="auto", params=params)
     for _ in range(args.warmup):
         flush.fill_(1)
-        out = ix.search(q, lo, hi, k, strategy="auto", params=params, out=out)
-    ix.collect_timing()
-    ix.timing(True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
+        plan.launch()
+    gevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    for s in range(args.steps):
-        flush.fill_(s & 0xFF)
-        evs[s][0].record(stream)
-        out = ix.search(q, lo, hi, k, strategy="auto", params=params, out=out)
-        evs[s][1].record(stream)
+    for s_ in range(args.steps):
+        flush.fill_(s_ & 0xFF)
+        gevs[s_][0].record(stream)
+        plan.launch()
+        gevs[s_][1].record(stream)
     torch.cuda.synchronize()
-    barrier()
-    wall = time.perf_counter() - wall0
-    ix.timing(False)
-    phases = ix.collect_timing()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    ms = float(np.mean(step_ms))
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = world * nq / (ms_max / 1000.0)
+    graph_ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in gevs]))
+    graph_ok = bool(torch.equal(plan.out["ids"], out["ids"]))
+    plan.close()
 
     # end to end through the host-buffer entry point (pinned memory)
     hq = torch.from_numpy(w.queries).pin_memory()
@@ -352,31 +418,6 @@ def main():
     h2d = nq * w.d * 4 + 2 * nq * 8
     d2h = nq * k * (8 + 4) + nq * 4 + nq * 4
 
-    # roofline of the dominant phase (algorithmic bytes per launch / event time)
-    hbm, peak_kind = peaks()
-    d = w.d
-    per_phase_ms = {ph: (v[0] / v[1] if v[1] else 0.0) for ph, v in phases.items()}
-    Sp = np.array([bin(int(m_)).count("1") for m_ in mask])
-    per = np.minimum(ix.M, -(-params.m // np.maximum(Sp, 1)))
-    isA, isC, isB = strat == 0, strat == 1, strat == 2
-    bytes_parts = {
-        # scan: every in-range row once (vector + its id)
-        "scan": float(((pb - pa) * (d * 4 + 4))[isA].sum()),
-        # graph: gathered vectors + the adjacency slots read per expansion
-        "hybrid": float((counters[isC, 0] * d * 4 + counters[isC, 1] * Sp[isC] * per[isC] * 4).sum()),
-        "post": float((counters[isB, 0] * d * 4 + counters[isB, 1] * (ix.M + (ix.S * ix.M + 31) // 32) * 4).sum()),
-    }
-    # the search kernel (all three strategies in one persistent launch) dominates the step
-    search_ms = per_phase_ms["search"]
-    alg_bytes = sum(bytes_parts.values())
-    achieved = alg_bytes / (search_ms / 1000.0) / 1e9 if search_ms > 0 else 0.0
-    digest = src_digest("search.cu", "common.cuh")
-    traffic = NCU_TRAFFIC.get(("batch_kernel", digest))
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "kernel": "batch_kernel (route excluded)", "peak_source": f"{peak_kind} hbm_gbs",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "algorithmic_bytes_by_strategy": bytes_parts}
-
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(path, w, params, k, args.cpu_budget, per_fraction=20)
@@ -392,12 +433,15 @@ def main():
                        "params": {"ef": params.ef, "ef_post": params.ef_post, "m": params.m,
                                   "cand_cap": params.cand_cap, "visited_cap": params.visited_cap,
                                   "warps_per_block": params.warps_per_block, "tau_a": tau_a, "tau_b": tau_b}},
-            "recall_by_fraction": {f"{100 * f_:g}%": round(r_, 4) for f_, r_ in per_frac.items()},
+            "recall_by_fraction": {f"{100 * f_:g}%": round(r_, 4) for f_, r_ in m32["recall"].items()},
             "routed": {"pre": int(isA.sum()), "hybrid": int(isC.sum()), "post": int(isB.sum())},
-            "status_flagged": int(((status & 3) != 0).sum()),
-            "phase_ms_per_step": {ph: round(v, 4) for ph, v in per_phase_ms.items()},
-            "wall_s_timed_region": wall,
+            "status_flagged": int(((m32["status"] & 3) != 0).sum()),
+            "phase_ms_per_step": {ph: round(v, 4) for ph, v in m32["phases"].items() if not ph.startswith("unused")},
+            "wall_s_timed_region": m32["wall"],
             "roofline": roofline,
+            "precision": precision,
+            "cuda_graph": {"ms_per_step": graph_ms, "value": world * nq / (graph_ms / 1000.0),
+                           "same_ids_as_direct": graph_ok},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 2 * args.steps,
             "clocks": clk,

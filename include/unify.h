@@ -48,6 +48,7 @@ extern "C" {
 #endif
 
 typedef struct unify_index unify_index_t; /* opaque, library-owned */
+typedef struct unify_plan unify_plan_t;   /* opaque: a captured search (CUDA graph) */
 
 typedef enum {
   UNIFY_AUTO = -1,
@@ -152,6 +153,26 @@ UNIFY_API int unify_search_auto(unify_index_t* idx, const float* q, const int64_
 UNIFY_API int unify_search_auto_host(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,
                            int64_t nq, int k, int ef, const unify_params_t* p, int64_t* out_ids,
                            float* out_dist, int32_t* out_count, uint32_t* out_status, void* stream);
+
+/* Captures one search of fixed buffers into a CUDA graph: the work-counter reset,
+ * the route kernel and the persistent search kernel. Arguments are those of
+ * unify_search (device buffers, out_counters not recorded). The call first runs
+ * one ordinary search on a private stream (it sizes the scratch and writes the
+ * outputs), then captures a second one. Synchronous. Later unify_plan_launch calls
+ * replay the search on whatever the buffers hold at launch time (update q, lo, hi
+ * in place between launches). While a plan lives, the index refuses searches that
+ * would need more scratch (UNIFY_E_LIMIT); plans and searches on one index share
+ * its scratch, so they must not run concurrently. */
+UNIFY_API int unify_plan_create(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,
+                                int64_t nq, int k, int ef, unify_strategy_t strategy, const unify_params_t* p,
+                                int64_t* out_ids, float* out_dist, int32_t* out_count, uint32_t* out_status,
+                                unify_plan_t** out);
+
+/* Launches a captured search on `stream` (one cudaGraphLaunch). Asynchronous. */
+UNIFY_API int unify_plan_launch(unify_plan_t* plan, void* stream);
+
+/* Releases the graph; the plan's index must still be alive. NULL is ignored. */
+UNIFY_API void unify_plan_destroy(unify_plan_t* plan);
 
 /* unify_search without any device allocation. The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc while searching

@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -82,6 +83,13 @@ def lib():
             L.unify_search_auto_host.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int,
                                                  ctypes.c_int, _P, _P, _P, _P, _P, _P]
             L.unify_search_auto_host.restype = ctypes.c_int
+            L.unify_plan_create.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, _P, _P, _P, _P, _P, ctypes.POINTER(_P)]
+            L.unify_plan_create.restype = ctypes.c_int
+            L.unify_plan_launch.argtypes = [_P, _P]
+            L.unify_plan_launch.restype = ctypes.c_int
+            L.unify_plan_destroy.argtypes = [_P]
+            L.unify_plan_destroy.restype = None
             L.unify_timing_enable.argtypes = [_P, ctypes.c_int]
             L.unify_timing_enable.restype = ctypes.c_int
             L.unify_timing_collect.argtypes = [_P, _P, _P]
@@ -119,8 +127,11 @@ class Index:
         _check(lib().unify_index_info(h, ctypes.byref(n), ctypes.byref(d), ctypes.byref(S), ctypes.byref(M),
                                       ctypes.byref(L)), "unify_index_info")
         self.n, self.d, self.S, self.M, self.max_level = n.value, d.value, S.value, M.value, L.value
+        self._plans = weakref.WeakSet()
 
     def close(self):
+        for p in list(getattr(self, "_plans", ())):
+            p.close()
         if getattr(self, "_h", None):
             lib().unify_free_index(self._h)
             self._h = None
@@ -173,6 +184,12 @@ class Index:
 
     PHASES = ("route", "search", "unused2", "unused3")
 
+    def plan(self, q, lo, hi, k: int, ef: int = 0, strategy="auto", params: Params | None = None):
+        """Captures a search of these device buffers into a CUDA graph (see Plan)."""
+        p = Plan(self, q, lo, hi, k, ef, strategy, params)
+        self._plans.add(p)
+        return p
+
     def timing(self, enable: bool = True):
         _check(lib().unify_timing_enable(self._h, 1 if enable else 0), "unify_timing_enable")
 
@@ -206,3 +223,45 @@ class Index:
                                             _stream_handle(self._torch, self.device)),
                "unify_search_auto_host")
         return out
+
+
+class Plan:
+    """A search captured into a CUDA graph for fixed device buffers. ``launch()``
+    replays it on the current stream; update ``q``, ``lo``, ``hi`` in place between
+    launches. Results land in ``out`` (ids, dist, count, status)."""
+
+    def __init__(self, index: Index, q, lo, hi, k, ef=0, strategy="auto", params=None):
+        torch = index._torch
+        self.index = index
+        self.q = index._dev(q, torch.float32).reshape(-1, index.d)
+        self.lo = index._dev(lo, torch.int64)
+        self.hi = index._dev(hi, torch.int64)
+        nq = self.q.shape[0]
+        self.out = dict(ids=torch.empty((nq, k), dtype=torch.int64, device=index.device),
+                        dist=torch.empty((nq, k), dtype=torch.float32, device=index.device),
+                        count=torch.empty(nq, dtype=torch.int32, device=index.device),
+                        status=torch.empty(nq, dtype=torch.int32, device=index.device))
+        st = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        self._params = params if params is not None else Params.defaults()
+        h = _P()
+        _check(lib().unify_plan_create(index._h, _ptr(self.q), _ptr(self.lo), _ptr(self.hi), nq, k, ef, st,
+                                       ctypes.byref(self._params), _ptr(self.out["ids"]), _ptr(self.out["dist"]),
+                                       _ptr(self.out["count"]), _ptr(self.out["status"]), ctypes.byref(h)),
+               "unify_plan_create")
+        self._h = h
+
+    def launch(self):
+        _check(lib().unify_plan_launch(self._h, _stream_handle(self.index._torch, self.index.device)),
+               "unify_plan_launch")
+        return self.out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().unify_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

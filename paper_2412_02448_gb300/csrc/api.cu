@@ -1,6 +1,7 @@
 // C ABI entry points: argument checks, parameters, scratch, and the launch
 // sequence route -> pre-filter scan (+ merge) -> hybrid search -> post search.
 #include <cstring>
+#include <new>
 #include <string>
 
 #include "common.cuh"
@@ -125,6 +126,7 @@ int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Para
   p.warps_per_block = d.warps_per_block;
   p.scan_rows = d.scan_rows;
   p.dtype = d.dtype;
+  p.rerank_mult = d.rerank_mult;
   p.tau_a = d.tau_a >= 0 ? d.tau_a : ix.n / 100;
   p.tau_b = d.tau_b >= 0 ? d.tau_b : ix.n / 2;
   if (p.ef < 1 || p.ef > 2048 || p.ef_post < 1 || p.ef_post > 2048) return fail(UNIFY_E_ARG, "ef and ef_post must be in [1, 2048]");
@@ -137,7 +139,14 @@ int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Para
   if (p.max_exp < 1) return fail(UNIFY_E_ARG, "max_expansions must be >= 1");
   if (p.warps_per_block < 1 || p.warps_per_block > 8) return fail(UNIFY_E_ARG, "warps_per_block must be in [1, 8]");
   if (p.scan_rows < 32) return fail(UNIFY_E_ARG, "scan_rows must be >= 32");
-  if (p.dtype != UNIFY_FP32) return fail(UNIFY_E_ARG, "dtype: only UNIFY_FP32 is available in this build");
+  if (p.dtype != UNIFY_FP32 && p.dtype != UNIFY_BF16 && p.dtype != UNIFY_FP8E4M3)
+    return fail(UNIFY_E_ARG, "dtype must be UNIFY_FP32, UNIFY_BF16 or UNIFY_FP8E4M3");
+  if (p.dtype != UNIFY_FP32) {
+    if (p.rerank_mult < 1 || (long)p.rerank_mult * k > kMaxCand)
+      return fail(UNIFY_E_ARG, "rerank_mult must be >= 1 with rerank_mult * k <= 4096");
+    // the re-rank reads its candidates from the candidate buffer
+    if (p.cand_cap < rerank_count(p)) p.cand_cap = rerank_count(p);
+  }
   const long smem = (long)p.warps_per_block * batch_smem_per_warp(p);
   if (smem > 227 * 1024) return fail(UNIFY_E_LIMIT, "graph search shared memory per CTA exceeds 227 KB; lower warps_per_block, cand_cap, visited_cap or ef");
   return UNIFY_OK;
@@ -187,7 +196,12 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
   if (nq == 0) return UNIFY_OK;
   if (!q || !lo || !hi || !out_ids || !out_dist || !out_count) return fail(UNIFY_E_ARG, "null query or output pointer");
   DeviceGuard guard(idx->ix.device);
-  cudaError_t e = ensure_scratch(idx->sc, nq, k);
+  if (idx->live_plans > 0 && (nq > idx->sc.cap_nq || k > idx->sc.cap_k))
+    return fail(UNIFY_E_LIMIT, "search larger than the scratch held by a live plan; destroy the plans first");
+  const int kk = rerank_count(p) > k ? rerank_count(p) : k;  // keys per partial scan list
+  if (idx->live_plans > 0 && kk > idx->sc.cap_k)
+    return fail(UNIFY_E_LIMIT, "search larger than the scratch held by a live plan; destroy the plans first");
+  cudaError_t e = ensure_scratch(idx->sc, nq, kk);
   if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
   Scratch& sc = idx->sc;
   e = cudaMemsetAsync(sc.counters, 0, kNumCounters * sizeof(int32_t), st);
@@ -242,6 +256,83 @@ extern "C" void unify_default_params(unify_params_t* p) {
 }
 
 extern "C" const char* unify_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int unify_plan_create(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,
+                                 int64_t nq, int k, int ef, unify_strategy_t strategy, const unify_params_t* p,
+                                 int64_t* out_ids, float* out_dist, int32_t* out_count, uint32_t* out_status,
+                                 unify_plan_t** out) {
+  if (!idx || !out) return fail(UNIFY_E_ARG, "unify_plan_create: null argument");
+  *out = nullptr;
+  if (nq < 1) return fail(UNIFY_E_ARG, "unify_plan_create: nq must be >= 1");
+  DeviceGuard guard(idx->ix.device);
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "unify_plan_create: stream");
+  // One ordinary search first: it sizes the scratch and sets kernel attributes, so
+  // that the captured search enqueues kernels only.
+  const bool timing = idx->tm.on;
+  idx->tm.on = false;
+  int rc = run_search(idx, q, lo, hi, nq, k, ef, (int)strategy, p, out_ids, out_dist, out_count, out_status,
+                      nullptr, cs);
+  if (rc == UNIFY_OK) {
+    e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) rc = cuda_fail(e, "unify_plan_create: first search");
+  }
+  unify_plan_t* plan = nullptr;
+  if (rc == UNIFY_OK) {
+    plan = new (std::nothrow) unify_plan_t;
+    if (!plan) rc = fail(UNIFY_E_NOMEM, "unify_plan_create: host allocation");
+  }
+  if (rc == UNIFY_OK) {
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "unify_plan_create: begin capture");
+    } else {
+      rc = run_search(idx, q, lo, hi, nq, k, ef, (int)strategy, p, out_ids, out_dist, out_count, out_status,
+                      nullptr, cs);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(cs, &g);
+      if (rc == UNIFY_OK && e != cudaSuccess) rc = cuda_fail(e, "unify_plan_create: end capture");
+      plan->graph = g;
+      if (rc == UNIFY_OK) {
+        e = cudaGraphInstantiate(&plan->exec, g, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "unify_plan_create: instantiate");
+      }
+    }
+  }
+  idx->tm.on = timing;
+  cudaStreamDestroy(cs);
+  if (rc != UNIFY_OK) {
+    if (plan) {
+      if (plan->exec) cudaGraphExecDestroy(plan->exec);
+      if (plan->graph) cudaGraphDestroy(plan->graph);
+      delete plan;
+    }
+    return rc;
+  }
+  plan->idx = idx;
+  idx->live_plans++;
+  *out = plan;
+  return UNIFY_OK;
+}
+
+extern "C" int unify_plan_launch(unify_plan_t* plan, void* stream) {
+  if (!plan || !plan->exec) return fail(UNIFY_E_ARG, "unify_plan_launch: null plan");
+  DeviceGuard guard(plan->idx->ix.device);
+  cudaError_t e = cudaGraphLaunch(plan->exec, (cudaStream_t)stream);
+  return e == cudaSuccess ? UNIFY_OK : cuda_fail(e, "unify_plan_launch");
+}
+
+extern "C" void unify_plan_destroy(unify_plan_t* plan) {
+  if (!plan) return;
+  {
+    DeviceGuard guard(plan->idx->ix.device);
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+  }
+  plan->idx->live_plans--;
+  delete plan;
+}
 
 extern "C" int unify_timing_enable(unify_index_t* idx, int enable) {
   if (!idx) return fail(UNIFY_E_ARG, "unify_timing_enable: null index");

@@ -6,6 +6,8 @@
 // (distance, id) lexicographically: the tie rule "equal distance -> smaller id".
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -141,16 +143,47 @@ __device__ __forceinline__ float warp_transpose_reduce(float (&v)[V]) {
   return v[0];
 }
 
-// Squared-L2 partial of one lane over its float4 chunks c = lane + 32 t.
-template <int CH>
-__device__ __forceinline__ float l2_partial(const float4 (&q)[CH], const float* row, int nchunks) {
+// Vector storage formats. A row is dp4 chunks of 4 elements; lane L handles chunks
+// L, L + 32, ... in every format, so the query registers and the reduction tree
+// are the same and only the load width differs (16, 8 or 4 bytes per chunk).
+struct StoreF32 {
+  static constexpr int kChunkBytes = 16;
+  __device__ static __forceinline__ float4 load(const unsigned char* row, int c, float) {
+    return __ldg(reinterpret_cast<const float4*>(row) + c);
+  }
+};
+struct StoreBF16 {  // bfloat16, converted from float32 with round-to-nearest-even
+  static constexpr int kChunkBytes = 8;
+  __device__ static __forceinline__ float4 load(const unsigned char* row, int c, float) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(row) + c);
+    // a bfloat16 is the upper half of a float32
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+  }
+};
+struct StoreFP8 {  // E4M3 codes of x / s with s = max|x| / 448 per vector
+  static constexpr int kChunkBytes = 4;
+  __device__ static __forceinline__ float4 load(const unsigned char* row, int c, float scale) {
+    const uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(row) + c);
+    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xffffu), __NV_E4M3);
+    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+    return make_float4(a.x * scale, a.y * scale, b.x * scale, b.y * scale);
+  }
+};
+
+// Squared-L2 partial of one lane over its chunks of a row in storage format T.
+template <class T, int CH>
+__device__ __forceinline__ float l2_partial_t(const float4 (&q)[CH], const unsigned char* row, int nchunks,
+                                              float scale) {
   const int lane = lane_id();
   float s = 0.f;
 #pragma unroll
   for (int t = 0; t < CH; ++t) {
     int c = lane + 32 * t;
     if (c < nchunks) {
-      float4 x = __ldg(reinterpret_cast<const float4*>(row) + c);
+      float4 x = T::load(row, c, scale);
       float a = q[t].x - x.x, b = q[t].y - x.y, e = q[t].z - x.z, f = q[t].w - x.w;
       s = fmaf(a, a, s);
       s = fmaf(b, b, s);

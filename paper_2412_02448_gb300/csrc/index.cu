@@ -94,11 +94,56 @@ __global__ void derive_kernel(const float* __restrict__ vec, const int32_t* __re
   }
 }
 
+// Reduced-precision copies, one warp per attribute-order position p (object v):
+// bfloat16 by round-to-nearest-even; FP8 E4M3 codes of x / s (saturating,
+// round-to-nearest-even) with s = max|x| / 448 (s = 1 for an all-zero vector).
+__global__ void lowp_kernel(const float* __restrict__ vec, const int32_t* __restrict__ sorted_ids, int64_t n,
+                            int dp, uint2* bf_id, uint2* bf_sorted, uint32_t* f8_id, uint32_t* f8_sorted,
+                            float* sc_id, float* sc_sorted) {
+  const int lane = threadIdx.x & 31;
+  const int dp4 = dp / 4;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += warps) {
+    const int32_t v = sorted_ids[p];
+    const float4* row = reinterpret_cast<const float4*>(vec + (int64_t)v * dp);
+    float mx = 0.f;
+    for (int c = lane; c < dp4; c += 32) {
+      const float4 x = row[c];
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+    }
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    const float s = mx > 0.f ? mx / 448.f : 1.f;
+    for (int c = lane; c < dp4; c += 32) {
+      const float4 x = row[c];
+      uint2 b;
+      b.x = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.x)) |
+            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.y)) << 16);
+      b.y = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.z)) |
+            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.w)) << 16);
+      const uint32_t f = (uint32_t)__nv_cvt_float_to_fp8(x.x / s, __NV_SATFINITE, __NV_E4M3) |
+                         ((uint32_t)__nv_cvt_float_to_fp8(x.y / s, __NV_SATFINITE, __NV_E4M3) << 8) |
+                         ((uint32_t)__nv_cvt_float_to_fp8(x.z / s, __NV_SATFINITE, __NV_E4M3) << 16) |
+                         ((uint32_t)__nv_cvt_float_to_fp8(x.w / s, __NV_SATFINITE, __NV_E4M3) << 24);
+      bf_id[(int64_t)v * dp4 + c] = b;
+      bf_sorted[p * dp4 + c] = b;
+      f8_id[(int64_t)v * dp4 + c] = f;
+      f8_sorted[p * dp4 + c] = f;
+    }
+    if (lane == 0) {
+      sc_id[v] = s;
+      sc_sorted[p] = s;
+    }
+  }
+}
+
 void free_device(DeviceIndex& ix) {
   void* ptrs[] = {ix.vec, ix.vec_sorted, ix.sorted_ids, ix.sorted_attr, ix.pos, ix.upper_base, ix.adj0,
-                  ix.gmask0, ix.adjU, ix.gmaskU, ix.seg_bounds, ix.seg_start};
+                  ix.gmask0, ix.adjU, ix.gmaskU, ix.seg_bounds, ix.seg_start, ix.vt_bf16, ix.vts_bf16,
+                  ix.vt_fp8, ix.vts_fp8, ix.scale_fp8, ix.scale_fp8_sorted};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  ix.vt_bf16 = ix.vts_bf16 = ix.vt_fp8 = ix.vts_fp8 = nullptr;
+  ix.scale_fp8 = ix.scale_fp8_sorted = nullptr;
   ix.vec = ix.vec_sorted = nullptr;
   ix.sorted_ids = ix.pos = ix.upper_base = ix.adj0 = ix.adjU = ix.seg_start = nullptr;
   ix.sorted_attr = ix.seg_bounds = nullptr;
@@ -275,8 +320,21 @@ extern "C" int unify_load_index(const char* path, int device, unify_index_t** ou
   if (e == cudaSuccess) e = cudaMalloc(&ix.vec_sorted, n * ix.dp * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&ix.sorted_attr, n * sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&ix.pos, n * sizeof(int32_t));
+  const uint64_t dp4 = (uint64_t)ix.dp / 4;
+  if (e == cudaSuccess) e = cudaMalloc(&ix.vt_bf16, n * dp4 * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&ix.vts_bf16, n * dp4 * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&ix.vt_fp8, n * dp4 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&ix.vts_fp8, n * dp4 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&ix.scale_fp8, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&ix.scale_fp8_sorted, n * sizeof(float));
   if (e == cudaSuccess) {
     derive_kernel<<<1024, 256>>>(ix.vec, ix.sorted_ids, d_attr, ix.n, ix.dp, ix.vec_sorted, ix.sorted_attr, ix.pos);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    lowp_kernel<<<1024, 256>>>(ix.vec, ix.sorted_ids, ix.n, ix.dp, reinterpret_cast<uint2*>(ix.vt_bf16),
+                               reinterpret_cast<uint2*>(ix.vts_bf16), reinterpret_cast<uint32_t*>(ix.vt_fp8),
+                               reinterpret_cast<uint32_t*>(ix.vts_fp8), ix.scale_fp8, ix.scale_fp8_sorted);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

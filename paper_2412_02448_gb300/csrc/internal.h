@@ -39,6 +39,13 @@ struct DeviceIndex {
   uint32_t* gmaskU = nullptr;   // (n_upper, W)
   int64_t* seg_bounds = nullptr;  // (S+1)
   int32_t* seg_start = nullptr;   // (S+1)
+  // reduced-precision copies (rows of dp/4 chunks of 4 elements): by id and in attribute order
+  unsigned char* vt_bf16 = nullptr;   // bfloat16, 8 bytes per chunk
+  unsigned char* vts_bf16 = nullptr;
+  unsigned char* vt_fp8 = nullptr;    // E4M3 codes of x / scale, 4 bytes per chunk
+  unsigned char* vts_fp8 = nullptr;
+  float* scale_fp8 = nullptr;         // per-vector scale max|x| / 448 (by id)
+  float* scale_fp8_sorted = nullptr;  // the same in attribute order
   int num_sms = 0;
 };
 
@@ -78,7 +85,7 @@ enum {
 };
 
 struct Params {
-  int k, ef, m, ef_post, cand_cap, vis_log2, max_exp, warps_per_block, scan_rows;
+  int k, ef, m, ef_post, cand_cap, vis_log2, max_exp, warps_per_block, scan_rows, rerank_mult;
   int64_t tau_a, tau_b;
   unify_dtype_t dtype;
 };
@@ -99,6 +106,7 @@ cudaError_t launch_route(const DeviceIndex& ix, const Scratch& sc, const int64_t
 cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
                          const Outputs& o, cudaStream_t st);
 int batch_smem_per_warp(const Params& p);
+int rerank_count(const Params& p);  // candidates re-ranked in FP32 (0 for FP32 storage)
 
 void set_error(const std::string& msg);
 int resolve_search_params(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Params& p);
@@ -132,4 +140,11 @@ struct unify_index {
   unify::DeviceIndex ix;
   unify::Scratch sc;
   unify::Timing tm;
+  int live_plans = 0;  // captured graphs that hold pointers into sc
+};
+
+struct unify_plan {
+  unify_index* idx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };

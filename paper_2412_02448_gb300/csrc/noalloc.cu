@@ -99,6 +99,8 @@ extern "C" int unify_search_noalloc(unify_index_t* idx, const float* q, const in
   Params prm;
   int rc = resolve_search_params(idx->ix, p, k, ef, prm);
   if (rc != UNIFY_OK) return rc;
+  if (rerank_count(prm) > kNoAllocMaxK)
+    return fail(UNIFY_E_LIMIT, "unify_search_noalloc: rerank_mult * k must be <= 16 (fixed scratch limit)");
   if (nq == 0) return UNIFY_OK;
   if (!q || !lo || !hi || !out_ids || !out_dist || !out_count)
     return fail(UNIFY_E_ARG, "unify_search_noalloc: null query or output pointer");

@@ -47,8 +47,13 @@
 namespace unify {
 
 struct BatchArgs {
-  const float* vec;
-  const float* vec_sorted;
+  const float* vec;                // float32 rows by id (re-rank, and traversal for FP32)
+  const unsigned char* vt;         // traversal rows by id in the storage format
+  const unsigned char* vts;        // the same rows in attribute order (scan)
+  const float* scale;              // FP8 per-vector scales by id (else null)
+  const float* scale_sorted;       // FP8 scales in attribute order
+  int row_bytes;                   // bytes per stored row
+  int rerank;                      // candidates re-ranked in FP32 (0: FP32 storage, none)
   const int32_t* sorted_ids;
   int dp4, d;
   int S, M, W, max_level, entry_global;
@@ -123,10 +128,11 @@ __device__ __forceinline__ void write_row(const uint64_t* keys, int cnt, int k, 
   }
 }
 
-// Distances of the candidates held by the lanes (cid >= 0), G at a time.
-template <int CH, int G>
-__device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, const float* vec, int dp4,
-                                            int* clist) {
+// Distances of the candidates held by the lanes (cid >= 0), G at a time, from
+// rows of `rows` (row_bytes each) in storage format T (scale: FP8 scales or null).
+template <class T, int CH, int G>
+__device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, const unsigned char* rows,
+                                            int row_bytes, const float* scale, int dp4, int* clist) {
   const unsigned vm = __ballot_sync(kFull, cid >= 0);
   const int nv = __popc(vm);
   const int my = __popc(vm & lanemask_lt());
@@ -139,7 +145,13 @@ __device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, cons
 #pragma unroll
     for (int u = 0; u < G; ++u) {
       const int c = g * G + u;
-      part[u] = (c < nv) ? l2_partial<CH>(q, vec + (int64_t)clist[c] * dp4 * 4, dp4) : 0.f;
+      if (c < nv) {
+        const int id = clist[c];
+        const float sc = scale ? __ldg(scale + id) : 1.f;
+        part[u] = l2_partial_t<T, CH>(q, rows + (int64_t)id * row_bytes, dp4, sc);
+      } else {
+        part[u] = 0.f;
+      }
     }
     const float red = warp_transpose_reduce<G>(part);
     const int u = my - g * G;
@@ -160,7 +172,7 @@ __device__ __forceinline__ int hybrid_slot(int ci, int per, uint32_t mask, int M
 }
 
 // One layer of Algorithm 1 (post) or Algorithm 7 (hybrid). Returns |ann|.
-template <int CH, int G>
+template <class T, int CH, int G>
 __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (&q)[CH], bool hybrid, int l,
                             int efl, uint64_t ep_key, bool ep_in, uint32_t mask, uint32_t full_mask, int per,
                             int pa, int pb, int& n_dist, int& n_exp, uint32_t& status) {
@@ -271,7 +283,7 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
         need = true;
         pv = __ldg(a.pos + cid);
       }
-      const float dist = batch_dist<CH, G>(q, cid, a.vec, a.dp4, w.clist);
+      const float dist = batch_dist<T, CH, G>(q, cid, a.vt, a.row_bytes, a.scale, a.dp4, w.clist);
       const bool inr = need ? (pv >= pa && pv < pb) : true;
       n_dist += __popc(__ballot_sync(kFull, cid >= 0));
       const uint64_t key = cid >= 0 ? make_key(dist, cid) : kKeyMax;
@@ -301,7 +313,39 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
   return nA;
 }
 
+// Keeps the k smallest keys: merges the lanes' keys that beat the current k-th.
+__device__ __forceinline__ int topk_offer(uint64_t* topk, int nt, int k, uint64_t key, int* R) {
+  const uint64_t thr = (nt >= k) ? topk[k - 1] : kKeyMax;
+  const bool pass = key < thr;
+  const unsigned bal = __ballot_sync(kFull, pass);
+  if (bal == 0) return nt;
+  uint64_t s = warp_sort_asc(pass ? key : kKeyMax);
+  int r0;
+  bool dropped;
+  return warp_merge(topk, nullptr, nt, k, s, __popc(bal), R, &r0, &dropped);
+}
+
+// FP32 re-rank: exact float32 distances (direct difference against the float32
+// rows) of the nc candidates in keys[], the k best written to row qi. tmp holds
+// >= k keys and does not overlap keys. Returns the number written.
 template <int CH, int G>
+__device__ int rerank_write(const BatchArgs& a, const WarpMem& w, const float4 (&q)[CH], const uint64_t* keys,
+                            int nc, int64_t qi, uint64_t* tmp) {
+  const int lane = lane_id();
+  int nt = 0;
+  for (int base = 0; base < nc; base += 32) {
+    const int t = base + lane;
+    const int cid = t < nc ? key_id(keys[t]) : -1;
+    const float dist = batch_dist<StoreF32, CH, G>(q, cid, reinterpret_cast<const unsigned char*>(a.vec),
+                                                   a.dp4 * 16, nullptr, a.dp4, w.clist);
+    const uint64_t key = cid >= 0 ? make_key(dist, cid) : kKeyMax;
+    nt = topk_offer(tmp, nt, a.k, key, w.R);
+  }
+  write_row(tmp, nt, a.k, qi, a.o);
+  return nt;
+}
+
+template <class T, int CH, int G>
 __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool hybrid) {
   const int lane = lane_id();
   const uint32_t mask = a.mask[qi];
@@ -321,7 +365,7 @@ __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool h
     const int efl0 = hybrid ? (a.ef_h > a.k ? a.ef_h : a.k) : (a.ef_p > a.k ? a.ef_p : a.k);
     // entry point: the first object on the top layer
     const int ep0 = a.entry_global;
-    const float d0 = batch_dist<CH, G>(q, lane == 0 ? ep0 : -1, a.vec, a.dp4, w.clist);
+    const float d0 = batch_dist<T, CH, G>(q, lane == 0 ? ep0 : -1, a.vt, a.row_bytes, a.scale, a.dp4, w.clist);
     uint64_t ep_key = make_key(__shfl_sync(kFull, d0, 0), ep0);
     n_dist = 1;
     int nA = 0;
@@ -339,11 +383,37 @@ __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool h
           ep_in = (mask >> seg) & 1u;
         }
       }
-      nA = search_layer<CH, G>(a, w, q, hybrid, l, l > 0 ? 1 : efl0, ep_key, ep_in, mask, full_mask, per, pa, pb,
+      nA = search_layer<T, CH, G>(a, w, q, hybrid, l, l > 0 ? 1 : efl0, ep_key, ep_in, mask, full_mask, per, pa, pb,
                                n_dist, n_exp, status);
       if (l > 0 && nA > 0) ep_key = w.ann[0];
     }
-    if (hybrid) {
+    if (a.rerank > 0) {
+      // reduced-precision storage: re-rank the first rerank_mult * k candidates in FP32
+      const uint64_t* src = w.ann;
+      int nc = nA;
+      if (!hybrid) {
+        // Strategy B: the range filter first, compacted into E (free after the search)
+        nc = 0;
+        for (int base = 0; base < nA && nc < a.rerank; base += 32) {
+          const int t = base + lane;
+          bool inr = false;
+          uint64_t key = kKeyMax;
+          if (t < nA) {
+            key = w.ann[t];
+            const int p = __ldg(a.pos + key_id(key));
+            inr = p >= pa && p < pb;
+          }
+          const unsigned bal = __ballot_sync(kFull, inr);
+          const int dst = nc + __popc(bal & lanemask_lt());
+          if (inr && dst < a.rerank) w.E[dst] = key;
+          nc += __popc(bal);
+        }
+        __syncwarp();
+        src = w.E;
+      }
+      if (nc > a.rerank) nc = a.rerank;
+      cnt = rerank_write<CH, G>(a, w, q, src, nc, qi, hybrid ? w.E : w.ann);
+    } else if (hybrid) {
       cnt = nA < a.k ? nA : a.k;
       write_row(w.ann, cnt, a.k, qi, a.o);
     } else {
@@ -385,22 +455,11 @@ __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool h
   __syncwarp();
 }
 
-// Keeps the k smallest keys: merges the lanes' keys that beat the current k-th.
-__device__ __forceinline__ int topk_offer(uint64_t* topk, int nt, int k, uint64_t key, int* R) {
-  const uint64_t thr = (nt >= k) ? topk[k - 1] : kKeyMax;
-  const bool pass = key < thr;
-  const unsigned bal = __ballot_sync(kFull, pass);
-  if (bal == 0) return nt;
-  uint64_t s = warp_sort_asc(pass ? key : kKeyMax);
-  int r0;
-  bool dropped;
-  return warp_merge(topk, nullptr, nt, k, s, __popc(bal), R, &r0, &dropped);
-}
-
-template <int CH>
+template <class T, int CH, int G>
 __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
   const int lane = lane_id();
-  uint64_t* topk = w.ann;  // ann_cap >= k
+  uint64_t* topk = w.ann;  // ann_cap >= kk
+  const int kk = a.rerank > 0 ? a.rerank : a.k;  // keys kept per list
   const int2 item = a.items[it];
   const int qi = item.x, b = item.y;
   const int pa = a.pa[qi], pb = a.pb[qi], nb = a.nblk[qi];
@@ -410,7 +469,7 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
   const int r1 = min(pb, r0 + rpb);
   float4 q[CH];
   load_query<CH>(q, a.q + (int64_t)qi * a.d, a.d);
-  constexpr int RB = (16 / CH) > 2 ? (16 / CH) : 2;  // rows per load batch (64 registers of loads)
+  constexpr int RB = (16 / CH) > 2 ? (16 / CH) : 2;  // rows per load batch
   int nt = 0;
   for (int base = r0; base < r1; base += 32) {
     float part[32];
@@ -420,11 +479,12 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
         const int row = min(base + h + r, r1 - 1);
-        const float4* src = reinterpret_cast<const float4*>(a.vec_sorted + (int64_t)row * a.dp4 * 4);
+        const unsigned char* src = a.vts + (int64_t)row * a.row_bytes;
+        const float sc = a.scale_sorted ? __ldg(a.scale_sorted + row) : 1.f;
 #pragma unroll
         for (int t = 0; t < CH; ++t) {
           const int c = lane + 32 * t;
-          x[r][t] = c < a.dp4 ? __ldg(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          x[r][t] = c < a.dp4 ? T::load(src, c, sc) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
 #pragma unroll
@@ -446,37 +506,37 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
     const int row = base + lane;
     uint64_t key = kKeyMax;
     if (row < r1) key = make_key(dist, __ldg(a.sorted_ids + row));
-    nt = topk_offer(topk, nt, a.k, key, w.R);
+    nt = topk_offer(topk, nt, kk, key, w.R);
   }
-  if (nb == 1) {
-    write_row(topk, nt, a.k, qi, a.o);
-    if (lane == 0) {
-      a.o.count[qi] = nt;
-      if (a.o.status) a.o.status[qi] = 0u;
-    }
+  if (nb > 1) {
+    // split query: publish the partial list; the warp finishing the last item merges
+    uint64_t* dst = a.part + (int64_t)it * kk;
+    for (int t = lane; t < kk; t += 32) dst[t] = t < nt ? topk[t] : kKeyMax;
+    __threadfence();
     __syncwarp();
-    return;
+    int prev = 0;
+    if (lane == 0) prev = atomicAdd(&a.done[qi], 1);
+    prev = __shfl_sync(kFull, prev, 0);
+    if (prev != nb - 1) return;
+    __threadfence();
+    const uint64_t* src = a.part + (int64_t)a.qbase[qi] * kk;
+    const int total = nb * kk;
+    nt = 0;
+    for (int off = 0; off < total; off += 32) {
+      const uint64_t key = (off + lane < total)
+                               ? __ldcg(reinterpret_cast<const unsigned long long*>(src) + off + lane)
+                               : kKeyMax;
+      nt = topk_offer(topk, nt, kk, key, w.R);
+    }
+    nt = min(nt, Y);
   }
-  // split query: publish the partial list; the warp finishing the last item merges
-  uint64_t* dst = a.part + (int64_t)it * a.k;
-  for (int t = lane; t < a.k; t += 32) dst[t] = t < nt ? topk[t] : kKeyMax;
-  __threadfence();
-  __syncwarp();
-  int prev = 0;
-  if (lane == 0) prev = atomicAdd(&a.done[qi], 1);
-  prev = __shfl_sync(kFull, prev, 0);
-  if (prev != nb - 1) return;
-  __threadfence();
-  const uint64_t* src = a.part + (int64_t)a.qbase[qi] * a.k;
-  const int total = nb * a.k;
-  nt = 0;
-  for (int off = 0; off < total; off += 32) {
-    const uint64_t key = (off + lane < total) ? __ldcg(reinterpret_cast<const unsigned long long*>(src) + off + lane)
-                                              : kKeyMax;
-    nt = topk_offer(topk, nt, a.k, key, w.R);
+  int cnt;
+  if (a.rerank > 0) {
+    cnt = rerank_write<CH, G>(a, w, q, topk, nt, qi, w.E);
+  } else {
+    cnt = min(nt, a.k);
+    write_row(topk, cnt, a.k, qi, a.o);
   }
-  const int cnt = min(nt, min(Y, a.k));
-  write_row(topk, cnt, a.k, qi, a.o);
   if (lane == 0) {
     a.o.count[qi] = cnt;
     if (a.o.status) a.o.status[qi] = 0u;
@@ -484,7 +544,7 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
   __syncwarp();
 }
 
-template <int CH, int G>
+template <class T, int CH, int G>
 __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -495,44 +555,76 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a) {
     if (lane == 0) idx = atomicAdd(&a.counters[CNT_TAKE], 1);
     idx = __shfl_sync(kFull, idx, 0);
     if (idx < nC) {
-      graph_query<CH, G>(a, w, a.queues[a.cap_nq + idx], true);
+      graph_query<T, CH, G>(a, w, a.queues[a.cap_nq + idx], true);
     } else if (idx < nC + nB) {
-      graph_query<CH, G>(a, w, a.queues[2 * a.cap_nq + (idx - nC)], false);
+      graph_query<T, CH, G>(a, w, a.queues[2 * a.cap_nq + (idx - nC)], false);
     } else if (idx < nC + nB + nI) {
-      scan_item<CH>(a, w, idx - nC - nB);
+      scan_item<T, CH, G>(a, w, idx - nC - nB);
     } else {
       break;
     }
   }
 }
 
-template <int CH, int G>
+template <class T, int CH, int G>
 static cudaError_t launch_t(const BatchArgs& a, int wpb, int num_sms, cudaStream_t st) {
   const int threads = 32 * wpb;
   const size_t smem = (size_t)wpb * a.warp_bytes;
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel<CH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(batch_kernel<T, CH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<CH, G>, threads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<T, CH, G>, threads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  batch_kernel<CH, G><<<num_sms * per_sm, threads, smem, st>>>(a);
+  batch_kernel<T, CH, G><<<num_sms * per_sm, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-int batch_smem_per_warp(const Params& p) {
-  int annc = p.ef > p.ef_post ? p.ef : p.ef_post;
-  if (annc < p.k) annc = p.k;
-  return batch_warp_bytes(p.cand_cap, annc, p.vis_log2);
+template <class T>
+static cudaError_t launch_dt(const BatchArgs& a, int wpb, int num_sms, cudaStream_t st) {
+  const int ch = (a.dp4 + 31) / 32;
+  if (ch <= 1) return launch_t<T, 1, 16>(a, wpb, num_sms, st);
+  if (ch <= 2) return launch_t<T, 2, 16>(a, wpb, num_sms, st);
+  if (ch <= 4) return launch_t<T, 4, 8>(a, wpb, num_sms, st);
+  return launch_t<T, 8, 8>(a, wpb, num_sms, st);
 }
+
+int rerank_count(const Params& p) { return p.dtype == UNIFY_FP32 ? 0 : p.rerank_mult * p.k; }
+
+int batch_ann_cap(const Params& p) {
+  int c = p.ef > p.ef_post ? p.ef : p.ef_post;
+  if (c < p.k) c = p.k;
+  if (c < rerank_count(p)) c = rerank_count(p);
+  return c;
+}
+
+int batch_smem_per_warp(const Params& p) { return batch_warp_bytes(p.cand_cap, batch_ann_cap(p), p.vis_log2); }
 
 cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
                          const Outputs& o, cudaStream_t st) {
   BatchArgs a;
   a.vec = ix.vec;
-  a.vec_sorted = ix.vec_sorted;
-  a.sorted_ids = ix.sorted_ids;
   a.dp4 = ix.dp / 4;
+  a.rerank = rerank_count(p);
+  if (p.dtype == UNIFY_BF16) {
+    a.vt = ix.vt_bf16;
+    a.vts = ix.vts_bf16;
+    a.scale = a.scale_sorted = nullptr;
+    a.row_bytes = a.dp4 * 8;
+  } else if (p.dtype == UNIFY_FP8E4M3) {
+    a.vt = ix.vt_fp8;
+    a.vts = ix.vts_fp8;
+    a.scale = ix.scale_fp8;
+    a.scale_sorted = ix.scale_fp8_sorted;
+    a.row_bytes = a.dp4 * 4;
+  } else {
+    a.vt = reinterpret_cast<const unsigned char*>(ix.vec);
+    a.vts = reinterpret_cast<const unsigned char*>(ix.vec_sorted);
+    a.scale = a.scale_sorted = nullptr;
+    a.row_bytes = a.dp4 * 16;
+  }
+  a.sorted_ids = ix.sorted_ids;
   a.d = ix.d;
   a.S = ix.S;
   a.M = ix.M;
@@ -563,18 +655,15 @@ cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* 
   a.ef_p = p.ef_post;
   a.m = p.m;
   a.cand_cap = p.cand_cap;
-  a.ann_cap = p.ef > p.ef_post ? p.ef : p.ef_post;
-  if (a.ann_cap < p.k) a.ann_cap = p.k;
+  a.ann_cap = batch_ann_cap(p);
   a.vis_log2 = p.vis_log2;
   a.max_exp = p.max_exp;
   a.warp_bytes = batch_warp_bytes(a.cand_cap, a.ann_cap, a.vis_log2);
   a.o = o;
   const int wpb = p.warps_per_block;
-  const int ch = (a.dp4 + 31) / 32;
-  if (ch <= 1) return launch_t<1, 16>(a, wpb, ix.num_sms, st);
-  if (ch <= 2) return launch_t<2, 16>(a, wpb, ix.num_sms, st);
-  if (ch <= 4) return launch_t<4, 8>(a, wpb, ix.num_sms, st);
-  return launch_t<8, 8>(a, wpb, ix.num_sms, st);
+  if (p.dtype == UNIFY_BF16) return launch_dt<StoreBF16>(a, wpb, ix.num_sms, st);
+  if (p.dtype == UNIFY_FP8E4M3) return launch_dt<StoreFP8>(a, wpb, ix.num_sms, st);
+  return launch_dt<StoreF32>(a, wpb, ix.num_sms, st);
 }
 
 }  // namespace unify

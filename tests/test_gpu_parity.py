@@ -242,3 +242,71 @@ def test_bad_index_files_rejected(U, tmp_path):
         U.Index(bad)
     with pytest.raises(U.UnifyError):
         U.Index(str(tmp_path / "missing.idx"))
+
+
+def test_cuda_graph_plan_replays_search(U, c2_small_index):
+    w, path = c2_small_index
+    ix = U.Index(path)
+    ta, tb = w.n // 100, w.n // 2
+    p = U.Params.defaults(tau_a=ta, tau_b=tb)
+    nq = 200
+    plan = ix.plan(w.queries[:nq], w.lo[:nq], w.hi[:nq], w.k, ef=64, params=p)
+    for shift in (0, 100):
+        # update the captured input buffers in place, then replay
+        plan.q.copy_(torch.from_numpy(w.queries[shift:shift + nq]))
+        plan.lo.copy_(torch.from_numpy(w.lo[shift:shift + nq]))
+        plan.hi.copy_(torch.from_numpy(w.hi[shift:shift + nq]))
+        got = _np(plan.launch())
+        ref = _np(ix.search(w.queries[shift:shift + nq], w.lo[shift:shift + nq], w.hi[shift:shift + nq], w.k,
+                            ef=64, params=p))
+        assert np.array_equal(got["ids"], ref["ids"]) and np.array_equal(got["count"], ref["count"])
+        assert np.array_equal(got["dist"], ref["dist"])
+    # a search needing more scratch than the plan holds is refused while the plan lives
+    big = np.repeat(w.queries[:1], 300_000, axis=0)
+    with pytest.raises(U.UnifyError, match="plan"):
+        ix.search(big, np.zeros(len(big), np.int64), np.zeros(len(big), np.int64), w.k)
+    plan.close()
+    r = ix.search(big[:5000], np.zeros(5000, np.int64), np.zeros(5000, np.int64), w.k)
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("strategy", ["pre", "hybrid", "post", "auto"])
+def test_bf16_storage_lossless_on_integer_data(U, c2_small_index, strategy):
+    """Coordinates 0..255 are exact in bfloat16, so the BF16 traversal and scan see
+    the FP32 distances and the FP32 re-rank returns the FP32 path's rows exactly."""
+    w, path = c2_small_index
+    ix = U.Index(path)
+    ta, tb = w.n // 100, w.n // 2
+    base = dict(tau_a=ta, tau_b=tb, cand_cap=CAND)
+    for scan_rows in (8192, 96):
+        f32 = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=48, strategy=strategy,
+                            params=U.Params.defaults(scan_rows=scan_rows, **base)))
+        b16 = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=48, strategy=strategy,
+                            params=U.Params.defaults(dtype=U.BF16, rerank_mult=4, scan_rows=scan_rows, **base)))
+        for key in ("ids", "dist", "count", "status"):
+            assert np.array_equal(f32[key], b16[key]), (strategy, key)
+
+
+@pytest.mark.parametrize("dataset", ["c2_small_index", "c1_index"])
+def test_fp8_storage_rerank(U, dataset, request):
+    """FP8 E4M3 with a per-vector scale is lossy; after the FP32 re-rank every
+    returned distance is the float32 direct distance of that id (within 1e-5 of
+    FP64) and recall stays high."""
+    w, path = request.getfixturevalue(dataset)
+    ix = U.Index(path)
+    ta, tb = w.n // 100, w.n // 2
+    X = w.vectors.astype(np.float64)
+    ex = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, w.k)
+    for dtype in (U.FP8E4M3, U.BF16):
+        for strategy in ("pre", "auto"):
+            p = U.Params.defaults(dtype=dtype, rerank_mult=4, tau_a=ta, tau_b=tb, m=32, cand_cap=CAND)
+            r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=96, strategy=strategy, params=p))
+            _valid(w, r, w.lo, w.hi)
+            for i in range(len(w.lo)):
+                c = r["count"][i]
+                ids = r["ids"][i, :c]
+                d64 = ((X[ids] - w.queries[i].astype(np.float64)) ** 2).sum(1)
+                assert np.all(np.abs(r["dist"][i, :c] - d64) <= 1e-5 * np.maximum(d64, 1e-30))
+            rec = oracle.recall(r["ids"], ex[0], ex[2], w.k)
+            floor = 0.97 if strategy == "pre" else 0.85
+            assert rec.mean() >= floor, (dataset, dtype, strategy, rec.mean())
