@@ -310,6 +310,14 @@ def main():
         rec = autotune.recall_rows(out["ids"].cpu().numpy(), t_ids, t_cnt, k)
         counters = out["counters"].cpu().numpy().astype(np.int64)
         status = out["status"].cpu().numpy()
+        timeline = {}
+        for nm, sel in (("pre", isA), ("hybrid", isC), ("post", isB)):
+            if sel.any():
+                st_, en_ = counters[sel, 2], counters[sel, 3]
+                du = en_ - st_
+                timeline[nm] = {"queries": int(sel.sum()), "dur_us_p50": float(np.percentile(du, 50)),
+                                "dur_us_p99": float(np.percentile(du, 99)), "dur_us_max": int(du.max()),
+                                "last_end_us": int(en_.max()), "first_start_us": int(st_.min())}
         out = ix.search(q, lo, hi, k, strategy="auto", params=params)
         for _ in range(warmup):
             flush.fill_(1)
@@ -339,7 +347,7 @@ def main():
         parts = algorithmic_bytes(params, counters)
         alg = sum(parts.values())
         achieved = alg / (search_ms / 1000.0) / 1e9 if search_ms > 0 else 0.0
-        return dict(ms=ms_max, value=world * nq / (ms_max / 1000.0), out=out, wall=wall,
+        return dict(ms=ms_max, value=world * nq / (ms_max / 1000.0), out=out, wall=wall, timeline=timeline,
                     recall=autotune.group_recall(rec, w.fractions), status=status,
                     phases={ph: (v[0] / v[1] if v[1] else 0.0) for ph, v in phases.items()},
                     achieved=achieved, alg=alg, parts=parts)
@@ -432,12 +440,14 @@ def main():
                        "l2": "flushed between steps (256 MiB write), inputs 1.6 GB > L2",
                        "params": {"ef": params.ef, "ef_post": params.ef_post, "m": params.m,
                                   "cand_cap": params.cand_cap, "visited_cap": params.visited_cap,
-                                  "warps_per_block": params.warps_per_block, "tau_a": tau_a, "tau_b": tau_b}},
+                                  "warps_per_block": params.warps_per_block, "scan_rows": params.scan_rows,
+                                  "tau_a": tau_a, "tau_b": tau_b}},
             "recall_by_fraction": {f"{100 * f_:g}%": round(r_, 4) for f_, r_ in m32["recall"].items()},
             "routed": {"pre": int(isA.sum()), "hybrid": int(isC.sum()), "post": int(isB.sum())},
             "status_flagged": int(((m32["status"] & 3) != 0).sum()),
             "phase_ms_per_step": {ph: round(v, 4) for ph, v in m32["phases"].items() if not ph.startswith("unused")},
             "wall_s_timed_region": m32["wall"],
+            "timeline_us": m32["timeline"],
             "roofline": roofline,
             "precision": precision,
             "cuda_graph": {"ms_per_step": graph_ms, "value": world * nq / (graph_ms / 1000.0),

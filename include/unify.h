@@ -134,7 +134,9 @@ UNIFY_API int unify_route(unify_index_t* idx, const int64_t* lo, const int64_t* 
  *   out_ids    nq x k int64, device;  out_dist nq x k float32 (squared L2), device
  *   out_count  nq int32, device: number of valid results in the row
  *   out_status nq uint32 bit set of UNIFY_Q_*, device, may be NULL
- *   out_counters nq x 2 int32 (distance evaluations, expansions), device, may be NULL
+ *   out_counters nq x 4 int32, device, may be NULL: distance evaluations (rows scanned
+ *              for Strategy A), expansions, and the start and end of the query's work
+ *              in microseconds since the search kernel's first work unit started
  * The first call with a larger nq grows the index's scratch buffers (a device
  * allocation); make that call before capturing the stream into a CUDA graph. */
 UNIFY_API int unify_search(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi, int64_t nq,

@@ -160,7 +160,8 @@ class Index:
     def search(self, q, lo, hi, k: int, ef: int = 0, strategy="auto", params: Params | None = None,
                out=None, counters: bool = False):
         """Returns dict(ids int64 [nq,k], dist float32 [nq,k], count int32 [nq], status int32 [nq]
-        [, counters int32 [nq,2]]) as device tensors. ``out`` may pass preallocated tensors."""
+        [, counters int32 [nq,4]: distance evaluations, expansions, start and end in microseconds])
+        as device tensors. ``out`` may pass preallocated tensors."""
         torch = self._torch
         q = self._dev(q, torch.float32).reshape(-1, self.d)
         lo, hi = self._dev(lo, torch.int64), self._dev(hi, torch.int64)
@@ -174,7 +175,7 @@ class Index:
                        count=torch.empty(nq, dtype=torch.int32, device=self.device),
                        status=torch.empty(nq, dtype=torch.int32, device=self.device))
             if counters:
-                out["counters"] = torch.empty((nq, 2), dtype=torch.int32, device=self.device)
+                out["counters"] = torch.empty((nq, 4), dtype=torch.int32, device=self.device)
         p = ctypes.byref(params) if params is not None else None
         _check(lib().unify_search(self._h, _ptr(q), _ptr(lo), _ptr(hi), nq, k, ef, st, p, _ptr(out["ids"]),
                                   _ptr(out["dist"]), _ptr(out["count"]), _ptr(out.get("status")),

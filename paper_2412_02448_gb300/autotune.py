@@ -105,7 +105,9 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
     best = None
     for extra in ({"warps_per_block": 4}, {"warps_per_block": 2}, {"warps_per_block": 8},
                   {"warps_per_block": 4, "cand_cap": 256}, {"warps_per_block": 4, "cand_cap": 1024},
-                  {"warps_per_block": 4, "visited_cap": 1024}, {"warps_per_block": 4, "visited_cap": 4096}):
+                  {"warps_per_block": 4, "visited_cap": 1024}, {"warps_per_block": 4, "visited_cap": 4096},
+                  {"warps_per_block": 4, "scan_rows": 1024}, {"warps_per_block": 4, "scan_rows": 2048},
+                  {"warps_per_block": 4, "scan_rows": 4096}):
         try:
             p, ms, rec = run(dict(chosen, **extra))
         except U.UnifyError:

@@ -41,6 +41,26 @@ __device__ __forceinline__ uint64_t warp_sort_asc(uint64_t x) {
   return x;
 }
 
+// The same network carrying a 32-bit payload with each key.
+__device__ __forceinline__ void warp_sort_asc_payload(uint64_t& x, uint32_t& f) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint64_t y = __shfl_xor_sync(kFull, x, j);
+      const uint32_t g = __shfl_xor_sync(kFull, f, j);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool take = (lower == up) ? (y < x) : (x < y);
+      if (take) {
+        x = y;
+        f = g;
+      }
+    }
+  }
+}
+
 // First index i in a[0, n) with a[i] >= x (per lane).
 __device__ __forceinline__ int lower_bound_u64(const uint64_t* a, int n, uint64_t x) {
   int lo = 0, hi = n;

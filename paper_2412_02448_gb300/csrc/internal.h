@@ -81,6 +81,7 @@ enum {
   CNT_QA = 0, CNT_QC = 1, CNT_QB = 2,  // queue lengths
   CNT_ITEMS = 3,                       // scan work items
   CNT_TAKE = 4,                        // head of the combined work queue
+  CNT_T0 = 8,                          // counters[8..9]: 64-bit global-timer origin of the search kernel
   kNumCounters = 16
 };
 

@@ -100,8 +100,10 @@ __global__ void route_kernel(RouteArgs a, const int64_t* __restrict__ seg_bounds
     a.done[i] = 0;
     for (int t = 0; t < nb; ++t) a.items[base + t] = make_int2((int)i, t);
     if (a.out_counters) {
-      a.out_counters[2 * i] = (int32_t)Y;
-      a.out_counters[2 * i + 1] = 0;
+      a.out_counters[4 * i] = (int32_t)Y;
+      a.out_counters[4 * i + 1] = 0;
+      a.out_counters[4 * i + 2] = 0x7fffffff;  // earliest item start (atomicMin)
+      a.out_counters[4 * i + 3] = 0;           // latest item end (atomicMax)
     }
   }
 }

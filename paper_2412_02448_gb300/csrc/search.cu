@@ -91,9 +91,13 @@ struct WarpMem {
   int* slots;
 };
 
+__host__ __device__ inline int flag_cap(int cand_cap, int ann_cap) {
+  return ((cand_cap > ann_cap ? cand_cap : ann_cap) + 15) & ~15;
+}
+
 __host__ __device__ inline int batch_warp_bytes(int cand_cap, int ann_cap, int vis_log2) {
   int b = cand_cap * 8 + ann_cap * 8 + (4 << vis_log2);
-  b += (cand_cap + 15) & ~15;
+  b += flag_cap(cand_cap, ann_cap);
   b += 32 * 4 + 32 * 4 + 64 * 4;
   return (b + 15) & ~15;
 }
@@ -104,7 +108,7 @@ __device__ __forceinline__ WarpMem carve(unsigned char* base, const BatchArgs& a
   w.ann = w.E + a.cand_cap;
   w.vis = reinterpret_cast<int32_t*>(w.ann + a.ann_cap);
   w.Ef = reinterpret_cast<uint8_t*>(w.vis + (1 << a.vis_log2));
-  w.R = reinterpret_cast<int*>(w.Ef + ((a.cand_cap + 15) & ~15));
+  w.R = reinterpret_cast<int*>(w.Ef + flag_cap(a.cand_cap, a.ann_cap));
   w.clist = w.R + 32;
   w.slots = w.clist + 32;
   return w;
@@ -112,6 +116,21 @@ __device__ __forceinline__ WarpMem carve(unsigned char* base, const BatchArgs& a
 
 __device__ __forceinline__ uint32_t vis_hash(int id, int log2) {
   return ((uint32_t)id * 0x9E3779B1u) >> (32 - log2);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Microseconds since the first work unit of this launch started (instrumented runs).
+__device__ __forceinline__ int us_since_start(int32_t* counters) {
+  unsigned long long* t0 = reinterpret_cast<unsigned long long*>(counters + CNT_T0);
+  const unsigned long long now = global_ns();
+  unsigned long long base = atomicCAS(t0, 0ull, now);
+  if (base == 0ull) base = now;
+  return (int)((now - base) / 1000ull);
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -171,24 +190,30 @@ __device__ __forceinline__ int hybrid_slot(int ci, int per, uint32_t mask, int M
   return *seg * M + s;
 }
 
-// One layer of Algorithm 1 (post) or Algorithm 7 (hybrid). Returns |ann|.
+// One layer of Algorithm 1 (post) or Algorithm 7 (hybrid). Returns |ann|; the ann
+// array is w.ann for hybrid. For post every candidate push is also an ann push, so
+// cand is a subset of ann and one sorted buffer of capacity efl holds both: the
+// result is then in w.ann as well (the buffer is w.ann itself).
 template <class T, int CH, int G>
 __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (&q)[CH], bool hybrid, int l,
                             int efl, uint64_t ep_key, bool ep_in, uint32_t mask, uint32_t full_mask, int per,
                             int pa, int pb, int& n_dist, int& n_exp, uint32_t& status) {
   const int lane = lane_id();
   const int H = 1 << a.vis_log2;
+  uint64_t* E = hybrid ? w.E : w.ann;  // candidate buffer
+  const int capE = hybrid ? a.cand_cap : efl;
   for (int t = lane; t < H; t += 32) w.vis[t] = -1;
   __syncwarp();
   const int ep = key_id(ep_key);
   if (lane == 0) {
-    w.E[0] = ep_key;
+    E[0] = ep_key;
     w.Ef[0] = 0;
-    if (ep_in) w.ann[0] = ep_key;
+    if (hybrid && ep_in) w.ann[0] = ep_key;
     w.vis[vis_hash(ep, a.vis_log2)] = ep;
   }
   __syncwarp();
-  int nE = 1, nA = ep_in ? 1 : 0, cursor = 0, exp_l = 0;
+  int nE = 1, nA = hybrid ? (ep_in ? 1 : 0) : 1, cursor = 0, exp_l = 0;
+  bool truncated = false;
   const int Sp = __popc(mask);
   const int SM = a.S * a.M;
   for (;;) {
@@ -208,7 +233,7 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
       status |= UNIFY_Q_LIMIT;
       break;
     }
-    const int o = key_id(w.E[cursor]);
+    const int o = key_id(E[cursor]);
     __syncwarp();
     if (lane == 0) w.Ef[cursor] = 1;
     __syncwarp();
@@ -245,7 +270,7 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
       const int j = cursor + 1 + lane;
       const unsigned bal = __ballot_sync(kFull, j < nE && w.Ef[j] == 0);
       if (bal) {
-        const int o2 = key_id(w.E[cursor + __ffs(bal)]);
+        const int o2 = key_id(E[cursor + __ffs(bal)]);
         const int32_t* adj2 = a.adj0 + (int64_t)o2 * SM;
         if (hybrid) {
           if (lane < ncand) {
@@ -287,25 +312,41 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
       const bool inr = need ? (pv >= pa && pv < pb) : true;
       n_dist += __popc(__ballot_sync(kFull, cid >= 0));
       const uint64_t key = cid >= 0 ? make_key(dist, cid) : kKeyMax;
-      const uint64_t thr = nA >= efl ? w.ann[efl - 1] : kKeyMax;
+      const uint64_t thr = nA >= efl ? (hybrid ? w.ann[efl - 1] : E[efl - 1]) : kKeyMax;
       bool keep = cid >= 0 && key < thr;
-      if (keep && (contains_u64(w.E, nE, key) || contains_u64(w.ann, nA, key))) keep = false;
+      // a visited object the filter forgot is still in E (or, after an overflow of
+      // E, possibly only in ann): drop it
+      if (keep && contains_u64(E, nE, key)) keep = false;
+      if (keep && hybrid && truncated && contains_u64(w.ann, nA, key)) keep = false;
       const unsigned kb = __ballot_sync(kFull, keep);
       if (kb == 0) continue;
       int r0;
       bool dropped;
-      const uint64_t sk = warp_sort_asc(keep ? key : kKeyMax);
-      nE = warp_merge(w.E, w.Ef, nE, a.cand_cap, sk, __popc(kb), w.R, &r0, &dropped);
-      if (dropped) status |= UNIFY_Q_TRUNCATED;
+      uint64_t sk = keep ? key : kKeyMax;
+      uint32_t fl = (keep && inr) ? 1u : 0u;
+      warp_sort_asc_payload(sk, fl);
+      const int nk = __popc(kb);
+      nE = warp_merge(E, w.Ef, nE, capE, sk, nk, w.R, &r0, &dropped);
       if (r0 < cursor) cursor = r0;
-      const bool ka = keep && inr;
-      const unsigned ab = __ballot_sync(kFull, ka);
+      if (!hybrid) {
+        nA = nE;  // cand and ann share the buffer; dropping beyond ef is ann's pop
+        if (cursor > nE) cursor = nE;
+        continue;
+      }
+      if (dropped) {
+        truncated = true;
+        status |= UNIFY_Q_TRUNCATED;
+      }
+      // in-range keys of the sorted batch, compacted in order
+      const unsigned ab = __ballot_sync(kFull, lane < nk && fl != 0u);
       if (ab) {
-        const uint64_t sa = warp_sort_asc(ka ? key : kKeyMax);
-        nA = warp_merge(w.ann, nullptr, nA, efl, sa, __popc(ab), w.R, &r0, &dropped);
+        const int na = __popc(ab);
+        const int src = lane < na ? (int)__fns(ab, 0, lane + 1) : 0;
+        const uint64_t v = __shfl_sync(kFull, sk, src);
+        nA = warp_merge(w.ann, nullptr, nA, efl, lane < na ? v : kKeyMax, na, w.R, &r0, &dropped);
       }
       if (nA >= efl) {
-        nE = upper_bound_u64(w.E, nE, w.ann[efl - 1]);
+        nE = upper_bound_u64(E, nE, w.ann[efl - 1]);
         if (cursor > nE) cursor = nE;
       }
     }
@@ -348,6 +389,8 @@ __device__ int rerank_write(const BatchArgs& a, const WarpMem& w, const float4 (
 template <class T, int CH, int G>
 __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool hybrid) {
   const int lane = lane_id();
+  int t_start = 0;
+  if (a.o.counters && lane == 0) t_start = us_since_start(a.counters);
   const uint32_t mask = a.mask[qi];
   const int pa = a.pa[qi], pb = a.pb[qi];
   uint32_t status = 0;
@@ -448,8 +491,10 @@ __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool h
     a.o.count[qi] = cnt;
     if (a.o.status) a.o.status[qi] = status;
     if (a.o.counters) {
-      a.o.counters[2 * (int64_t)qi] = n_dist;
-      a.o.counters[2 * (int64_t)qi + 1] = n_exp;
+      a.o.counters[4 * (int64_t)qi] = n_dist;
+      a.o.counters[4 * (int64_t)qi + 1] = n_exp;
+      a.o.counters[4 * (int64_t)qi + 2] = t_start;
+      a.o.counters[4 * (int64_t)qi + 3] = us_since_start(a.counters);
     }
   }
   __syncwarp();
@@ -462,6 +507,7 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
   const int kk = a.rerank > 0 ? a.rerank : a.k;  // keys kept per list
   const int2 item = a.items[it];
   const int qi = item.x, b = item.y;
+  if (a.o.counters && lane == 0) atomicMin(&a.o.counters[4 * (int64_t)qi + 2], us_since_start(a.counters));
   const int pa = a.pa[qi], pb = a.pb[qi], nb = a.nblk[qi];
   const int Y = pb - pa;
   const int rpb = (Y + nb - 1) / (nb > 0 ? nb : 1);
@@ -517,7 +563,10 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
     int prev = 0;
     if (lane == 0) prev = atomicAdd(&a.done[qi], 1);
     prev = __shfl_sync(kFull, prev, 0);
-    if (prev != nb - 1) return;
+    if (prev != nb - 1) {
+      if (a.o.counters && lane == 0) atomicMax(&a.o.counters[4 * (int64_t)qi + 3], us_since_start(a.counters));
+      return;
+    }
     __threadfence();
     const uint64_t* src = a.part + (int64_t)a.qbase[qi] * kk;
     const int total = nb * kk;
@@ -540,6 +589,7 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
   if (lane == 0) {
     a.o.count[qi] = cnt;
     if (a.o.status) a.o.status[qi] = 0u;
+    if (a.o.counters) atomicMax(&a.o.counters[4 * (int64_t)qi + 3], us_since_start(a.counters));
   }
   __syncwarp();
 }
