@@ -212,6 +212,9 @@ def main():
     ap.add_argument("--cand-cap", type=int, default=512)
     ap.add_argument("--visited-cap", type=int, default=2048)
     ap.add_argument("--warps-per-block", type=int, default=4)
+    ap.add_argument("--tau-a", type=int, default=-1)
+    ap.add_argument("--tau-b", type=int, default=-1)
+    ap.add_argument("--scan-rows", type=int, default=8192)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the BF16/FP8 lines")
@@ -277,15 +280,24 @@ def main():
     torch.cuda.synchronize()
     t_ids, t_cnt = truth["ids"].cpu().numpy(), truth["count"].cpu().numpy()
 
-    base = U.Params.defaults(tau_a=tau_a, tau_b=tau_b, ef=args.ef, ef_post=args.ef_post or args.ef, m=args.m,
+    if args.tau_a >= 0:
+        tau_a = args.tau_a
+    if args.tau_b >= 0:
+        tau_b = args.tau_b
+    base = U.Params.defaults(tau_a=tau_a, tau_b=tau_b, scan_rows=args.scan_rows, ef=args.ef, ef_post=args.ef_post or args.ef, m=args.m,
                              cand_cap=args.cand_cap, visited_cap=args.visited_cap,
                              warps_per_block=args.warps_per_block)
     route = ix.route(lo, hi, tau_a, tau_b)
-    strat = route["strategy"].cpu().numpy()
     pa, pb = route["pa"].cpu().numpy().astype(np.int64), route["pb"].cpu().numpy().astype(np.int64)
     mask = route["mask"].cpu().numpy().astype(np.uint32)
-    isA, isC, isB = strat == 0, strat == 1, strat == 2
     Sp = np.array([bin(int(m_)).count("1") for m_ in mask])
+    Y = pb - pa
+    routing = {}
+
+    def set_routing(params):
+        a_ = Y <= params.tau_a
+        b_ = (~a_) & (Y >= params.tau_b)
+        routing.update(isA=a_, isB=b_, isC=~(a_ | b_))
     hbm, peak_kind = peaks()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -293,6 +305,7 @@ def main():
 
     def algorithmic_bytes(params, counters):
         """Bytes the search kernel must move per launch (kernels)."""
+        isA, isB, isC = routing["isA"], routing["isB"], routing["isC"]
         row = {U.FP32: 4 * d, U.BF16: 2 * d, U.FP8E4M3: d + 4}[params.dtype]
         per = np.minimum(ix.M, -(-params.m // np.maximum(Sp, 1)))
         rr = 0 if params.dtype == U.FP32 else params.rerank_mult * k * 4 * d
@@ -305,6 +318,8 @@ def main():
         return parts
 
     def measure(params, steps, warmup):
+        set_routing(params)
+        isA, isB, isC = routing["isA"], routing["isB"], routing["isC"]
         out = ix.search(q, lo, hi, k, strategy="auto", params=params, counters=True)
         torch.cuda.synchronize()
         rec = autotune.recall_rows(out["ids"].cpu().numpy(), t_ids, t_cnt, k)
@@ -315,9 +330,16 @@ def main():
             if sel.any():
                 st_, en_ = counters[sel, 2], counters[sel, 3]
                 du = en_ - st_
+                idxs = np.flatnonzero(sel)
+                slow = idxs[np.argsort(du)[-3:][::-1]]
                 timeline[nm] = {"queries": int(sel.sum()), "dur_us_p50": float(np.percentile(du, 50)),
                                 "dur_us_p99": float(np.percentile(du, 99)), "dur_us_max": int(du.max()),
-                                "last_end_us": int(en_.max()), "first_start_us": int(st_.min())}
+                                "last_end_us": int(en_.max()), "first_start_us": int(st_.min()),
+                                "slowest": [{"frac": float(w.fractions[i_]), "Y": int(pb[i_] - pa[i_]),
+                                             "segments": int(Sp[i_]), "n_exp": int(counters[i_, 1]),
+                                             "n_dist": int(counters[i_, 0]),
+                                             "us": int(counters[i_, 3] - counters[i_, 2]),
+                                             "status": int(status[i_])} for i_ in slow]}
         out = ix.search(q, lo, hi, k, strategy="auto", params=params)
         for _ in range(warmup):
             flush.fill_(1)
@@ -348,6 +370,7 @@ def main():
         alg = sum(parts.values())
         achieved = alg / (search_ms / 1000.0) / 1e9 if search_ms > 0 else 0.0
         return dict(ms=ms_max, value=world * nq / (ms_max / 1000.0), out=out, wall=wall, timeline=timeline,
+                    routed=(isA.sum(), isC.sum(), isB.sum()),
                     recall=autotune.group_recall(rec, w.fractions), status=status,
                     phases={ph: (v[0] / v[1] if v[1] else 0.0) for ph, v in phases.items()},
                     achieved=achieved, alg=alg, parts=parts)
@@ -441,9 +464,9 @@ def main():
                        "params": {"ef": params.ef, "ef_post": params.ef_post, "m": params.m,
                                   "cand_cap": params.cand_cap, "visited_cap": params.visited_cap,
                                   "warps_per_block": params.warps_per_block, "scan_rows": params.scan_rows,
-                                  "tau_a": tau_a, "tau_b": tau_b}},
+                                  "tau_a": params.tau_a, "tau_b": params.tau_b}},
             "recall_by_fraction": {f"{100 * f_:g}%": round(r_, 4) for f_, r_ in m32["recall"].items()},
-            "routed": {"pre": int(isA.sum()), "hybrid": int(isC.sum()), "post": int(isB.sum())},
+            "routed": {"pre": int(m32["routed"][0]), "hybrid": int(m32["routed"][1]), "post": int(m32["routed"][2])},
             "status_flagged": int(((m32["status"] & 3) != 0).sum()),
             "phase_ms_per_step": {ph: round(v, 4) for ph, v in m32["phases"].items() if not ph.startswith("unused")},
             "wall_s_timed_region": m32["wall"],

@@ -50,77 +50,113 @@ def _time_search(index, q, lo, hi, k, params, reps, torch, strategy="auto"):
 
 
 def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=None,
-         efs=(16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512), ms_=(16, 24, 32, 48, 64), reps=3, log=None):
+         efs=(16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512), ms_=(16, 24, 32, 48, 64), reps=3, log=None,
+         calibrate_tau=True, tau_a_fracs=(0.01, 0.015, 0.02, 0.03, 0.05, 0.08),
+         tau_b_fracs=(0.3, 0.4, 0.5, 0.6, 0.75)):
     """Returns (Params, report). q/lo/hi are device tensors; truth_* and groups numpy.
 
-    Hybrid (C): for every selection width m (Section 4.2, the paper's m), the
-    smallest ef meeting the target on the C-routed queries of every group; the
-    fastest (m, ef) pair wins. Post-filter (B): the smallest ef_post meeting the
-    target on the B-routed queries. Then the CTA shape and buffer sizes."""
+    1. Beam widths under the router of ``base``: the smallest ef_post meeting the
+       target on the B-routed queries of every group; for every selection width m
+       (the paper's m) the smallest ef meeting it on the C-routed queries; the
+       fastest (m, ef) pair wins.
+    2. Range-aware thresholds (Section 4.2: tau_A and tau_B derived from sample
+       queries run under the strategies): the (tau_A, tau_B) pair with the fastest
+       batch whose recall meets the target in every group; then step 1 again under
+       the new router.
+    3. CTA shape, buffer sizes and scan work-item size."""
     import torch
 
     import paper_2412_02448_gb300 as U
 
     base = base or U.Params.defaults()
-    strat = index.route(lo, hi, base.tau_a, base.tau_b)["strategy"].cpu().numpy()
     report = {"trials": []}
+    n = index.n
 
-    def run(extra):
-        p = U.Params.defaults(**{f: getattr(base, f) for f, _ in U.Params._fields_})
+    def make(extra, ref=None):
+        ref = ref if ref is not None else base
+        p = U.Params.defaults(**{f: getattr(ref, f) for f, _ in U.Params._fields_})
         for kk, v in extra.items():
             setattr(p, kk, v)
         if max(p.ef, p.ef_post) > p.cand_cap // 2:
             p.cand_cap = min(4096, 2 * max(p.ef, p.ef_post))
+        return p
+
+    def run(p):
         ms, out = _time_search(index, q, lo, hi, k, p, reps, torch)
         ids = out["ids"].cpu().numpy()
-        return p, ms, recall_rows(ids, truth_ids, truth_count, k)
+        return ms, recall_rows(ids, truth_ids, truth_count, k)
 
-    def smallest_ef(sel, fixed, field):
-        for ef in efs:
-            if ef < k:
-                continue
-            p, ms, rec = run(dict(fixed, **{field: ef}))
-            gr = group_recall(rec, groups, sel)
-            report["trials"].append({"params": dict(fixed, **{field: ef}), "ms": ms, "recall": gr})
-            if log:
-                log(f"tune {dict(fixed, **{field: ef})}: {ms:.3f} ms/batch, recall {gr}")
-            if min(gr.values()) >= target:
-                return ef, ms
-        return None, None
+    def note(p, ms, gr, what):
+        report["trials"].append({"what": what, "ef": p.ef, "ef_post": p.ef_post, "m": p.m,
+                                 "tau_a": p.tau_a, "tau_b": p.tau_b, "ms": ms, "recall": gr})
+        if log:
+            log(f"tune {what} ef={p.ef} ef_post={p.ef_post} m={p.m} tau=({p.tau_a},{p.tau_b}): "
+                f"{ms:.3f} ms/batch, recall {gr}")
 
-    chosen = {"ef": efs[0], "ef_post": efs[0], "m": base.m}
-    selB, selC = strat == U.POST, strat == U.HYBRID
-    if selB.any():
-        ef, _ = smallest_ef(selB, {"ef": efs[0]}, "ef_post")
-        chosen["ef_post"] = ef if ef is not None else efs[-1]
-    if selC.any():
-        best_c = None
-        for m in ms_:
-            ef, ms = smallest_ef(selC, {"m": m, "ef_post": chosen["ef_post"]}, "ef")
-            if ef is not None and (best_c is None or ms < best_c[2]):
-                best_c = (m, ef, ms)
-        if best_c is None:
-            best_c = (ms_[-1], efs[-1], None)
-        chosen["m"], chosen["ef"] = best_c[0], best_c[1]
+    def beams(ref):
+        strat = index.route(lo, hi, ref.tau_a, ref.tau_b)["strategy"].cpu().numpy()
+        chosen = {"ef": ref.ef, "ef_post": ref.ef_post, "m": ref.m}
+        selB, selC = strat == U.POST, strat == U.HYBRID
+        if selB.any():
+            chosen["ef_post"] = efs[-1]
+            for ef in efs:
+                if ef < k:
+                    continue
+                p = make(dict(chosen, ef_post=ef), ref)
+                ms, rec = run(p)
+                gr = group_recall(rec, groups, selB)
+                note(p, ms, gr, "ef_post")
+                if min(gr.values()) >= target:
+                    chosen["ef_post"] = ef
+                    break
+        if selC.any():
+            best_c = None
+            for m in ms_:
+                for ef in efs:
+                    if ef < k:
+                        continue
+                    p = make(dict(chosen, m=m, ef=ef), ref)
+                    ms, rec = run(p)
+                    gr = group_recall(rec, groups, selC)
+                    note(p, ms, gr, "hybrid")
+                    if min(gr.values()) >= target:
+                        if best_c is None or ms < best_c[2]:
+                            best_c = (m, ef, ms)
+                        break
+            if best_c is None:
+                best_c = (ms_[-1], efs[-1], None)
+            chosen["m"], chosen["ef"] = best_c[0], best_c[1]
+        return make(chosen, ref)
+
+    cur = beams(base)
+    if calibrate_tau:
+        best = None
+        for fa in tau_a_fracs:
+            for fb in tau_b_fracs:
+                p = make({"tau_a": int(fa * n), "tau_b": int(fb * n)}, cur)
+                ms, rec = run(p)
+                gr = group_recall(rec, groups)
+                note(p, ms, gr, "tau")
+                if min(gr.values()) >= target and (best is None or ms < best[1]):
+                    best = (p, ms)
+        if best is not None:
+            cur = beams(best[0])
     best = None
-    for extra in ({"warps_per_block": 4}, {"warps_per_block": 2}, {"warps_per_block": 8},
-                  {"warps_per_block": 4, "cand_cap": 256}, {"warps_per_block": 4, "cand_cap": 1024},
-                  {"warps_per_block": 4, "visited_cap": 1024}, {"warps_per_block": 4, "visited_cap": 4096},
-                  {"warps_per_block": 4, "scan_rows": 1024}, {"warps_per_block": 4, "scan_rows": 2048},
-                  {"warps_per_block": 4, "scan_rows": 4096}):
+    for extra in ({}, {"warps_per_block": 2}, {"warps_per_block": 8}, {"cand_cap": 256}, {"cand_cap": 1024},
+                  {"visited_cap": 1024}, {"visited_cap": 4096}, {"scan_rows": 1024}, {"scan_rows": 2048},
+                  {"scan_rows": 4096}):
+        p = make(extra, cur)
         try:
-            p, ms, rec = run(dict(chosen, **extra))
+            ms, rec = run(p)
         except U.UnifyError:
             continue
         gr = group_recall(rec, groups)
-        report["trials"].append({"params": dict(chosen, **extra), "ms": ms, "recall": gr})
-        if log:
-            log(f"tune shape {dict(chosen, **extra)}: {ms:.3f} ms/batch, recall {gr}")
+        note(p, ms, gr, f"shape {extra}")
         if min(gr.values()) >= target and (best is None or ms < best[1]):
             best = (p, ms, gr)
     if best is None:
-        p, ms, rec = run(chosen)
-        best = (p, ms, group_recall(rec, groups))
+        ms, rec = run(cur)
+        best = (cur, ms, group_recall(rec, groups))
     report["chosen"] = {f: getattr(best[0], f) for f, _ in U.Params._fields_}
     report["ms"] = best[1]
     report["recall"] = best[2]
