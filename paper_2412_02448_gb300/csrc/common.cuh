@@ -138,7 +138,7 @@ __device__ __forceinline__ int warp_merge(uint64_t* arr, uint8_t* flags, int n, 
   return (n + nb) < cap ? (n + nb) : cap;
 }
 
-// Transposed warp reduction of V partial values per lane (V in {8, 16, 32}).
+// Transposed warp reduction of V partial values per lane (V in {2, 4, 8, 16, 32}).
 // Afterwards the lanes whose index >> log2(32/V) equals u hold the sum over all
 // 32 lanes of value u. Every value is summed by the same tree (pairs across lane
 // bit 4, then bit 3, ..., bit 0), so a vector's distance does not depend on the

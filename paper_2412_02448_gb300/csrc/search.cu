@@ -149,28 +149,52 @@ __device__ __forceinline__ void write_row(const uint64_t* keys, int cnt, int k, 
 
 // Distances of the candidates held by the lanes (cid >= 0), G at a time, from
 // rows of `rows` (row_bytes each) in storage format T (scale: FP8 scales or null).
+// All G row loads of a group are issued before any of them is used (slots past
+// the last candidate reload the last candidate's row and are discarded), so a
+// group costs one memory latency, not G.
 template <class T, int CH, int G>
 __device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, const unsigned char* rows,
                                             int row_bytes, const float* scale, int dp4, int* clist) {
+  const int lane = lane_id();
   const unsigned vm = __ballot_sync(kFull, cid >= 0);
   const int nv = __popc(vm);
   const int my = __popc(vm & lanemask_lt());
   if (cid >= 0) clist[my] = cid;
   __syncwarp();
-  constexpr int SH = (G == 8) ? 2 : (G == 16 ? 1 : 0);
+  constexpr int SH = (G == 32) ? 0 : (G == 16) ? 1 : (G == 8) ? 2 : (G == 4) ? 3 : 4;  // log2(32 / G)
   float result = 0.f;
   for (int g = 0; g * G < nv; ++g) {
-    float part[G];
+    int ids[G];
 #pragma unroll
     for (int u = 0; u < G; ++u) {
       const int c = g * G + u;
-      if (c < nv) {
-        const int id = clist[c];
-        const float sc = scale ? __ldg(scale + id) : 1.f;
-        part[u] = l2_partial_t<T, CH>(q, rows + (int64_t)id * row_bytes, dp4, sc);
-      } else {
-        part[u] = 0.f;
+      ids[u] = clist[c < nv ? c : nv - 1];
+    }
+    float4 x[G][CH];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const unsigned char* row = rows + (int64_t)ids[u] * row_bytes;
+      const float sc = scale ? __ldg(scale + ids[u]) : 1.f;
+#pragma unroll
+      for (int t = 0; t < CH; ++t) {
+        const int c = lane + 32 * t;
+        x[u][t] = c < dp4 ? T::load(row, c, sc) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
+    }
+    float part[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      float s = 0.f;
+#pragma unroll
+      for (int t = 0; t < CH; ++t) {
+        const float e0 = q[t].x - x[u][t].x, e1 = q[t].y - x[u][t].y;
+        const float e2 = q[t].z - x[u][t].z, e3 = q[t].w - x[u][t].w;
+        s = fmaf(e0, e0, s);
+        s = fmaf(e1, e1, s);
+        s = fmaf(e2, e2, s);
+        s = fmaf(e3, e3, s);
+      }
+      part[u] = (g * G + u < nv) ? s : 0.f;
     }
     const float red = warp_transpose_reduce<G>(part);
     const int u = my - g * G;
@@ -595,7 +619,7 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
 }
 
 template <class T, int CH, int G>
-__global__ void __launch_bounds__(256) batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const WarpMem w = carve(smem_raw + (size_t)warp * a.warp_bytes, a);
@@ -633,11 +657,12 @@ static cudaError_t launch_t(const BatchArgs& a, int wpb, int num_sms, cudaStream
 
 template <class T>
 static cudaError_t launch_dt(const BatchArgs& a, int wpb, int num_sms, cudaStream_t st) {
+  // G candidates per distance group: G * CH = 16 row chunks (64 registers) in flight
   const int ch = (a.dp4 + 31) / 32;
   if (ch <= 1) return launch_t<T, 1, 16>(a, wpb, num_sms, st);
-  if (ch <= 2) return launch_t<T, 2, 16>(a, wpb, num_sms, st);
-  if (ch <= 4) return launch_t<T, 4, 8>(a, wpb, num_sms, st);
-  return launch_t<T, 8, 8>(a, wpb, num_sms, st);
+  if (ch <= 2) return launch_t<T, 2, 8>(a, wpb, num_sms, st);
+  if (ch <= 4) return launch_t<T, 4, 4>(a, wpb, num_sms, st);
+  return launch_t<T, 8, 2>(a, wpb, num_sms, st);
 }
 
 int rerank_count(const Params& p) { return p.dtype == UNIFY_FP32 ? 0 : p.rerank_mult * p.k; }
