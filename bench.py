@@ -62,7 +62,7 @@ def cache_dir():
 
 def get_index(w, rank, world, barrier):
     import hsig_build
-    path = os.path.join(cache_dir(), f"{w.name}_n{w.n}_s{w.seed}_{hsig_build.source_digest()}.idx")
+    path = hsig_build.cached_index_path(cache_dir(), w.name, w.n, w.seed)
     if rank == 0 and not os.path.exists(path):
         t = time.time()
         hsig_build.build_index(w.vectors, w.attrs, path, w.S, w.M, w.efc, seed=w.seed)
@@ -215,6 +215,7 @@ def main():
     ap.add_argument("--tau-a", type=int, default=-1)
     ap.add_argument("--tau-b", type=int, default=-1)
     ap.add_argument("--scan-rows", type=int, default=8192)
+    ap.add_argument("--reg-budget", type=int, default=128)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the BF16/FP8 lines")
@@ -247,7 +248,7 @@ def main():
         __graft_entry__.build()
     barrier()
     import paper_2412_02448_gb300 as U
-    from paper_2412_02448_gb300 import autotune
+    from paper_2412_02448_gb300 import autotune, replicas
     from workloads import make_workload
 
     over = {}
@@ -258,13 +259,8 @@ def main():
     w0 = make_workload("c2", seed=args.seed, **over)
     path = get_index(w0, rank, world, barrier)
     # weak scaling: every rank searches its own batch of the same shape
-    if rank == 0:
-        w = w0
-    else:
-        w = make_workload("c2", seed=args.seed, **over)
-        rng = np.random.default_rng([args.seed, 100 + rank])
-        perm = rng.permutation(len(w.lo))
-        w.queries, w.lo, w.hi, w.fractions = w.queries[perm], w.lo[perm], w.hi[perm], w.fractions[perm]
+    w = w0
+    w.queries, w.lo, w.hi, w.fractions = replicas.rank_batch(w.queries, w.lo, w.hi, w.fractions, rank, args.seed)
     ix = U.Index(path, device=local)
     dev = torch.device("cuda", local)
     q = torch.from_numpy(w.queries).to(dev)
@@ -286,7 +282,7 @@ def main():
         tau_b = args.tau_b
     base = U.Params.defaults(tau_a=tau_a, tau_b=tau_b, scan_rows=args.scan_rows, ef=args.ef, ef_post=args.ef_post or args.ef, m=args.m,
                              cand_cap=args.cand_cap, visited_cap=args.visited_cap,
-                             warps_per_block=args.warps_per_block)
+                             warps_per_block=args.warps_per_block, reg_budget=args.reg_budget)
     route = ix.route(lo, hi, tau_a, tau_b)
     pa, pb = route["pa"].cpu().numpy().astype(np.int64), route["pb"].cpu().numpy().astype(np.int64)
     mask = route["mask"].cpu().numpy().astype(np.uint32)
@@ -361,15 +357,12 @@ def main():
         ix.timing(False)
         phases = ix.collect_timing()
         ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in evs]))
-        t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-        ms_max = float(t_local.item())
+        ms_max = replicas.max_over_ranks(ms, world, dev)
         search_ms = phases["search"][0] / max(1, phases["search"][1])
         parts = algorithmic_bytes(params, counters)
         alg = sum(parts.values())
         achieved = alg / (search_ms / 1000.0) / 1e9 if search_ms > 0 else 0.0
-        return dict(ms=ms_max, value=world * nq / (ms_max / 1000.0), out=out, wall=wall, timeline=timeline,
+        return dict(ms=ms_max, value=replicas.aggregate_qps(nq, world, ms_max), out=out, wall=wall, timeline=timeline,
                     routed=(isA.sum(), isC.sum(), isB.sum()),
                     recall=autotune.group_recall(rec, w.fractions), status=status,
                     phases={ph: (v[0] / v[1] if v[1] else 0.0) for ph, v in phases.items()},
@@ -442,10 +435,7 @@ def main():
     for _ in range(e2e_steps):
         ix.search_auto_host(hq, hlo, hhi, k, params=params, out=hout)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    t_e2e = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_value = world * nq / float(t_e2e.item())
+    e2e_value = replicas.aggregate_qps(nq, world, 1000.0 * replicas.max_over_ranks(e2e_s, world, dev))
     h2d = nq * w.d * 4 + 2 * nq * 8
     d2h = nq * k * (8 + 4) + nq * 4 + nq * 4
 
@@ -464,6 +454,7 @@ def main():
                        "params": {"ef": params.ef, "ef_post": params.ef_post, "m": params.m,
                                   "cand_cap": params.cand_cap, "visited_cap": params.visited_cap,
                                   "warps_per_block": params.warps_per_block, "scan_rows": params.scan_rows,
+                                  "reg_budget": params.reg_budget,
                                   "tau_a": params.tau_a, "tau_b": params.tau_b}},
             "recall_by_fraction": {f"{100 * f_:g}%": round(r_, 4) for f_, r_ in m32["recall"].items()},
             "routed": {"pre": int(m32["routed"][0]), "hybrid": int(m32["routed"][1]), "post": int(m32["routed"][2])},

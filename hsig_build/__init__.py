@@ -30,6 +30,12 @@ def source_digest() -> str:
         return hashlib.sha1(f.read()).hexdigest()[:10]
 
 
+def cached_index_path(cache_dir: str, name: str, n: int, seed: int) -> str:
+    """File name under cache_dir for the index of a seeded workload (shared by the
+    benchmark and the full-size tests so one build serves both)."""
+    return os.path.join(cache_dir, f"{name}_n{n}_s{seed}_{source_digest()}.idx")
+
+
 def compile(force: bool = False) -> str:
     """Compile the builder into hsig_build/libhsig_build.so (skipped when current)."""
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):

@@ -91,8 +91,12 @@ typedef struct {
   int cand_cap;        /* candidate buffer entries per query, default 512 (<= 4096) */
   int visited_cap;     /* visited-filter slots per query, power of two, default 2048 */
   int max_expansions;  /* expansions per layer before UNIFY_Q_LIMIT, default 100000 */
-  int warps_per_block; /* graph-search warps per CTA, default 4 */
+  int warps_per_block; /* search warps per CTA (one query or scan item each), 1..4, default 4 */
   int scan_rows;       /* pre-filter rows per scan work item, default 8192 */
+  int reg_budget;      /* registers per thread of the search kernel: 128 (16 warps per SM),
+                          80 (24 warps) or 64 (32 warps, smaller distance groups); default 128.
+                          More resident warps hide more memory latency when shared memory
+                          (cand_cap, visited_cap, ef) also fits. */
 } unify_params_t;
 
 /* Fills *p with the defaults above. */

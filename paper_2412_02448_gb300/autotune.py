@@ -142,9 +142,12 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
         if best is not None:
             cur = beams(best[0])
     best = None
-    for extra in ({}, {"warps_per_block": 2}, {"warps_per_block": 8}, {"cand_cap": 256}, {"cand_cap": 1024},
+    for extra in ({}, {"warps_per_block": 2}, {"cand_cap": 256}, {"cand_cap": 1024},
                   {"visited_cap": 1024}, {"visited_cap": 4096}, {"scan_rows": 1024}, {"scan_rows": 2048},
-                  {"scan_rows": 4096}):
+                  {"scan_rows": 4096}, {"reg_budget": 80, "visited_cap": 1024},
+                  {"reg_budget": 80, "visited_cap": 1024, "cand_cap": 256},
+                  {"reg_budget": 64, "visited_cap": 512, "cand_cap": 256},
+                  {"reg_budget": 64, "visited_cap": 1024, "cand_cap": 128}):
         p = make(extra, cur)
         try:
             ms, rec = run(p)

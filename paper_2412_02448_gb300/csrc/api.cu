@@ -125,6 +125,7 @@ int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Para
   p.max_exp = d.max_expansions;
   p.warps_per_block = d.warps_per_block;
   p.scan_rows = d.scan_rows;
+  p.reg_budget = d.reg_budget;
   p.dtype = d.dtype;
   p.rerank_mult = d.rerank_mult;
   p.tau_a = d.tau_a >= 0 ? d.tau_a : ix.n / 100;
@@ -137,7 +138,9 @@ int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Para
   p.vis_log2 = 0;
   while ((1 << p.vis_log2) < d.visited_cap) ++p.vis_log2;
   if (p.max_exp < 1) return fail(UNIFY_E_ARG, "max_expansions must be >= 1");
-  if (p.warps_per_block < 1 || p.warps_per_block > 8) return fail(UNIFY_E_ARG, "warps_per_block must be in [1, 8]");
+  if (p.warps_per_block < 1 || p.warps_per_block > 4) return fail(UNIFY_E_ARG, "warps_per_block must be in [1, 4]");
+  if (p.reg_budget != 128 && p.reg_budget != 80 && p.reg_budget != 64)
+    return fail(UNIFY_E_ARG, "reg_budget must be 128, 80 or 64");
   if (p.scan_rows < 32) return fail(UNIFY_E_ARG, "scan_rows must be >= 32");
   if (p.dtype != UNIFY_FP32 && p.dtype != UNIFY_BF16 && p.dtype != UNIFY_FP8E4M3)
     return fail(UNIFY_E_ARG, "dtype must be UNIFY_FP32, UNIFY_BF16 or UNIFY_FP8E4M3");
@@ -253,6 +256,7 @@ extern "C" void unify_default_params(unify_params_t* p) {
   p->max_expansions = 100000;
   p->warps_per_block = 4;
   p->scan_rows = 8192;
+  p->reg_budget = 128;
 }
 
 extern "C" const char* unify_last_error(void) { return g_last_error.c_str(); }

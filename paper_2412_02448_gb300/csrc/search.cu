@@ -618,8 +618,10 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
   __syncwarp();
 }
 
-template <class T, int CH, int G>
-__global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs a) {
+// MINB: minimum resident CTAs of 128 threads per SM the register allocation must
+// allow (4 -> 128 registers, 6 -> 80, 8 -> 64).
+template <class T, int CH, int G, int MINB>
+__global__ void __launch_bounds__(128, MINB) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const WarpMem w = carve(smem_raw + (size_t)warp * a.warp_bytes, a);
@@ -640,29 +642,34 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs a) {
   }
 }
 
-template <class T, int CH, int G>
+template <class T, int CH, int G, int MINB>
 static cudaError_t launch_t(const BatchArgs& a, int wpb, int num_sms, cudaStream_t st) {
   const int threads = 32 * wpb;
   const size_t smem = (size_t)wpb * a.warp_bytes;
-  cudaError_t e =
-      cudaFuncSetAttribute(batch_kernel<T, CH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, CH, G, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<T, CH, G>, threads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<T, CH, G, MINB>, threads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  batch_kernel<T, CH, G><<<num_sms * per_sm, threads, smem, st>>>(a);
+  batch_kernel<T, CH, G, MINB><<<num_sms * per_sm, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <class T>
-static cudaError_t launch_dt(const BatchArgs& a, int wpb, int num_sms, cudaStream_t st) {
-  // G candidates per distance group: G * CH = 16 row chunks (64 registers) in flight
+static cudaError_t launch_dt(const BatchArgs& a, int wpb, int regs, int num_sms, cudaStream_t st) {
+  // G candidates per distance group: G * CH = 16 row chunks (64 registers) in flight,
+  // 8 chunks under the 64-register budget
   const int ch = (a.dp4 + 31) / 32;
-  if (ch <= 1) return launch_t<T, 1, 16>(a, wpb, num_sms, st);
-  if (ch <= 2) return launch_t<T, 2, 8>(a, wpb, num_sms, st);
-  if (ch <= 4) return launch_t<T, 4, 4>(a, wpb, num_sms, st);
-  return launch_t<T, 8, 2>(a, wpb, num_sms, st);
+  if (ch <= 1) {
+    if (regs == 80) return launch_t<T, 1, 16, 6>(a, wpb, num_sms, st);
+    if (regs == 64) return launch_t<T, 1, 8, 8>(a, wpb, num_sms, st);
+    return launch_t<T, 1, 16, 4>(a, wpb, num_sms, st);
+  }
+  if (ch <= 2) return launch_t<T, 2, 8, 4>(a, wpb, num_sms, st);
+  if (ch <= 4) return launch_t<T, 4, 4, 4>(a, wpb, num_sms, st);
+  return launch_t<T, 8, 2, 4>(a, wpb, num_sms, st);
 }
 
 int rerank_count(const Params& p) { return p.dtype == UNIFY_FP32 ? 0 : p.rerank_mult * p.k; }
@@ -736,9 +743,9 @@ cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* 
   a.warp_bytes = batch_warp_bytes(a.cand_cap, a.ann_cap, a.vis_log2);
   a.o = o;
   const int wpb = p.warps_per_block;
-  if (p.dtype == UNIFY_BF16) return launch_dt<StoreBF16>(a, wpb, ix.num_sms, st);
-  if (p.dtype == UNIFY_FP8E4M3) return launch_dt<StoreFP8>(a, wpb, ix.num_sms, st);
-  return launch_dt<StoreF32>(a, wpb, ix.num_sms, st);
+  if (p.dtype == UNIFY_BF16) return launch_dt<StoreBF16>(a, wpb, p.reg_budget, ix.num_sms, st);
+  if (p.dtype == UNIFY_FP8E4M3) return launch_dt<StoreFP8>(a, wpb, p.reg_budget, ix.num_sms, st);
+  return launch_dt<StoreF32>(a, wpb, p.reg_budget, ix.num_sms, st);
 }
 
 }  // namespace unify

@@ -43,3 +43,15 @@ def c1_index():
 def c2_small_index():
     """c2-shaped (integer-valued, d=128, S=16) at n = 20,000: float32 distances are exact."""
     return built_index("c2", n=20_000, nq=300)
+
+
+@pytest.fixture(scope="session")
+def c3_small_index():
+    """GloVe-like shape: d = 96 unit vectors, log-uniform range fractions."""
+    return built_index("c3", n=20_000, nq=200)
+
+
+@pytest.fixture(scope="session")
+def c5_small_index():
+    """GIST-like shape: d = 960 non-negative values in [0, 1]."""
+    return built_index("c5", n=6_000, nq=120, efc=60)

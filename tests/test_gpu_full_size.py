@@ -1,0 +1,67 @@
+"""Parity at the full benchmark size: c2 (n = 1,000,000, d = 128, 10,000 queries,
+ranges 0.1/1/10/50/100 %), the whole batch searched in the benchmark's launch
+configuration (fused persistent kernel, tuned-style parameters), and a stratified
+sample of rows checked one by one against the CPU oracle. Integer-valued vectors make
+the GPU's float32 distances exact, so sampled rows must equal the oracle's literal
+search id for id (rows the GPU flags are checked for validity instead), and Strategy A
+rows must equal the exact answer."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PARAMS = dict(ef=16, ef_post=96, m=24, cand_cap=256, visited_cap=2048, tau_a=10_000, tau_b=400_000)
+
+
+@pytest.fixture(scope="module")
+def full():
+    import __graft_entry__
+    __graft_entry__.build()
+    import hsig_build
+    import paper_2412_02448_gb300 as U
+    from conftest import cache_dir
+    from workloads import make_workload
+    w = make_workload("c2", seed=2024)
+    path = hsig_build.cached_index_path(cache_dir(), w.name, w.n, w.seed)
+    if not os.path.exists(path):
+        hsig_build.build_index(w.vectors, w.attrs, path, w.S, w.M, w.efc, seed=w.seed)
+    return U, w, path
+
+
+def test_full_size_sampled_parity(full):
+    U, w, path = full
+    ix = U.Index(path)
+    p = U.Params.defaults(**PARAMS)
+    r = ix.search(w.queries, w.lo, w.hi, w.k, strategy="auto", params=p, counters=True)
+    torch.cuda.synchronize()
+    r = {k: v.cpu().numpy() for k, v in r.items()}
+    rng = np.random.default_rng(0)
+    fr = np.unique(w.fractions)
+    sample = np.concatenate([rng.choice(np.flatnonzero(w.fractions == f), 12, replace=False) for f in fr])
+    oi = oracle.OracleIndex(path)
+    o = oi.search(w.queries[sample], w.lo[sample], w.hi[sample], w.k, ef=PARAMS["ef"], m=PARAMS["m"],
+                  ef_post=PARAMS["ef_post"], strategy="auto", tau_a=PARAMS["tau_a"], tau_b=PARAMS["tau_b"])
+    ex = oracle.exact_knn(w.vectors, w.attrs, w.queries[sample], w.lo[sample], w.hi[sample], w.k)
+    assert set(o["strategy"].tolist()) == {0, 1, 2}
+    ok = (r["status"][sample] & 3) == 0
+    assert ok.mean() > 0.9
+    assert np.array_equal(r["ids"][sample][ok], o["ids"][ok])
+    assert np.array_equal(r["count"][sample][ok], o["count"][ok])
+    fin = np.isfinite(o["dist"][ok])
+    assert np.array_equal(r["dist"][sample][ok][fin].astype(np.float64), o["dist"][ok][fin])
+    assert np.array_equal(r["counters"][sample][ok, 1], o["n_exp"][ok])
+    pre = o["strategy"] == 0
+    assert np.array_equal(r["ids"][sample][pre], ex[0][pre])
+    # every row of the batch is a valid result
+    A = w.attrs
+    for i in range(0, len(w.lo), 7):
+        c = r["count"][i]
+        ids = r["ids"][i, :c]
+        assert np.all((A[ids] >= w.lo[i]) & (A[ids] <= w.hi[i])) and len(set(ids.tolist())) == c
+    rec = oracle.recall(r["ids"][sample], ex[0], ex[2], w.k)
+    assert rec.mean() >= 0.95

@@ -310,3 +310,56 @@ def test_fp8_storage_rerank(U, dataset, request):
             rec = oracle.recall(r["ids"], ex[0], ex[2], w.k)
             floor = 0.97 if strategy == "pre" else 0.85
             assert rec.mean() >= floor, (dataset, dtype, strategy, rec.mean())
+
+
+def test_register_budgets_give_identical_results(U, c1_index):
+    """The 128/80/64-register variants differ in distance-group size only; every
+    vector's distance uses the same lane order and reduction tree, so with the same
+    buffer sizes every row (flagged ones included) is bit-identical on real data."""
+    w, path = c1_index
+    ix = U.Index(path)
+    ta, tb = w.n // 100, w.n // 2
+    for strategy in ("auto", "hybrid", "post"):
+        ref = None
+        for regs in (128, 80, 64):
+            p = U.Params.defaults(tau_a=ta, tau_b=tb, reg_budget=regs, visited_cap=1024, cand_cap=512)
+            r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy=strategy, params=p, counters=True))
+            if ref is None:
+                ref = r
+                continue
+            for key in ("ids", "dist", "count", "status"):
+                assert np.array_equal(r[key], ref[key]), (regs, strategy, key)
+            assert np.array_equal(r["counters"][:, :2], ref["counters"][:, :2]), (regs, strategy)
+
+
+@pytest.mark.parametrize("dataset", ["c3_small_index", "c5_small_index"])
+def test_other_widths_real_data(U, dataset, request):
+    """d = 96 (one partial chunk per lane) and d = 960 (eight chunks per lane, the
+    widest kernel variant) on real-valued data: the exact pre-filter within the FP64
+    tie band, distances within 1e-5 of FP64, graph strategies valid with high recall,
+    and every storage format."""
+    w, path = request.getfixturevalue(dataset)
+    ix = U.Index(path)
+    X = w.vectors.astype(np.float64)
+    ex_ids, ex_d, ex_c = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, w.k)
+    ta, tb = w.n // 100, w.n // 2
+    for dtype in (U.FP32, U.BF16, U.FP8E4M3):
+        for strategy in ("pre", "auto", "hybrid", "post"):
+            for regs in (128, 64):
+                p = U.Params.defaults(dtype=dtype, tau_a=ta, tau_b=tb, m=32, cand_cap=CAND, reg_budget=regs,
+                                      visited_cap=1024, scan_rows=512)
+                r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=128, strategy=strategy, params=p))
+                _valid(w, r, w.lo, w.hi)
+                for i in range(len(w.lo)):
+                    c = r["count"][i]
+                    ids = r["ids"][i, :c]
+                    d64 = ((X[ids] - w.queries[i].astype(np.float64)) ** 2).sum(1)
+                    assert np.all(np.abs(r["dist"][i, :c] - d64) <= 1e-5 * np.maximum(d64, 1e-30)), (dtype, strategy)
+                rec = oracle.recall(r["ids"], ex_ids, ex_c, w.k)
+                if strategy == "pre":
+                    assert np.array_equal(r["count"], ex_c)
+                    assert rec.mean() >= (0.999 if dtype == U.FP32 else 0.98), (dataset, dtype, regs, rec.mean())
+                elif strategy == "auto":
+                    # forced post-filtering on narrow ranges is poor by design (the
+                    # paper's motivation for routing); the routed batch must be good
+                    assert rec.mean() >= 0.85, (dataset, dtype, regs, rec.mean())
