@@ -400,7 +400,19 @@ def main():
                 "value": r_["value"], "ms_per_step": r_["ms"],
                 "recall_by_fraction": {f"{100 * f_:g}%": round(v_, 4) for f_, v_ in r_["recall"].items()},
                 "roofline_frac": r_["achieved"] / hbm, "achieved_gbs": r_["achieved"],
-                "params": {"ef": p_.ef, "ef_post": p_.ef_post, "m": p_.m, "rerank_mult": p_.rerank_mult}}
+                "routed": {"pre": int(r_["routed"][0]), "hybrid": int(r_["routed"][1]), "post": int(r_["routed"][2])},
+                "phase_ms_per_step": {ph: round(v, 4) for ph, v in r_["phases"].items() if not ph.startswith("unused")},
+                "params": {"ef": p_.ef, "ef_post": p_.ef_post, "m": p_.m, "rerank_mult": p_.rerank_mult,
+                           "tau_a": p_.tau_a, "tau_b": p_.tau_b, "tc_scan": p_.tc_scan}}
+            if dt == U.BF16:
+                # the same parameters with the other pre-filter scan (tensor cores or warps)
+                p0 = U.Params.defaults(**{f: getattr(p_, f) for f, _ in U.Params._fields_})
+                p0.tc_scan = 1 - p_.tc_scan
+                r0 = measure(p0, max(3, args.steps // 2), args.warmup)
+                precision[name]["tensor_core_scan" if p0.tc_scan else "warp_scan"] = {
+                    "value": r0["value"], "ms_per_step": r0["ms"],
+                    "phase_ms_per_step": {ph: round(v, 4) for ph, v in r0["phases"].items()
+                                          if not ph.startswith("unused")}}
 
     # the same step replayed as one CUDA graph (counter reset, route, search kernel)
     plan = ix.plan(q, lo, hi, k, strategy="auto", params=params)

@@ -97,6 +97,11 @@ typedef struct {
                           80 (24 warps) or 64 (32 warps, smaller distance groups); default 128.
                           More resident warps hide more memory latency when shared memory
                           (cand_cap, visited_cap, ef) also fits. */
+  int tc_scan;         /* 1: with UNIFY_BF16 storage, Strategy A queries are scanned on the
+                          tensor cores (tcgen05 MMA over TMA-staged row tiles shared by 128
+                          queries, top rerank_mult * k by bf16 distance, FP32 re-rank) when
+                          d is a multiple of 8, d <= 1024 and rerank_mult * k <= 64;
+                          0 (default): warp scan */
 } unify_params_t;
 
 /* Fills *p with the defaults above. */
@@ -202,7 +207,8 @@ UNIFY_API int unify_search_noalloc(unify_index_t* idx, const float* q, const int
 /* Per-phase timing of searches with CUDA events recorded on the search stream.
  * While enabled, every search records one event pair around each phase it runs:
  * 0 = route (range bounds, masks, work queues), 1 = the search kernel (hybrid,
- * post-filter and pre-filter work of the batch); 2 and 3 are reserved (zero). */
+ * post-filter and pre-filter work of the batch), 2 = the tensor-core pre-filter scan
+ * (when used); 3 is reserved (zero). */
 UNIFY_API int unify_timing_enable(unify_index_t* idx, int enable);
 
 /* Waits for the recorded events, writes per phase the summed milliseconds

@@ -63,7 +63,8 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
        queries run under the strategies): the (tau_A, tau_B) pair with the fastest
        batch whose recall meets the target in every group; then step 1 again under
        the new router.
-    3. CTA shape, buffer sizes and scan work-item size."""
+    3. CTA shape, buffer sizes, scan work-item size, register budget and (BF16
+       storage) the tensor-core pre-filter scan."""
     import torch
 
     import paper_2412_02448_gb300 as U
@@ -142,12 +143,16 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
         if best is not None:
             cur = beams(best[0])
     best = None
-    for extra in ({}, {"warps_per_block": 2}, {"cand_cap": 256}, {"cand_cap": 1024},
+    shapes = [{}, {"warps_per_block": 2}, {"cand_cap": 256}, {"cand_cap": 1024},
                   {"visited_cap": 1024}, {"visited_cap": 4096}, {"scan_rows": 1024}, {"scan_rows": 2048},
                   {"scan_rows": 4096}, {"reg_budget": 80, "visited_cap": 1024},
                   {"reg_budget": 80, "visited_cap": 1024, "cand_cap": 256},
                   {"reg_budget": 64, "visited_cap": 512, "cand_cap": 256},
-                  {"reg_budget": 64, "visited_cap": 1024, "cand_cap": 128}):
+                  {"reg_budget": 64, "visited_cap": 1024, "cand_cap": 128}]
+    if cur.dtype == U.BF16:
+        # pre-filter queries on the tensor cores instead of the warp scan
+        shapes.append({"tc_scan": 1 - cur.tc_scan})
+    for extra in shapes:
         p = make(extra, cur)
         try:
             ms, rec = run(p)

@@ -40,6 +40,16 @@ void free_core(Scratch& sc) {
   release(sc.items);
   release(sc.part);
   release(sc.counters);
+  release(sc.tc_bucket);
+  release(sc.tc_aq);
+  release(sc.tc_aqn);
+  if (sc.tc_qb) cudaFree(sc.tc_qb);
+  sc.tc_qb = nullptr;
+  release(sc.tc_tile);
+  release(sc.tc_part);
+  release(sc.tc_thr);
+  sc.tc_rows = 0;
+  sc.tc_dpq = 0;
   sc.cap_nq = 0;
   sc.cap_k = 0;
 }
@@ -63,8 +73,9 @@ cudaError_t alloc(T*& p, size_t elems) {
 }
 
 // Grows the scratch to hold nq queries with k results (device allocation).
-cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k) {
-  if (sc.counters && nq <= sc.cap_nq && k <= sc.cap_k) return cudaSuccess;
+cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k, int d) {
+  const int dpq = ((d + 63) / 64) * 64;  // bfloat16 query rows of the tensor-core scan
+  if (sc.counters && nq <= sc.cap_nq && k <= sc.cap_k && dpq <= sc.tc_dpq) return cudaSuccess;
   int64_t cap = nq > sc.cap_nq ? nq : sc.cap_nq;
   if (cap < 256) cap = 256;
   int kc = k > sc.cap_k ? k : sc.cap_k;
@@ -81,10 +92,21 @@ cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k) {
   if (e == cudaSuccess) e = alloc(sc.items, cap * kMaxScanBlocks);
   if (e == cudaSuccess) e = alloc(sc.part, (size_t)cap * kMaxScanBlocks * kc);
   if (e == cudaSuccess) e = alloc(sc.counters, kNumCounters);
+  const int64_t rows = ((cap + kTcQueryTile - 1) / kTcQueryTile) * kTcQueryTile;
+  if (e == cudaSuccess) e = alloc(sc.tc_bucket, 1024);
+  if (e == cudaSuccess) e = alloc(sc.tc_aq, rows);
+  if (e == cudaSuccess) e = alloc(sc.tc_aqn, rows);
+  if (e == cudaSuccess) e = cudaMalloc(&sc.tc_qb, (size_t)rows * dpq * 2);
+  if (e == cudaSuccess) e = alloc(sc.tc_tile, 4 * (rows / kTcQueryTile) + 1);
+  // at most kTcUnitsPerTile units per tile, one list of at most 64 keys per query and unit
+  if (e == cudaSuccess) e = alloc(sc.tc_part, (size_t)rows * kTcUnitsPerTile * 64);
+  if (e == cudaSuccess) e = alloc(sc.tc_thr, rows);
   if (e != cudaSuccess) {
     free_core(sc);
     return e;
   }
+  sc.tc_rows = rows;
+  sc.tc_dpq = dpq;
   sc.cap_nq = cap;
   sc.cap_k = kc;
   return cudaSuccess;
@@ -126,6 +148,7 @@ int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Para
   p.warps_per_block = d.warps_per_block;
   p.scan_rows = d.scan_rows;
   p.reg_budget = d.reg_budget;
+  p.tc_scan = d.tc_scan;
   p.dtype = d.dtype;
   p.rerank_mult = d.rerank_mult;
   p.tau_a = d.tau_a >= 0 ? d.tau_a : ix.n / 100;
@@ -204,7 +227,7 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
   const int kk = rerank_count(p) > k ? rerank_count(p) : k;  // keys per partial scan list
   if (idx->live_plans > 0 && kk > idx->sc.cap_k)
     return fail(UNIFY_E_LIMIT, "search larger than the scratch held by a live plan; destroy the plans first");
-  cudaError_t e = ensure_scratch(idx->sc, nq, kk);
+  cudaError_t e = ensure_scratch(idx->sc, nq, kk, idx->ix.d);
   if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
   Scratch& sc = idx->sc;
   e = cudaMemsetAsync(sc.counters, 0, kNumCounters * sizeof(int32_t), st);
@@ -216,9 +239,15 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
                      sc.strat, &o, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "route kernel");
+  const bool tc = (strategy == UNIFY_PRE || strategy == UNIFY_AUTO) && tc_scan_available(idx->ix, p);
+  if (tc) {
+    PhaseTimer t(idx->tm, 2, st);
+    e = launch_tcscan(idx->ix, sc, q, p, o, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core pre-filter scan");
+  }
   {
     PhaseTimer t(idx->tm, 1, st);
-    e = launch_batch(idx->ix, sc, q, p, o, st);
+    e = launch_batch(idx->ix, sc, q, p, o, st, tc);
   }
   if (e != cudaSuccess) return cuda_fail(e, "search kernel");
   return UNIFY_OK;
@@ -257,6 +286,7 @@ extern "C" void unify_default_params(unify_params_t* p) {
   p->warps_per_block = 4;
   p->scan_rows = 8192;
   p->reg_budget = 128;
+  p->tc_scan = 0;
 }
 
 extern "C" const char* unify_last_error(void) { return g_last_error.c_str(); }

@@ -99,7 +99,7 @@ __global__ void derive_kernel(const float* __restrict__ vec, const int32_t* __re
 // round-to-nearest-even) with s = max|x| / 448 (s = 1 for an all-zero vector).
 __global__ void lowp_kernel(const float* __restrict__ vec, const int32_t* __restrict__ sorted_ids, int64_t n,
                             int dp, uint2* bf_id, uint2* bf_sorted, uint32_t* f8_id, uint32_t* f8_sorted,
-                            float* sc_id, float* sc_sorted) {
+                            float* sc_id, float* sc_sorted, float* xn_sorted) {
   const int lane = threadIdx.x & 31;
   const int dp4 = dp / 4;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -113,6 +113,7 @@ __global__ void lowp_kernel(const float* __restrict__ vec, const int32_t* __rest
     }
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     const float s = mx > 0.f ? mx / 448.f : 1.f;
+    float nn = 0.f;  // squared norm of the bfloat16 row
     for (int c = lane; c < dp4; c += 32) {
       const float4 x = row[c];
       uint2 b;
@@ -124,14 +125,22 @@ __global__ void lowp_kernel(const float* __restrict__ vec, const int32_t* __rest
                          ((uint32_t)__nv_cvt_float_to_fp8(x.y / s, __NV_SATFINITE, __NV_E4M3) << 8) |
                          ((uint32_t)__nv_cvt_float_to_fp8(x.z / s, __NV_SATFINITE, __NV_E4M3) << 16) |
                          ((uint32_t)__nv_cvt_float_to_fp8(x.w / s, __NV_SATFINITE, __NV_E4M3) << 24);
+      const float b0 = __uint_as_float(b.x << 16), b1 = __uint_as_float(b.x & 0xffff0000u);
+      const float b2 = __uint_as_float(b.y << 16), b3 = __uint_as_float(b.y & 0xffff0000u);
+      nn = fmaf(b0, b0, nn);
+      nn = fmaf(b1, b1, nn);
+      nn = fmaf(b2, b2, nn);
+      nn = fmaf(b3, b3, nn);
       bf_id[(int64_t)v * dp4 + c] = b;
       bf_sorted[p * dp4 + c] = b;
       f8_id[(int64_t)v * dp4 + c] = f;
       f8_sorted[p * dp4 + c] = f;
     }
+    for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
     if (lane == 0) {
       sc_id[v] = s;
       sc_sorted[p] = s;
+      xn_sorted[p] = nn;
     }
   }
 }
@@ -139,11 +148,11 @@ __global__ void lowp_kernel(const float* __restrict__ vec, const int32_t* __rest
 void free_device(DeviceIndex& ix) {
   void* ptrs[] = {ix.vec, ix.vec_sorted, ix.sorted_ids, ix.sorted_attr, ix.pos, ix.upper_base, ix.adj0,
                   ix.gmask0, ix.adjU, ix.gmaskU, ix.seg_bounds, ix.seg_start, ix.vt_bf16, ix.vts_bf16,
-                  ix.vt_fp8, ix.vts_fp8, ix.scale_fp8, ix.scale_fp8_sorted};
+                  ix.vt_fp8, ix.vts_fp8, ix.scale_fp8, ix.scale_fp8_sorted, ix.xn_bf16_sorted};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ix.vt_bf16 = ix.vts_bf16 = ix.vt_fp8 = ix.vts_fp8 = nullptr;
-  ix.scale_fp8 = ix.scale_fp8_sorted = nullptr;
+  ix.scale_fp8 = ix.scale_fp8_sorted = ix.xn_bf16_sorted = nullptr;
   ix.vec = ix.vec_sorted = nullptr;
   ix.sorted_ids = ix.pos = ix.upper_base = ix.adj0 = ix.adjU = ix.seg_start = nullptr;
   ix.sorted_attr = ix.seg_bounds = nullptr;
@@ -327,6 +336,7 @@ extern "C" int unify_load_index(const char* path, int device, unify_index_t** ou
   if (e == cudaSuccess) e = cudaMalloc(&ix.vts_fp8, n * dp4 * 4);
   if (e == cudaSuccess) e = cudaMalloc(&ix.scale_fp8, n * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&ix.scale_fp8_sorted, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&ix.xn_bf16_sorted, n * sizeof(float));
   if (e == cudaSuccess) {
     derive_kernel<<<1024, 256>>>(ix.vec, ix.sorted_ids, d_attr, ix.n, ix.dp, ix.vec_sorted, ix.sorted_attr, ix.pos);
     e = cudaGetLastError();
@@ -334,7 +344,8 @@ extern "C" int unify_load_index(const char* path, int device, unify_index_t** ou
   if (e == cudaSuccess) {
     lowp_kernel<<<1024, 256>>>(ix.vec, ix.sorted_ids, ix.n, ix.dp, reinterpret_cast<uint2*>(ix.vt_bf16),
                                reinterpret_cast<uint2*>(ix.vts_bf16), reinterpret_cast<uint32_t*>(ix.vt_fp8),
-                               reinterpret_cast<uint32_t*>(ix.vts_fp8), ix.scale_fp8, ix.scale_fp8_sorted);
+                               reinterpret_cast<uint32_t*>(ix.vts_fp8), ix.scale_fp8, ix.scale_fp8_sorted,
+                               ix.xn_bf16_sorted);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

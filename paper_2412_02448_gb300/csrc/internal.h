@@ -46,6 +46,7 @@ struct DeviceIndex {
   unsigned char* vts_fp8 = nullptr;
   float* scale_fp8 = nullptr;         // per-vector scale max|x| / 448 (by id)
   float* scale_fp8_sorted = nullptr;  // the same in attribute order
+  float* xn_bf16_sorted = nullptr;    // squared norms of the bfloat16 rows, attribute order
   int num_sms = 0;
 };
 
@@ -64,6 +65,16 @@ struct Scratch {
   int2* items = nullptr;       // cap_nq * kMaxScanBlocks scan work items (query, block)
   uint64_t* part = nullptr;    // cap_nq * kMaxScanBlocks * cap_k partial top-k keys
   int32_t* counters = nullptr; // kNumCounters ints, zeroed per call
+  // tensor-core pre-filter scan
+  int32_t* tc_bucket = nullptr;  // 1024 bucket counters / cursors
+  int32_t* tc_aq = nullptr;      // pre-filter query ids in bucketed order
+  float* tc_aqn = nullptr;       // squared norms of their bfloat16 vectors
+  void* tc_qb = nullptr;         // their bfloat16 vectors, tc_rows x tc_dpq
+  int32_t* tc_tile = nullptr;    // per tile: first row, row blocks, units, unit offsets (4 x tiles + 1)
+  uint64_t* tc_part = nullptr;   // per work unit: kTcQueryTile lists of up to 64 candidate keys
+  unsigned long long* tc_thr = nullptr;  // per pre-filter query: threshold key shared by its units
+  int64_t tc_rows = 0;
+  int tc_dpq = 0;
   // host-buffer staging
   int64_t stage_nq = 0;
   int stage_k = 0, stage_d = 0;
@@ -76,17 +87,22 @@ struct Scratch {
   uint32_t* s_status = nullptr;
 };
 
+constexpr int kTcQueryTile = 128;   // pre-filter queries per tensor-core tile
+constexpr int kTcUnitsPerTile = 16;  // at most this many work units per tile
+
 // counters[] layout
 enum {
   CNT_QA = 0, CNT_QC = 1, CNT_QB = 2,  // queue lengths
   CNT_ITEMS = 3,                       // scan work items
   CNT_TAKE = 4,                        // head of the combined work queue
   CNT_T0 = 8,                          // counters[8..9]: 64-bit global-timer origin of the search kernel
+  CNT_TC_ERR = 10,                     // the tensor-core scan timed out on a wait
+  CNT_TC_UNITS = 11,                   // work units of the tensor-core scan
   kNumCounters = 16
 };
 
 struct Params {
-  int k, ef, m, ef_post, cand_cap, vis_log2, max_exp, warps_per_block, scan_rows, rerank_mult, reg_budget;
+  int k, ef, m, ef_post, cand_cap, vis_log2, max_exp, warps_per_block, scan_rows, rerank_mult, reg_budget, tc_scan;
   int64_t tau_a, tau_b;
   unify_dtype_t dtype;
 };
@@ -105,7 +121,10 @@ cudaError_t launch_route(const DeviceIndex& ix, const Scratch& sc, const int64_t
                          int build_queues, int32_t* out_pa, int32_t* out_pb, uint32_t* out_mask,
                          int32_t* out_strat, const Outputs* outs, cudaStream_t st);
 cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
-                         const Outputs& o, cudaStream_t st);
+                         const Outputs& o, cudaStream_t st, bool skip_scan = false);
+bool tc_scan_available(const DeviceIndex& ix, const Params& p);
+cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
+                          const Outputs& o, cudaStream_t st);
 int batch_smem_per_warp(const Params& p);
 int rerank_count(const Params& p);  // candidates re-ranked in FP32 (0 for FP32 storage)
 

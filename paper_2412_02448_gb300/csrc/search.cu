@@ -43,6 +43,7 @@
 // [pa, pb) and loads clamp to the last valid row.
 #include "common.cuh"
 #include "internal.h"
+#include "warp_ops.cuh"
 
 namespace unify {
 
@@ -78,6 +79,7 @@ struct BatchArgs {
   int32_t* counters;
   int k, ef_h, ef_p, m, cand_cap, ann_cap, vis_log2, max_exp;
   int warp_bytes;
+  int skip_scan;  // the pre-filter queries were searched by the tensor-core scan
   Outputs o;
 };
 
@@ -135,75 +137,6 @@ __device__ __forceinline__ int us_since_start(int32_t* counters) {
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-__device__ __forceinline__ void write_row(const uint64_t* keys, int cnt, int k, int64_t qi, const Outputs& o) {
-  const int lane = lane_id();
-  for (int t = lane; t < k; t += 32) {
-    const bool v = t < cnt;
-    const uint64_t key = v ? keys[t] : kKeyMax;
-    o.ids[qi * k + t] = v ? (int64_t)key_id(key) : (int64_t)-1;
-    o.dist[qi * k + t] = v ? key_dist(key) : __int_as_float(0x7f800000);
-  }
-}
-
-// Distances of the candidates held by the lanes (cid >= 0), G at a time, from
-// rows of `rows` (row_bytes each) in storage format T (scale: FP8 scales or null).
-// All G row loads of a group are issued before any of them is used (slots past
-// the last candidate reload the last candidate's row and are discarded), so a
-// group costs one memory latency, not G.
-template <class T, int CH, int G>
-__device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, const unsigned char* rows,
-                                            int row_bytes, const float* scale, int dp4, int* clist) {
-  const int lane = lane_id();
-  const unsigned vm = __ballot_sync(kFull, cid >= 0);
-  const int nv = __popc(vm);
-  const int my = __popc(vm & lanemask_lt());
-  if (cid >= 0) clist[my] = cid;
-  __syncwarp();
-  constexpr int SH = (G == 32) ? 0 : (G == 16) ? 1 : (G == 8) ? 2 : (G == 4) ? 3 : 4;  // log2(32 / G)
-  float result = 0.f;
-  for (int g = 0; g * G < nv; ++g) {
-    int ids[G];
-#pragma unroll
-    for (int u = 0; u < G; ++u) {
-      const int c = g * G + u;
-      ids[u] = clist[c < nv ? c : nv - 1];
-    }
-    float4 x[G][CH];
-#pragma unroll
-    for (int u = 0; u < G; ++u) {
-      const unsigned char* row = rows + (int64_t)ids[u] * row_bytes;
-      const float sc = scale ? __ldg(scale + ids[u]) : 1.f;
-#pragma unroll
-      for (int t = 0; t < CH; ++t) {
-        const int c = lane + 32 * t;
-        x[u][t] = c < dp4 ? T::load(row, c, sc) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-    float part[G];
-#pragma unroll
-    for (int u = 0; u < G; ++u) {
-      float s = 0.f;
-#pragma unroll
-      for (int t = 0; t < CH; ++t) {
-        const float e0 = q[t].x - x[u][t].x, e1 = q[t].y - x[u][t].y;
-        const float e2 = q[t].z - x[u][t].z, e3 = q[t].w - x[u][t].w;
-        s = fmaf(e0, e0, s);
-        s = fmaf(e1, e1, s);
-        s = fmaf(e2, e2, s);
-        s = fmaf(e3, e3, s);
-      }
-      part[u] = (g * G + u < nv) ? s : 0.f;
-    }
-    const float red = warp_transpose_reduce<G>(part);
-    const int u = my - g * G;
-    const bool mine = cid >= 0 && u >= 0 && u < G;
-    const float v = __shfl_sync(kFull, red, mine ? (u << SH) : 0);
-    if (mine) result = v;
-  }
-  __syncwarp();
-  return result;
 }
 
 // Slot (segment * M + s) of the ci-th selected neighbour (hybrid, S2 selection).
@@ -376,18 +309,6 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
     }
   }
   return nA;
-}
-
-// Keeps the k smallest keys: merges the lanes' keys that beat the current k-th.
-__device__ __forceinline__ int topk_offer(uint64_t* topk, int nt, int k, uint64_t key, int* R) {
-  const uint64_t thr = (nt >= k) ? topk[k - 1] : kKeyMax;
-  const bool pass = key < thr;
-  const unsigned bal = __ballot_sync(kFull, pass);
-  if (bal == 0) return nt;
-  uint64_t s = warp_sort_asc(pass ? key : kKeyMax);
-  int r0;
-  bool dropped;
-  return warp_merge(topk, nullptr, nt, k, s, __popc(bal), R, &r0, &dropped);
 }
 
 // FP32 re-rank: exact float32 distances (direct difference against the float32
@@ -625,7 +546,7 @@ __global__ void __launch_bounds__(128, MINB) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const WarpMem w = carve(smem_raw + (size_t)warp * a.warp_bytes, a);
-  const int nC = a.counters[CNT_QC], nB = a.counters[CNT_QB], nI = a.counters[CNT_ITEMS];
+  const int nC = a.counters[CNT_QC], nB = a.counters[CNT_QB], nI = a.skip_scan ? 0 : a.counters[CNT_ITEMS];
   for (;;) {
     int idx = 0;
     if (lane == 0) idx = atomicAdd(&a.counters[CNT_TAKE], 1);
@@ -684,8 +605,9 @@ int batch_ann_cap(const Params& p) {
 int batch_smem_per_warp(const Params& p) { return batch_warp_bytes(p.cand_cap, batch_ann_cap(p), p.vis_log2); }
 
 cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
-                         const Outputs& o, cudaStream_t st) {
+                         const Outputs& o, cudaStream_t st, bool skip_scan) {
   BatchArgs a;
+  a.skip_scan = skip_scan ? 1 : 0;
   a.vec = ix.vec;
   a.dp4 = ix.dp / 4;
   a.rerank = rerank_count(p);

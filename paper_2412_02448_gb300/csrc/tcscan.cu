@@ -1,0 +1,804 @@
+// Strategy A (pre-filtering, Section 4.2) for many queries at once on the 5th-
+// generation tensor cores: queries x in-range vectors is a dense contraction.
+//
+// The pre-filter queries of a batch are bucketed by the first position pa of
+// their range in the attribute order and converted to bfloat16, so that 128
+// consecutive queries (a tile) cover neighbouring rows. The rows of the union of
+// a tile's ranges are split into work units of whole 256-row blocks, spread over
+// all SMs. For a block, TMA stages 64-column slices of the tile's queries and of
+// the block's attribute-ordered bfloat16 rows (128-byte swizzled) and tcgen05.mma
+// forms D = Q X^T (M = 128 queries, N = 256 rows, K = 16 per instruction, float32
+// accumulation in tensor memory, two accumulators so that the epilogue of one
+// block overlaps the products of the next).
+//
+// Epilogue: tensor-memory lane q is query q of the tile, so thread q reads its
+// own query's 256 dot products, turns each into the squared distance
+// ||x||^2 + ||q||^2 - 2 x.q (norms of the bfloat16 values) and keeps, among the
+// rows inside its range [pa, pb), the rerank_mult * k = R smallest keys
+// (distance, id) of the unit in a private max-heap in shared memory. The first R
+// keys fill the heap unordered (a predicated store per column); the warp then
+// sorts that heap into descending order (a max-heap) in one cooperative pass;
+// later keys that beat the heap's top wait in a short queue and replace the top,
+// one per lane per round. Every query also has a threshold shared by all units
+// of its tile in global memory (the smallest heap top published so far): a unit
+// holding R keys at or below it rules out every larger key everywhere, so each
+// unit filters with the smaller of its own top and the shared one.
+//
+// A unit's lists go to global memory; a last kernel merges the lists of every
+// query's units, re-ranks the candidates with exact float32 direct-difference
+// distances against the float32 vectors, as the other reduced-precision paths
+// do, and writes the result row. On integer-valued vectors of at most 8 bits and
+// d <= 128 every term is an exact integer below 2^24, so the result equals the
+// exact float32 scan.
+//
+// Roles in a CTA of 6 warps: warps 0-3 epilogue (warp w reads tensor-memory
+// lanes 32w..32w+31), warp 4 lane 0 issues TMA loads, warp 5 lane 0 issues the
+// MMAs and owns the tensor-memory allocation. Stages of shared memory (query
+// slice 16 KB + row slice 32 KB per 64 columns of K) are handed over with
+// mbarriers. Every wait is bounded (a number of polls and an elapsed time); a
+// timeout sets an error flag instead of hanging, the waiting warp stops, and the
+// copies and products in flight are drained before the CTA releases its tensor
+// memory and exits.
+//
+// Bounds (checked against the buffers each launch receives): a unit's rows lie
+// in [tile_lo, tile_lo + 256 nb) and loads past n are zero-filled by TMA (rows)
+// or guarded (norms, ids); the query tile's TMA rows end at tc_rows (a multiple
+// of 128); part holds at most kTcUnitsPerTile units per tile; heap and queue
+// columns are indexed by the thread's own query (< 128) and slot (< R <= 64,
+// < kTcQueue).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "warp_ops.cuh"
+
+namespace unify {
+
+namespace {
+
+constexpr int kTcQ = kTcQueryTile;  // queries per tile (MMA M = tensor-memory lanes)
+constexpr int kTcRows = 256;        // rows per block (MMA N = tensor-memory columns per accumulator)
+constexpr int kTcKc = 64;           // K elements per stage (one 128-byte swizzle row)
+constexpr int kTcStages = 2;
+constexpr int kTcQueue = 32;        // keys queued per query before they replace the heap top
+constexpr int kTcRMax = 64;         // candidates kept per query for the re-rank
+constexpr int kBuckets = 1024;
+constexpr int kStageA = kTcQ * kTcKc * 2;     // 16 KB of queries
+constexpr int kStageB = kTcRows * kTcKc * 2;  // 32 KB of rows
+constexpr long long kWaitLimit = 1ll << 22;   // polls
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s of elapsed time
+
+struct TcSmem {
+  // 1024-byte aligned stages first
+  uint8_t a[kTcStages][kStageA];
+  uint8_t b[kTcStages][kStageB];
+  uint64_t heap[kTcRMax][kTcQ];  // column q: the max-heap of query q
+  uint64_t qk[kTcQueue][kTcQ];   // column q: keys waiting for the heap of query q
+  uint64_t full[kTcStages], empty[kTcStages], accf[2], acce[2], drain;
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the completion of the phase with the given parity; false on timeout.
+// A few immediate polls, then polls with a growing sleep in between, bounded
+// both by the number of polls and by kWaitNs of elapsed time.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+#pragma unroll 1
+  for (int i = 0; i < 16; ++i)
+    if (mbar_try(addr, parity)) return true;
+  const uint64_t t0 = global_ns();
+  unsigned ns = 32;
+#pragma unroll 1
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try(addr, parity)) return true;
+    __nanosleep(ns);
+    if (ns < 512) ns <<= 1;
+    if ((i & 63) == 63 && global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in 128-byte swizzled atoms
+// (8 rows x 128 bytes, 1024 bytes apart), start address 1024-byte aligned except
+// for the 32-byte steps along K inside an atom.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset: 8-row atoms
+  d |= (uint64_t)1 << 46;              // descriptor version
+  d |= (uint64_t)2 << 61;              // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: bf16 A and B, f32 accumulator, K-major A and
+// B, M = 128, N = 256.
+__device__ __forceinline__ uint32_t idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcRows >> 3) << 17) | ((uint32_t)(kTcQ >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive float32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Replaces the largest key of the full max-heap in column c of h (R keys) by
+// key and restores the heap order.
+__device__ __forceinline__ void heap_replace_top(uint64_t (*h)[kTcQ], int c, int R, uint64_t key) {
+  int i = 0;
+  for (;;) {
+    int ch = 2 * i + 1;
+    if (ch >= R) break;
+    uint64_t ck = h[ch][c];
+    if (ch + 1 < R) {
+      const uint64_t c2 = h[ch + 1][c];
+      if (c2 > ck) {
+        ck = c2;
+        ++ch;
+      }
+    }
+    if (ck <= key) break;
+    h[i][c] = ck;
+    i = ch;
+  }
+  h[i][c] = key;
+}
+
+// The whole warp sorts the R <= 64 keys of column c of h into descending order,
+// which is a max-heap (bitonic network over 64 positions, lane l holding
+// positions l and l + 32; the missing positions are filled with 0, the smallest
+// key, and sort to the end).
+__device__ __forceinline__ void warp_heapify_col(uint64_t (*h)[kTcQ], int c, int R) {
+  const int lane = lane_id();
+  uint64_t e0 = lane < R ? h[lane][c] : 0ull;
+  uint64_t e1 = lane + 32 < R ? h[lane + 32][c] : 0ull;
+#pragma unroll
+  for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == 32) {
+        // positions l and l + 32, one direction for the whole sequence
+        const uint64_t mx = e0 > e1 ? e0 : e1, mn = e0 > e1 ? e1 : e0;
+        e0 = mx;
+        e1 = mn;
+      } else {
+        const uint64_t y0 = __shfl_xor_sync(kFull, e0, j);
+        const uint64_t y1 = __shfl_xor_sync(kFull, e1, j);
+        const bool lower = (lane & j) == 0;
+        // descending blocks where (position & k) == 0, ascending elsewhere
+        const bool d0 = (lane & k) == 0, d1 = ((lane + 32) & k) == 0;
+        const bool big0 = lower == d0, big1 = lower == d1;
+        e0 = big0 ? (e0 > y0 ? e0 : y0) : (e0 < y0 ? e0 : y0);
+        e1 = big1 ? (e1 > y1 ? e1 : y1) : (e1 < y1 ? e1 : y1);
+      }
+    }
+  }
+  if (lane < R) h[lane][c] = e0;
+  if (lane + 32 < R) h[lane + 32][c] = e1;
+  __syncwarp();
+}
+
+struct TcArgs {
+  const int32_t* sorted_ids;
+  const float* xn;     // ||bf16(x)||^2 in attribute order
+  const float* vec;    // float32 rows by id (re-rank)
+  const float* q;      // float32 queries (re-rank)
+  int dp4, d, KC, num_sms;
+  int64_t n;
+  const int32_t* pa;
+  const int32_t* pb;
+  const int32_t* aq;    // pre-filter query ids in bucketed order
+  const float* aqn;     // ||bf16(q)||^2 in the same order
+  int32_t* tile_lo;     // first row of each tile's union range
+  int32_t* tile_nb;     // 256-row blocks of the union range
+  int32_t* tile_units;  // work units the range is split into
+  int32_t* unit_off;    // exclusive prefix of tile_units (ntiles + 1)
+  uint64_t* part;       // per unit and query of its tile: R candidate keys
+  unsigned long long* qthr;  // per query (bucketed order): smallest key known to have R keys at or below it
+  int32_t* counters;
+  int k, R;
+  Outputs o;
+};
+
+// Tile of work unit x (the last tile whose first unit is <= x).
+__device__ __forceinline__ int unit_tile(const TcArgs& a, int ntiles, int x) {
+  int lo = 0, hi = ntiles;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a.unit_off[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Rows [r0, r1) of unit u of tile t: blocks [u nb / U, (u + 1) nb / U) of the
+// tile's range (r1 may pass the end of the data; those rows are not used).
+__device__ __forceinline__ void tile_unit_rows(const TcArgs& a, int t, int u, int* r0, int* r1) {
+  const int nb = a.tile_nb[t], U = a.tile_units[t];
+  const int b0 = (int)((int64_t)u * nb / U), b1 = (int)((int64_t)(u + 1) * nb / U);
+  *r0 = a.tile_lo[t] + b0 * kTcRows;
+  *r1 = a.tile_lo[t] + b1 * kTcRows;
+}
+
+__global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                          const __grid_constant__ CUtensorMap tmQ, TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023));
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  const int nA = a.counters[CNT_QA];
+  const int ntiles = (nA + kTcQ - 1) / kTcQ;
+  const int nunits = a.counters[CNT_TC_UNITS];
+  int* err = a.counters + CNT_TC_ERR;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kTcStages; ++i) {
+      mbar_init(&s.full[i], 1);
+      mbar_init(&s.empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&s.accf[i], 1);
+      mbar_init(&s.acce[i], 4 * 32);
+    }
+    mbar_init(&s.drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem)),
+                 "r"(2 * kTcRows)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s.tmem;
+
+  if (warp == 4) {
+    // ---- TMA producer (lane 0 issues; the warp stays converged)
+    if (lane == 0) {
+      bool ok = true;
+      long long it = 0;
+      for (int x = blockIdx.x; x < nunits && ok; x += gridDim.x) {
+        const int t = unit_tile(a, ntiles, x);
+        int r0, r1;
+        tile_unit_rows(a, t, x - a.unit_off[t], &r0, &r1);
+        for (int row0 = r0; row0 < r1 && ok; row0 += kTcRows)
+          for (int kc = 0; kc < a.KC; ++kc, ++it) {
+            const int st = (int)(it % kTcStages);
+            const long long u = it / kTcStages;
+            if (u > 0 && !mbar_wait(&s.empty[st], (uint32_t)((u - 1) & 1))) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(&s.full[st], kStageA + kStageB);
+            tma_load_2d(s.a[st], &tmQ, kc * kTcKc, t * kTcQ, &s.full[st]);
+            tma_load_2d(s.b[st], &tmX, kc * kTcKc, row0, &s.full[st]);
+          }
+      }
+      // no copy may still be landing in shared memory when the CTA leaves: wait
+      // (bounded) for the last load issued into every stage
+      for (int st = 0; st < kTcStages; ++st) {
+        if (it <= st) continue;
+        const long long last_use = (it - 1 - st) / kTcStages;
+        if (!mbar_wait(&s.full[st], (uint32_t)(last_use & 1))) ok = false;
+      }
+      if (!ok) atomicExch(err, 1);
+    }
+    __syncwarp();
+  } else if (warp == 5) {
+    // ---- MMA issuer (lane 0 issues; the warp stays converged)
+    if (lane == 0) {
+      bool ok = true;
+      const uint32_t idesc = idesc_bf16();
+      long long it = 0, g = 0;
+      for (int x = blockIdx.x; x < nunits && ok; x += gridDim.x) {
+        const int t = unit_tile(a, ntiles, x);
+        int r0, r1;
+        tile_unit_rows(a, t, x - a.unit_off[t], &r0, &r1);
+        for (int row0 = r0; row0 < r1 && ok; row0 += kTcRows, ++g) {
+          const int ab = (int)(g & 1);
+          const long long ua = g >> 1;
+          if (ua > 0 && !mbar_wait(&s.acce[ab], (uint32_t)((ua - 1) & 1))) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d_tmem = tmem + (uint32_t)(ab * kTcRows);
+          for (int kc = 0; kc < a.KC; ++kc, ++it) {
+            const int st = (int)(it % kTcStages);
+            if (!mbar_wait(&s.full[st], (uint32_t)((it / kTcStages) & 1))) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t da = sw128_desc(smem_u32(s.a[st]));
+            const uint64_t db = sw128_desc(smem_u32(s.b[st]));
+#pragma unroll
+            for (int kk = 0; kk < kTcKc / 16; ++kk)
+              umma_bf16(d_tmem, da + 2 * kk, db + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+            umma_commit(&s.empty[st]);
+          }
+          if (!ok) break;
+          umma_commit(&s.accf[ab]);
+        }
+      }
+      // every product issued has completed before tensor memory is released
+      umma_commit(&s.drain);
+      if (!mbar_wait(&s.drain, 0)) ok = false;
+      if (!ok) atomicExch(err, 1);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue warps 0-3: thread q = query q of the tile = tensor-memory lane q.
+    // The warps run independently (no block-wide barrier); a timed-out wait ends
+    // the warp's loop (decided warp-wide) and the issuers time out in turn.
+    const int tq = threadIdx.x;
+    bool failed = false;
+    long long g = 0;
+    for (int x = blockIdx.x; x < nunits && !failed; x += gridDim.x) {
+      const int t = unit_tile(a, ntiles, x);
+      int r0, r1;
+      tile_unit_rows(a, t, x - a.unit_off[t], &r0, &r1);
+      const int qpos = t * kTcQ + tq;
+      const bool qv = qpos < nA;
+      int pa = 0, pb = 0;
+      float qn = 0.f;
+      if (qv) {
+        const int qi = a.aq[qpos];
+        pa = a.pa[qi];
+        pb = a.pb[qi];
+        qn = a.aqn[qpos];
+      }
+      int cnt = 0;                 // keys in the heap column of this query
+      bool heaped = false;         // the column holds R keys in heap order
+      uint64_t thr_own = kKeyMax;  // largest key of the full heap of this unit
+      for (int row0 = r0; row0 < r1; row0 += kTcRows, ++g) {
+        const int ab = (int)(g & 1);
+        // squared norms and ids of the block's rows: lane j holds row row0 + 32c + j
+        // of chunk c (loads in flight while the accumulator is awaited)
+        float xr[kTcRows / 32];
+        int32_t ir[kTcRows / 32];
+#pragma unroll
+        for (int c = 0; c < kTcRows / 32; ++c) {
+          const int64_t row = (int64_t)row0 + c * 32 + lane;
+          xr[c] = row < a.n ? __ldg(a.xn + row) : 0.f;
+          ir[c] = row < a.n ? __ldg(a.sorted_ids + row) : 0;
+        }
+        // the query's threshold so far over every unit of its tile; it only
+        // decreases, so a stale value is still valid
+        const uint64_t tg = qv ? *reinterpret_cast<volatile unsigned long long*>(a.qthr + qpos) : kKeyMax;
+        const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);  // this query's columns
+        const bool ok = __all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1)));
+        if (!ok) {
+          failed = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint64_t thr = thr_own < tg ? thr_own : tg;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * kTcRows);
+#pragma unroll
+        for (int c = 0; c < kTcRows / 32; ++c) {
+          const bool need = c1 > c * 32 && c0 < c * 32 + 32;
+          if (!__any_sync(kFull, need)) continue;
+          float v[32];
+          tmem_ld32(taddr + (uint32_t)(c * 32), v);
+          // keys below the threshold: the first R fill the column unordered, later
+          // ones wait in the queue
+          int nq = 0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = c * 32 + j;
+            const float xv = __shfl_sync(kFull, xr[c], j);
+            const int32_t idj = __shfl_sync(kFull, ir[c], j);
+            const uint64_t key = make_key(fmaxf(xv + qn - 2.f * v[j], 0.f), idj);
+            if (col >= c0 && col < c1 && key < thr) {
+              if (cnt < a.R) {
+                s.heap[cnt][tq] = key;
+                ++cnt;
+              } else {
+                s.qk[nq][tq] = key;
+                ++nq;
+              }
+            }
+          }
+          // columns that just reached R keys become heaps (one warp-wide sort each)
+          const bool fresh = cnt == a.R && !heaped;
+          unsigned fill = __ballot_sync(kFull, fresh);
+          while (fill) {
+            const int l = __ffs(fill) - 1;
+            fill &= fill - 1;
+            warp_heapify_col(s.heap, warp * 32 + l, a.R);
+          }
+          if (fresh) {
+            heaped = true;
+            thr_own = s.heap[0][tq];
+            thr = thr_own < tg ? thr_own : tg;
+          }
+          // queued keys replace the heap top, one per lane per round
+          while (__any_sync(kFull, nq > 0)) {
+            if (nq > 0) {
+              const uint64_t key = s.qk[--nq][tq];
+              if (key < thr) {
+                heap_replace_top(s.heap, tq, a.R, key);
+                thr_own = s.heap[0][tq];
+                thr = thr_own < tg ? thr_own : tg;
+              }
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&s.acce[ab]);
+        if (qv && thr_own < tg) atomicMin(a.qthr + qpos, (unsigned long long)thr_own);
+      }
+      if (failed) break;
+      // this unit's list for the query (unsorted, padded with the largest key)
+      uint64_t* dst = a.part + ((int64_t)x * kTcQ + tq) * a.R;
+      for (int r = 0; r < a.R; ++r) dst[r] = r < cnt ? s.heap[r][tq] : kKeyMax;
+    }
+    if (failed) atomicExch(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 5) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcRows)
+                 : "memory");
+  }
+}
+
+// One warp per tile: the union of its queries' ranges in 256-row blocks.
+__global__ void tc_tile_prep(TcArgs a) {
+  const int nA = a.counters[CNT_QA];
+  const int ntiles = (nA + kTcQ - 1) / kTcQ;
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += warps) {
+    const int q0 = t * kTcQ, nq = min(kTcQ, nA - q0);
+    int lo = INT_MAX, hi = 0;
+    for (int i = lane; i < nq; i += 32) {
+      const int qi = a.aq[q0 + i];
+      const int p0 = a.pa[qi], p1 = a.pb[qi];
+      if (p1 > p0) {
+        lo = min(lo, p0);
+        hi = max(hi, p1);
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      lo = min(lo, __shfl_xor_sync(kFull, lo, off));
+      hi = max(hi, __shfl_xor_sync(kFull, hi, off));
+    }
+    if (lane == 0) {
+      a.tile_lo[t] = lo == INT_MAX ? 0 : lo;
+      a.tile_nb[t] = lo == INT_MAX ? 0 : (hi - lo + kTcRows - 1) / kTcRows;
+    }
+  }
+}
+
+// One CTA of 1024 threads: splits every tile into work units of about equal
+// length, about two units per SM over the whole batch (at least one per tile
+// with rows, at most kTcUnitsPerTile and at most one per block), and writes the
+// exclusive prefix of the units per tile; the total goes to the counters.
+__global__ void tc_unit_plan(TcArgs a) {
+  __shared__ int sm[1024];
+  __shared__ unsigned long long tot;
+  __shared__ int carry;
+  const int nA = a.counters[CNT_QA];
+  const int ntiles = (nA + kTcQ - 1) / kTcQ;
+  unsigned long long mine = 0;
+  for (int t = threadIdx.x; t < ntiles; t += 1024) mine += (unsigned long long)a.tile_nb[t];
+  for (int off = 16; off > 0; off >>= 1) mine += __shfl_xor_sync(kFull, mine, off);
+  if (threadIdx.x == 0) {
+    tot = 0;
+    carry = 0;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) atomicAdd(&tot, mine);
+  __syncthreads();
+  const long long total = tot > 0 ? (long long)tot : 1;
+  const long long target = 2ll * a.num_sms;
+  for (int base = 0; base < ntiles; base += 1024) {
+    const int t = base + threadIdx.x;
+    int v = 0;
+    if (t < ntiles) {
+      const int nb = a.tile_nb[t];
+      v = (int)((nb * target + total - 1) / total);
+      v = max(v, nb > 0 ? 1 : 0);
+      v = min(v, min(nb, kTcUnitsPerTile));
+      a.tile_units[t] = v;
+    }
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      const int w = threadIdx.x >= off ? sm[threadIdx.x - off] : 0;
+      __syncthreads();
+      sm[threadIdx.x] += w;
+      __syncthreads();
+    }
+    if (t < ntiles) a.unit_off[t] = carry + sm[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += sm[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.unit_off[ntiles] = carry;
+    a.counters[CNT_TC_UNITS] = carry;
+  }
+}
+
+// One warp per pre-filter query: merges the lists of the units of its tile that
+// overlap its range, re-ranks the candidates with exact float32 distances and
+// writes the result row. After a timed-out wait the rows are empty and flagged.
+template <int CH, int G>
+__global__ void __launch_bounds__(128) tc_finish(TcArgs a) {
+  __shared__ uint64_t top[4][kTcRMax];
+  __shared__ uint64_t out[4][kTcRMax];
+  __shared__ int R[4][32];
+  __shared__ int clist[4][32];
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  const int nA = a.counters[CNT_QA];
+  const bool failed = a.counters[CNT_TC_ERR] != 0;
+  const int warps = gridDim.x * 4;
+  for (int pos = blockIdx.x * 4 + warp; pos < nA; pos += warps) {
+    const int t = pos / kTcQ, j = pos - t * kTcQ;
+    const int qi = a.aq[pos];
+    const int pa = a.pa[qi], pb = a.pb[qi];
+    const int u0 = a.unit_off[t], U = a.tile_units[t];
+    int nt = 0;
+    for (int u = 0; u < U && pb > pa && !failed; ++u) {
+      int r0, r1;
+      tile_unit_rows(a, t, u, &r0, &r1);
+      if (r1 <= pa || r0 >= pb) continue;
+      const uint64_t* src = a.part + ((int64_t)(u0 + u) * kTcQ + j) * a.R;
+      for (int off = 0; off < a.R; off += 32) {
+        const uint64_t key = off + lane < a.R ? src[off + lane] : kKeyMax;
+        nt = topk_offer(top[warp], nt, a.R, key, R[warp]);
+      }
+    }
+    float4 qv[CH];
+    load_query<CH>(qv, a.q + (int64_t)qi * a.d, a.d);
+    int no = 0;
+    for (int off = 0; off < nt; off += 32) {
+      int cid = off + lane < nt ? key_id(top[warp][off + lane]) : -1;
+      if (cid >= a.n) cid = -1;
+      const float dist = batch_dist<StoreF32, CH, G>(qv, cid, reinterpret_cast<const unsigned char*>(a.vec),
+                                                     a.dp4 * 16, nullptr, a.dp4, clist[warp]);
+      no = topk_offer(out[warp], no, a.k, cid >= 0 ? make_key(dist, cid) : kKeyMax, R[warp]);
+    }
+    write_row(out[warp], no, a.k, qi, a.o);
+    if (lane == 0) {
+      a.o.count[qi] = no;
+      if (a.o.status) a.o.status[qi] = failed ? UNIFY_Q_LIMIT : 0u;
+      if (a.o.counters) {
+        a.o.counters[4 * (int64_t)qi + 2] = 0;
+        a.o.counters[4 * (int64_t)qi + 3] = 0;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Pre-filter queries per bucket of pa.
+__global__ void tc_bucket_count(const int32_t* __restrict__ queues, const int32_t* __restrict__ pa,
+                                int32_t* counters, int32_t* bucket, int64_t n) {
+  const int nA = counters[CNT_QA];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nA; i += gridDim.x * blockDim.x) {
+    const int qi = queues[i];
+    const int b = (int)(((int64_t)pa[qi] * kBuckets) / (n + 1));
+    atomicAdd(&bucket[b], 1);
+  }
+}
+
+// Exclusive prefix sum of the bucket counts (one CTA of 1024 threads).
+__global__ void tc_bucket_scan(int32_t* bucket) {
+  __shared__ int sm[kBuckets];
+  const int t = threadIdx.x;
+  sm[t] = bucket[t];
+  __syncthreads();
+  for (int off = 1; off < kBuckets; off <<= 1) {
+    const int v = t >= off ? sm[t - off] : 0;
+    __syncthreads();
+    sm[t] += v;
+    __syncthreads();
+  }
+  bucket[t] = sm[t] - bucket[t];  // exclusive start, used as a fill cursor
+}
+
+// Places every pre-filter query in its bucket, writes its bfloat16 vector
+// (zero-padded to dpq) and the squared norm of those bfloat16 values, and resets
+// its shared threshold.
+__global__ void tc_scatter(const int32_t* __restrict__ queues, const int32_t* __restrict__ pa,
+                           const float* __restrict__ q, int d, int dpq, int32_t* counters, int32_t* bucket,
+                           int64_t n, int32_t* aq, float* aqn, __nv_bfloat16* qb, unsigned long long* qthr) {
+  const int nA = counters[CNT_QA];
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nA; i += warps) {
+    const int qi = queues[i];
+    int pos = 0;
+    if (lane == 0) {
+      const int b = (int)(((int64_t)pa[qi] * kBuckets) / (n + 1));
+      pos = atomicAdd(&bucket[b], 1);
+    }
+    pos = __shfl_sync(kFull, pos, 0);
+    float ss = 0.f;
+    for (int c = lane; c < dpq; c += 32) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(c < d ? q[(int64_t)qi * d + c] : 0.f);
+      qb[(int64_t)pos * dpq + c] = h;
+      const float f = __bfloat162float(h);
+      ss = fmaf(f, f, ss);
+    }
+    for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(kFull, ss, off);
+    if (lane == 0) {
+      aq[pos] = qi;
+      aqn[pos] = ss;
+      qthr[pos] = kKeyMax;
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult qr;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
+            cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2D bfloat16 tensor map: rows of `cols` elements, `row_bytes` apart, boxes of
+// box_cols x box_rows with 128-byte swizzle; reads outside the tensor return 0.
+bool encode_2d_bf16(CUtensorMap* tm, const void* base, uint64_t cols, uint64_t rows, uint64_t row_bytes,
+                    uint32_t box_cols, uint32_t box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {box_cols, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
+
+}  // namespace
+
+bool tc_scan_available(const DeviceIndex& ix, const Params& p) {
+  return p.dtype == UNIFY_BF16 && p.tc_scan && (ix.dp % 8) == 0 && rerank_count(p) <= kTcRMax &&
+         ix.d <= 1024 && encode_fn() != nullptr;
+}
+
+cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
+                          const Outputs& o, cudaStream_t st) {
+  const int dpq = ((ix.d + kTcKc - 1) / kTcKc) * kTcKc;
+  cudaError_t e = cudaMemsetAsync(sc.tc_bucket, 0, kBuckets * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  tc_bucket_count<<<ix.num_sms * 2, 256, 0, st>>>(sc.queues, sc.pa, sc.counters, sc.tc_bucket, ix.n);
+  tc_bucket_scan<<<1, kBuckets, 0, st>>>(sc.tc_bucket);
+  tc_scatter<<<ix.num_sms * 4, 256, 0, st>>>(sc.queues, sc.pa, q, ix.d, dpq, sc.counters, sc.tc_bucket, ix.n,
+                                             sc.tc_aq, sc.tc_aqn, reinterpret_cast<__nv_bfloat16*>(sc.tc_qb),
+                                             sc.tc_thr);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap tmX, tmQ;
+  if (!encode_2d_bf16(&tmX, ix.vts_bf16, (uint64_t)ix.dp, (uint64_t)ix.n, (uint64_t)ix.dp * 2, kTcKc, kTcRows) ||
+      !encode_2d_bf16(&tmQ, sc.tc_qb, (uint64_t)dpq, (uint64_t)sc.tc_rows, (uint64_t)dpq * 2, kTcKc, kTcQ))
+    return cudaErrorInvalidValue;
+  const int tiles = (int)(sc.tc_rows / kTcQ);
+  TcArgs a;
+  a.sorted_ids = ix.sorted_ids;
+  a.xn = ix.xn_bf16_sorted;
+  a.vec = ix.vec;
+  a.q = q;
+  a.dp4 = ix.dp / 4;
+  a.d = ix.d;
+  a.KC = dpq / kTcKc;
+  a.num_sms = ix.num_sms;
+  a.n = ix.n;
+  a.pa = sc.pa;
+  a.pb = sc.pb;
+  a.aq = sc.tc_aq;
+  a.aqn = sc.tc_aqn;
+  a.tile_lo = sc.tc_tile;
+  a.tile_nb = sc.tc_tile + tiles;
+  a.tile_units = sc.tc_tile + 2 * tiles;
+  a.unit_off = sc.tc_tile + 3 * tiles;
+  a.part = sc.tc_part;
+  a.qthr = sc.tc_thr;
+  a.counters = sc.counters;
+  a.k = p.k;
+  a.R = rerank_count(p);
+  a.o = o;
+  tc_tile_prep<<<ix.num_sms, 256, 0, st>>>(a);
+  tc_unit_plan<<<1, 1024, 0, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = tc_smem_bytes();
+  e = cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  tc_scan_kernel<<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // FP32 re-rank with the row-width variants of the search kernel
+  const int ch = (a.dp4 + 31) / 32;
+  if (ch <= 1)
+    tc_finish<1, 16><<<ix.num_sms * 4, 128, 0, st>>>(a);
+  else if (ch <= 2)
+    tc_finish<2, 8><<<ix.num_sms * 4, 128, 0, st>>>(a);
+  else if (ch <= 4)
+    tc_finish<4, 4><<<ix.num_sms * 4, 128, 0, st>>>(a);
+  else
+    tc_finish<8, 2><<<ix.num_sms * 4, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace unify

@@ -363,3 +363,52 @@ def test_other_widths_real_data(U, dataset, request):
                     # forced post-filtering on narrow ranges is poor by design (the
                     # paper's motivation for routing); the routed batch must be good
                     assert rec.mean() >= 0.85, (dataset, dtype, regs, rec.mean())
+
+
+def test_tensor_core_scan_matches_warp_scan(U, c2_small_index):
+    """The tcgen05 pre-filter scan (bf16 MMA over row tiles shared by 128 queries,
+    per-query heaps, FP32 re-rank) gives the warp scan's rows exactly on integer
+    data: ragged tiles (300, 129, 65 and 1 queries), several work units per tile,
+    and re-rank widths R = k, 4k, 6k."""
+    w, path = c2_small_index
+    ix = U.Index(path)
+    for nq in (len(w.lo), 129, 65, 1):
+        Q, lo, hi = w.queries[:nq], w.lo[:nq], w.hi[:nq]
+        ref = _np(ix.search(Q, lo, hi, w.k, strategy="pre"))
+        for rm in (1, 4, 6):
+            tc = _np(ix.search(Q, lo, hi, w.k, strategy="pre",
+                               params=U.Params.defaults(dtype=U.BF16, rerank_mult=rm, tc_scan=1)))
+            for key in ("ids", "dist", "count", "status"):
+                assert np.array_equal(tc[key], ref[key]), (nq, rm, key)
+    # routed batch: the tensor-core phase takes the pre-filter queries, the search
+    # kernel the others, and the rows equal the warp-scan batch's
+    p0 = U.Params.defaults(dtype=U.BF16, rerank_mult=4, tau_a=w.n // 20, tau_b=w.n // 2, cand_cap=CAND)
+    p1 = U.Params.defaults(dtype=U.BF16, rerank_mult=4, tau_a=w.n // 20, tau_b=w.n // 2, cand_cap=CAND, tc_scan=1)
+    r0 = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy="auto", params=p0))
+    r1 = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy="auto", params=p1))
+    for key in ("ids", "dist", "count", "status"):
+        assert np.array_equal(r0[key], r1[key]), key
+
+
+def test_tensor_core_scan_wide_rows(U, c5_small_index):
+    """d = 960 (15 K-slices per block) on real data: the bf16 candidates are chosen
+    by the expanded distance form, so rows may differ from the exact scan only by
+    near-ties; every returned distance is the float32 distance of its id (within
+    1e-4 relative of FP64, d = 960 terms), and recall against the exact answer is
+    near 1."""
+    w, path = c5_small_index
+    ix = U.Index(path)
+    X = w.vectors.astype(np.float64)
+    ex = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, w.k)
+    r = _np(ix.search(w.queries, w.lo, w.hi, w.k, strategy="pre",
+                      params=U.Params.defaults(dtype=U.BF16, rerank_mult=4, tc_scan=1)))
+    _valid(w, r, w.lo, w.hi)
+    assert np.array_equal(r["count"], np.minimum(ex[2], w.k))
+    assert np.all(r["status"] == 0)
+    for i in range(len(w.lo)):
+        c = r["count"][i]
+        ids = r["ids"][i, :c]
+        d64 = ((X[ids] - w.queries[i].astype(np.float64)) ** 2).sum(1)
+        assert np.all(np.abs(r["dist"][i, :c] - d64) <= 1e-4 * np.maximum(d64, 1e-30))
+    rec = oracle.recall(r["ids"], ex[0], ex[2], w.k)
+    assert rec.mean() >= 0.99, rec.mean()
