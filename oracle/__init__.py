@@ -57,6 +57,8 @@ def _load():
                                              ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                              ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P]
             lib.orc_search_batch.restype = ctypes.c_int
+            lib.orc_search_batch_sel.argtypes = lib.orc_search_batch.argtypes + [ctypes.c_int]
+            lib.orc_search_batch_sel.restype = ctypes.c_int
             lib.orc_route_batch.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                             P, P, P, P, P]
             lib.orc_route_batch.restype = ctypes.c_int
@@ -118,8 +120,10 @@ class OracleIndex:
         self.close()
 
     def search(self, queries, lo, hi, k, ef=100, m=16, ef_post=None, strategy="auto",
-               tau_a=0, tau_b=0, threads=None):
-        """O2. Returns dict(ids, dist, count, strategy, n_dist, n_exp)."""
+               tau_a=0, tau_b=0, threads=None, selection=2):
+        """O2. Returns dict(ids, dist, count, strategy, n_dist, n_exp). selection: 2 = S2
+        (first ceil(m/S') slots per intersected chunk), 1 = S1 (the m neighbours nearest
+        to the expanded object over all intersected chunks)."""
         Q = _c(queries, np.float32)
         lo, hi = _c(lo, np.int64), _c(hi, np.int64)
         nq = lo.shape[0]
@@ -127,10 +131,10 @@ class OracleIndex:
                    count=np.empty(nq, np.int64), strategy=np.empty(nq, np.int32),
                    n_dist=np.empty(nq, np.int64), n_exp=np.empty(nq, np.int64))
         st = STRATEGY[strategy] if isinstance(strategy, str) else int(strategy)
-        rc = self._lib.orc_search_batch(self._h, _p(Q), _p(lo), _p(hi), nq, k, ef, m, ef_post or ef, st,
-                                        tau_a, tau_b, threads or default_threads(), _p(out["ids"]),
-                                        _p(out["dist"]), _p(out["count"]), _p(out["strategy"]),
-                                        _p(out["n_dist"]), _p(out["n_exp"]))
+        rc = self._lib.orc_search_batch_sel(self._h, _p(Q), _p(lo), _p(hi), nq, k, ef, m, ef_post or ef, st,
+                                            tau_a, tau_b, threads or default_threads(), _p(out["ids"]),
+                                            _p(out["dist"]), _p(out["count"]), _p(out["strategy"]),
+                                            _p(out["n_dist"]), _p(out["n_exp"]), int(selection))
         if rc != 0:
             raise RuntimeError(f"orc_search_batch failed: {rc}")
         return out

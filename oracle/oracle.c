@@ -28,8 +28,12 @@
  *      "the object lies in an intersected segment"; layer 0 runs it with k = ef and
  *      the test lo <= a <= hi. Start: the global entry point (highest level).
  *      If ann stays empty on a layer, the entry point is kept.
- *   R6 Selection S2: the first ceil(m / S') slots of every intersected chunk,
- *      S' = number of intersected segments, chunks visited in ascending segment id.
+ *   R6 Selection S2 (default): the first ceil(m / S') slots of every intersected
+ *      chunk, S' = number of intersected segments, chunks visited in ascending
+ *      segment id. Selection S1 (Section 4.2, first strategy; Section 5.7): every
+ *      neighbour in the intersected chunks, ordered by (distance to the expanded
+ *      object, id) with distances in FP64, and the first m of them. Only distances
+ *      to the query count as distance evaluations.
  *   R7 Post-filter: Algorithm 1 over bitmap-marked slots (k = 1 on upper layers,
  *      k = ef_post on layer 0), then the range filter, then the first k.
  *   R8 A result holds min(k, found) entries sorted by (distance, id); the rest of
@@ -342,6 +346,7 @@ int orc_route(int64_t Y, int64_t tau_a, int64_t tau_b) {
 typedef struct {
   heap_t cand, ann;
   unsigned char* visited;
+  void* sel;  /* S1 selection buffer, S * M keys */
   int64_t n_dist, n_exp;
 } scratch_t;
 
@@ -353,6 +358,7 @@ static int sc_init(scratch_t* s, int64_t n) {
 }
 
 static void sc_free(scratch_t* s) {
+  free(s->sel);
   free(s->cand.a);
   free(s->ann.a);
   free(s->visited);
@@ -419,8 +425,27 @@ static int alg1_global(const orc_index* ix, const float* q, int32_t ep, int l, i
 
 /* Algorithm 7 (HybridFilteringLayer) on layer l with the selection of R6. The ann
  * test is lo <= a <= hi on layer 0 and "in an intersected segment" above (R5). */
+/* Selection S1 (R6): the neighbours of o in the intersected chunks, by (FP64
+ * distance to o, id); the first m go to sel[0, return value). */
+static int select_s1(const orc_index* ix, const int32_t* adj, int32_t o, int m, uint32_t mask, key_t_* sel) {
+  int n = 0;
+  const float* xo = ix->vectors + (int64_t)o * ix->d;
+  for (int i = 0; i < ix->S; ++i) {
+    if (!((mask >> i) & 1u)) continue;
+    const int32_t* chunk = adj + (int64_t)i * ix->M;
+    for (int t = 0; t < ix->M; ++t) {
+      int32_t v = chunk[t];
+      if (v < 0) break;
+      key_t_ kv = {gamma64(xo, ix->vectors + (int64_t)v * ix->d, ix->d), v};
+      sel[n++] = kv;
+    }
+  }
+  qsort(sel, (size_t)n, sizeof(key_t_), key_cmp);
+  return n < m ? n : m;
+}
+
 static int alg7(const orc_index* ix, const float* q, int32_t ep, int l, int k, int m, uint32_t mask,
-                int64_t lo, int64_t hi, scratch_t* s) {
+                int64_t lo, int64_t hi, int selection, scratch_t* s) {
   heap_t *cand = &s->cand, *ann = &s->ann;
   cand->n = 0;
   ann->n = 0;
@@ -441,21 +466,37 @@ static int alg7(const orc_index* ix, const float* q, int32_t ep, int l, int k, i
     if (ann->n >= k && key_less(ann->a[0], o)) break;
     s->n_exp++;
     const int32_t* adj = row_adj(ix, (int32_t)o.id, l);
-    for (int i = 0; i < ix->S; ++i) {
-      if (!((mask >> i) & 1u)) continue;
-      const int32_t* chunk = adj + (int64_t)i * ix->M;
-      for (int t = 0; t < per; ++t) {
-        int32_t v = chunk[t];
-        if (v < 0) break;
-        if (s->visited[v]) continue;
-        s->visited[v] = 1;
-        key_t_ kv = {gamma64(q, ix->vectors + (int64_t)v * ix->d, ix->d), v};
-        s->n_dist++;
-        if (ann->n < k || key_less(kv, ann->a[0])) {
-          if (heap_push(cand, kv)) return -1;
-          if (ANN_TEST(v) && heap_push(ann, kv)) return -1;
-          if (ann->n > k) heap_pop(ann);
+    /* the selected neighbours, in selection order */
+    int nsel = 0;
+    if (selection == 1) {
+      if (!s->sel) {
+        s->sel = malloc((size_t)ix->S * ix->M * sizeof(key_t_));
+        if (!s->sel) return -1;
+      }
+      nsel = select_s1(ix, adj, (int32_t)o.id, m, mask, (key_t_*)s->sel);
+    }
+    for (int i = 0, t = 0, j = 0;;) {
+      int32_t v;
+      if (selection == 1) {
+        if (j >= nsel) break;
+        v = (int32_t)((key_t_*)s->sel)[j++].id;
+      } else {
+        while (i < ix->S && (!((mask >> i) & 1u) || t >= per || adj[(int64_t)i * ix->M + t] < 0)) {
+          ++i;
+          t = 0;
         }
+        if (i >= ix->S) break;
+        v = adj[(int64_t)i * ix->M + t];
+        ++t;
+      }
+      if (s->visited[v]) continue;
+      s->visited[v] = 1;
+      key_t_ kv = {gamma64(q, ix->vectors + (int64_t)v * ix->d, ix->d), v};
+      s->n_dist++;
+      if (ann->n < k || key_less(kv, ann->a[0])) {
+        if (heap_push(cand, kv)) return -1;
+        if (ANN_TEST(v) && heap_push(ann, kv)) return -1;
+        if (ann->n > k) heap_pop(ann);
       }
     }
   }
@@ -488,15 +529,15 @@ static int64_t strategy_post(const orc_index* ix, const float* q, int64_t lo, in
 
 /* Strategy C (R5, R6). */
 static int64_t strategy_hybrid(const orc_index* ix, const float* q, int64_t lo, int64_t hi, int k,
-                               int ef, int m, scratch_t* s, key_t_* out) {
+                               int ef, int m, int selection, scratch_t* s, key_t_* out) {
   uint32_t mask = orc_segment_mask(ix, lo, hi);
   if (mask == 0) return 0;
   int32_t ep = ix->entry_global;
   for (int l = ix->max_level; l >= 1; --l) {
-    if (alg7(ix, q, ep, l, 1, m, mask, lo, hi, s)) return -1;
+    if (alg7(ix, q, ep, l, 1, m, mask, lo, hi, selection, s)) return -1;
     if (s->ann.n > 0) ep = (int32_t)s->ann.a[0].id;
   }
-  if (alg7(ix, q, ep, 0, ef, m, mask, lo, hi, s)) return -1;
+  if (alg7(ix, q, ep, 0, ef, m, mask, lo, hi, selection, s)) return -1;
   int64_t c = s->ann.n;
   key_t_* tmp = (key_t_*)malloc((size_t)(c > 0 ? c : 1) * sizeof(key_t_));
   if (!tmp) return -1;
@@ -514,7 +555,7 @@ typedef struct {
   const float* Q;
   const int64_t *lo, *hi;
   int64_t nq;
-  int k, ef, m, ef_post, strategy;
+  int k, ef, m, ef_post, strategy, selection;
   int64_t tau_a, tau_b;
   int64_t* out_ids;
   double* out_dist;
@@ -555,7 +596,7 @@ static void* search_worker(void* arg) {
     int64_t c;
     if (st == STRAT_A) c = strategy_pre(ix, q, lo, hi, b->k, &s, out);
     else if (st == STRAT_B) c = strategy_post(ix, q, lo, hi, b->k, b->ef_post, &s, out);
-    else c = strategy_hybrid(ix, q, lo, hi, b->k, b->ef, b->m, &s, out);
+    else c = strategy_hybrid(ix, q, lo, hi, b->k, b->ef, b->m, b->selection, &s, out);
     if (c < 0) {
       pthread_mutex_lock(&b->mu); b->failed = 1; pthread_mutex_unlock(&b->mu);
       c = 0;
@@ -574,20 +615,22 @@ static void* search_worker(void* arg) {
   return NULL;
 }
 
-/* O2 over a batch of queries. strategy: 0 = A, 1 = C, 2 = B, -1 = range-aware (R3).
+/* O2 over a batch of queries. strategy: 0 = A, 1 = C, 2 = B, -1 = range-aware (R3);
+ * selection: 2 = S2, 1 = S1 (R6) for Strategy C.
  * Queries are independent; threads only split the batch. */
-int orc_search_batch(const orc_index* ix, const float* Q, const int64_t* lo, const int64_t* hi,
-                     int64_t nq, int k, int ef, int m, int ef_post, int strategy, int64_t tau_a,
-                     int64_t tau_b, int threads, int64_t* out_ids, double* out_dist,
-                     int64_t* out_count, int32_t* out_strategy, int64_t* out_ndist, int64_t* out_nexp) {
+int orc_search_batch_sel(const orc_index* ix, const float* Q, const int64_t* lo, const int64_t* hi,
+                         int64_t nq, int k, int ef, int m, int ef_post, int strategy, int64_t tau_a,
+                         int64_t tau_b, int threads, int64_t* out_ids, double* out_dist,
+                         int64_t* out_count, int32_t* out_strategy, int64_t* out_ndist, int64_t* out_nexp,
+                         int selection) {
   if (!ix || !Q || !lo || !hi || nq < 0 || k < 1 || ef < 1 || m < 1 || ef_post < 1 || !out_ids ||
-      !out_dist || !out_count || strategy < -1 || strategy > 2)
+      !out_dist || !out_count || strategy < -1 || strategy > 2 || (selection != 1 && selection != 2))
     return ORC_EARG;
   if (threads < 1) threads = 1;
   batch_t b;
   memset(&b, 0, sizeof(b));
   b.ix = ix; b.Q = Q; b.lo = lo; b.hi = hi; b.nq = nq; b.k = k; b.ef = ef; b.m = m;
-  b.ef_post = ef_post; b.strategy = strategy; b.tau_a = tau_a; b.tau_b = tau_b;
+  b.ef_post = ef_post; b.strategy = strategy; b.tau_a = tau_a; b.tau_b = tau_b; b.selection = selection;
   b.out_ids = out_ids; b.out_dist = out_dist; b.out_count = out_count;
   b.out_strategy = out_strategy; b.out_ndist = out_ndist; b.out_nexp = out_nexp;
   pthread_mutex_init(&b.mu, NULL);
@@ -601,6 +644,15 @@ int orc_search_batch(const orc_index* ix, const float* Q, const int64_t* lo, con
   free(th);
   pthread_mutex_destroy(&b.mu);
   return b.failed ? ORC_ENOMEM : ORC_OK;
+}
+
+/* O2 with selection S2. */
+int orc_search_batch(const orc_index* ix, const float* Q, const int64_t* lo, const int64_t* hi,
+                     int64_t nq, int k, int ef, int m, int ef_post, int strategy, int64_t tau_a,
+                     int64_t tau_b, int threads, int64_t* out_ids, double* out_dist,
+                     int64_t* out_count, int32_t* out_strategy, int64_t* out_ndist, int64_t* out_nexp) {
+  return orc_search_batch_sel(ix, Q, lo, hi, nq, k, ef, m, ef_post, strategy, tau_a, tau_b, threads, out_ids,
+                              out_dist, out_count, out_strategy, out_ndist, out_nexp, 2);
 }
 
 typedef struct {

@@ -297,6 +297,67 @@ def test_hybrid_unbounded_beam_is_exact(c1_index, tmp_path):
     assert nonempty >= 30
 
 
+def test_hybrid_s1_unbounded_beam_is_exact(c1_index, tmp_path):
+    """Selection S1 (Section 4.2's first strategy): every neighbour in the intersected
+    chunks, ordered by distance to the expanded object, the first m. With ef above
+    |R| the result must be the exact top-k of the in-range part of the closure over
+    those edges, computed here independently: numpy FP64 owner distances, lexsort by
+    (distance, id), the first m per object, scipy BFS. The S1 edges must also differ
+    from the S2 edges of the same m for some query (the pin is not vacuous)."""
+    w, path = c1_index
+    flat = str(tmp_path / "flat.idx")
+    ix = _flat_copy(path, flat)
+    n, S, M = ix["n"], ix["S"], ix["M"]
+    adj = np.asarray(ix["adj0"]).reshape(n, S * M)
+    X = w.vectors.astype(np.float64)
+    safe = np.where(adj >= 0, adj, 0)
+    dv = ((X[safe] - X[:, None, :]) ** 2).sum(-1)  # owner distance of every slot
+    oi = oracle.OracleIndex(flat)
+    sel = np.flatnonzero(w.fractions <= 0.10)[:24]
+    Q, lo, hi = w.queries[sel], w.lo[sel], w.hi[sel]
+    m = 8
+    r = oi.search(Q, lo, hi, w.k, ef=n, m=m, strategy="hybrid", selection=1)
+    rt = oi.route(lo, hi)
+    ep = ix["entry_global"]
+    nonempty = differs = 0
+    slot_seg = np.repeat(np.arange(S), M)
+    for i in range(len(sel)):
+        mask = int(rt["mask"][i])
+        ok = (adj >= 0) & (((mask >> slot_seg) & 1) == 1)[None, :]
+        d = np.where(ok, dv, np.inf)
+        ids = np.where(ok, adj, np.iinfo(np.int32).max)
+        order = np.lexsort((ids, d), axis=-1)[:, :m]
+        pick = np.take_along_axis(ok, order, axis=1)
+        vv = np.repeat(np.arange(n), m).reshape(n, m)[pick]
+        uu = np.take_along_axis(adj, order, axis=1)[pick]
+        reach = _closure(n, vv, uu, ep)
+        inr = reach[(w.attrs[reach] >= lo[i]) & (w.attrs[reach] <= hi[i])]
+        want = _topk_fp64(w.vectors, Q[i], inr, w.k)
+        nonempty += len(want) > 0
+        assert int(r["count"][i]) == len(want), i
+        assert np.array_equal(r["ids"][i, :len(want)], want), i
+        segs = [j for j in range(S) if (mask >> j) & 1]
+        per = min(M, -(-m // len(segs)))
+        ch = adj.reshape(n, S, M)[:, segs, :per].reshape(n, -1)
+        v2, t2 = np.nonzero(ch >= 0)
+        differs += set(zip(v2.tolist(), ch[v2, t2].tolist())) != set(zip(vv.tolist(), uu.tolist()))
+    assert nonempty >= 16
+    assert differs >= 1
+
+
+def test_s1_with_every_slot_equals_s2(c1_index):
+    """With m >= S'M both selections take every neighbour in the intersected chunks
+    (S1 only orders them differently, and one expansion's neighbours give the same
+    outcome in any order), so S1 and S2 must agree on ids, distances and counts."""
+    w, path = c1_index
+    oi = oracle.OracleIndex(path)
+    m = 16 * 32
+    a = oi.search(w.queries, w.lo, w.hi, w.k, ef=64, m=m, strategy="hybrid", selection=2)
+    b = oi.search(w.queries, w.lo, w.hi, w.k, ef=64, m=m, strategy="hybrid", selection=1)
+    for key in ("ids", "dist", "count", "n_dist", "n_exp"):
+        assert np.array_equal(a[key], b[key]), key
+
+
 def test_post_unbounded_beam_is_exact(c1_index, tmp_path):
     """Strategy B with ef_post >= n keeps every node reachable from the entry point
     over the bitmap-marked slots; after the range filter the result must be the
