@@ -384,7 +384,7 @@ def main():
     m32 = measure(params, args.steps, args.warmup)
     clk = clocks.stop()
     value, ms_max, out = m32["value"], m32["ms"], m32["out"]
-    digest = src_digest("search.cu", "common.cuh")
+    digest = src_digest("search.cu", "common.cuh", "warp_ops.cuh", "internal.h")
     roofline = {"bound": "hbm", "achieved": m32["achieved"], "peak": hbm, "unit": "GB/s",
                 "frac": m32["achieved"] / hbm, "traffic": NCU_TRAFFIC.get(("batch_kernel", digest)),
                 "kernel": "batch_kernel (route excluded)", "peak_source": f"{peak_kind} hbm_gbs",

@@ -37,7 +37,7 @@ class Params(ctypes.Structure):
                 ("rerank_mult", ctypes.c_int), ("dtype", ctypes.c_int), ("tau_a", ctypes.c_int64),
                 ("tau_b", ctypes.c_int64), ("cand_cap", ctypes.c_int), ("visited_cap", ctypes.c_int),
                 ("max_expansions", ctypes.c_int), ("warps_per_block", ctypes.c_int),
-                ("scan_rows", ctypes.c_int), ("reg_budget", ctypes.c_int), ("tc_scan", ctypes.c_int)]
+                ("scan_rows", ctypes.c_int), ("reg_budget", ctypes.c_int), ("tc_scan", ctypes.c_int), ("selection", ctypes.c_int)]
 
     @classmethod
     def defaults(cls, **kw) -> "Params":

@@ -149,12 +149,15 @@ int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Para
   p.scan_rows = d.scan_rows;
   p.reg_budget = d.reg_budget;
   p.tc_scan = d.tc_scan;
+  p.selection = d.selection;
   p.dtype = d.dtype;
   p.rerank_mult = d.rerank_mult;
   p.tau_a = d.tau_a >= 0 ? d.tau_a : ix.n / 100;
   p.tau_b = d.tau_b >= 0 ? d.tau_b : ix.n / 2;
   if (p.ef < 1 || p.ef > 2048 || p.ef_post < 1 || p.ef_post > 2048) return fail(UNIFY_E_ARG, "ef and ef_post must be in [1, 2048]");
   if (p.m < 1 || p.m > 1024) return fail(UNIFY_E_ARG, "m must be in [1, 1024]");
+  if (p.selection != 1 && p.selection != 2) return fail(UNIFY_E_ARG, "selection must be 1 (S1) or 2 (S2)");
+  if (p.selection == 1 && p.m > 64) return fail(UNIFY_E_ARG, "selection S1 takes m <= 64");
   if (p.cand_cap < 32 || p.cand_cap > kMaxCand) return fail(UNIFY_E_ARG, "cand_cap must be in [32, 4096]");
   if (d.visited_cap < 64 || d.visited_cap > 65536 || (d.visited_cap & (d.visited_cap - 1)))
     return fail(UNIFY_E_ARG, "visited_cap must be a power of two in [64, 65536]");
@@ -287,6 +290,7 @@ extern "C" void unify_default_params(unify_params_t* p) {
   p->scan_rows = 8192;
   p->reg_budget = 128;
   p->tc_scan = 0;
+  p->selection = 2;
 }
 
 extern "C" const char* unify_last_error(void) { return g_last_error.c_str(); }

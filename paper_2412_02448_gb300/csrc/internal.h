@@ -102,7 +102,7 @@ enum {
 };
 
 struct Params {
-  int k, ef, m, ef_post, cand_cap, vis_log2, max_exp, warps_per_block, scan_rows, rerank_mult, reg_budget, tc_scan;
+  int k, ef, m, ef_post, cand_cap, vis_log2, max_exp, warps_per_block, scan_rows, rerank_mult, reg_budget, tc_scan, selection;
   int64_t tau_a, tau_b;
   unify_dtype_t dtype;
 };

@@ -78,6 +78,7 @@ struct BatchArgs {
   uint64_t* part;
   int32_t* counters;
   int k, ef_h, ef_p, m, cand_cap, ann_cap, vis_log2, max_exp;
+  int s1;  // hybrid selection S1 (the m neighbours nearest to the expanded object) instead of S2
   int warp_bytes;
   int skip_scan;  // the pre-filter queries were searched by the tensor-core scan
   Outputs o;
@@ -90,7 +91,7 @@ struct WarpMem {
   uint8_t* Ef;
   int* R;
   int* clist;
-  int* slots;
+  int* slots;  // post-filter: 64 bitmap-marked slots; hybrid S1: 64 selected keys (uint64)
 };
 
 __host__ __device__ inline int flag_cap(int cand_cap, int ann_cap) {
@@ -100,7 +101,7 @@ __host__ __device__ inline int flag_cap(int cand_cap, int ann_cap) {
 __host__ __device__ inline int batch_warp_bytes(int cand_cap, int ann_cap, int vis_log2) {
   int b = cand_cap * 8 + ann_cap * 8 + (4 << vis_log2);
   b += flag_cap(cand_cap, ann_cap);
-  b += 32 * 4 + 32 * 4 + 64 * 4;
+  b += 32 * 4 + 32 * 4 + 64 * 8;
   return (b + 15) & ~15;
 }
 
@@ -199,7 +200,38 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
     const int64_t row = (l == 0) ? (int64_t)o : ((int64_t)__ldg(a.upper_base + o) + (l - 1));
     const int32_t* adj = (l == 0 ? a.adj0 : a.adjU) + row * SM;
     int ncand;
-    if (hybrid) {
+    if (hybrid && a.s1) {
+      // Selection S1: every neighbour of o in the intersected chunks, by (distance
+      // to o, id), the first m (these owner distances are not query distance
+      // evaluations and are not counted)
+      float4 xo[CH];
+      {
+        const unsigned char* orow = a.vt + (int64_t)o * a.row_bytes;
+        const float sc = a.scale ? __ldg(a.scale + o) : 1.f;
+#pragma unroll
+        for (int t = 0; t < CH; ++t) {
+          const int c = lane + 32 * t;
+          xo[t] = c < a.dp4 ? T::load(orow, c, sc) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+      uint64_t* selk = reinterpret_cast<uint64_t*>(w.slots);
+      const int msel = a.m < 64 ? a.m : 64;
+      const int tot = Sp * a.M;
+      int ns = 0;
+      for (int b0 = 0; b0 < tot; b0 += 32) {
+        const int ci = b0 + lane;
+        int cid = -1;
+        if (ci < tot) {
+          const int kseg = ci / a.M;
+          const int sl = ci - kseg * a.M;
+          const int sg = (int)__fns(mask, 0, kseg + 1);
+          cid = __ldg(adj + sg * a.M + sl);
+        }
+        const float dv = batch_dist<T, CH, G>(xo, cid, a.vt, a.row_bytes, a.scale, a.dp4, w.clist);
+        ns = topk_offer(selk, ns, msel, cid >= 0 ? make_key(dv, cid) : kKeyMax, w.R);
+      }
+      ncand = ns;
+    } else if (hybrid) {
       ncand = Sp * per;
     } else {
       // all bitmap words in one round trip, then compaction by ballots
@@ -229,11 +261,13 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
       if (bal) {
         const int o2 = key_id(E[cursor + __ffs(bal)]);
         const int32_t* adj2 = a.adj0 + (int64_t)o2 * SM;
-        if (hybrid) {
+        if (hybrid && !a.s1) {
           if (lane < ncand) {
             int sg;
             prefetch_l2(adj2 + hybrid_slot(lane, per, mask, a.M, &sg));
           }
+        } else if (hybrid) {
+          if (lane * 32 < SM) prefetch_l2(adj2 + lane * 32);
         } else {
           if (lane * 32 < SM) prefetch_l2(adj2 + lane * 32);
           if (lane == 31) prefetch_l2(a.gmask0 + (int64_t)o2 * a.W);
@@ -243,7 +277,10 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
     for (int rb = 0; rb < ncand; rb += 32) {
       const int ci = rb + lane;
       int cid = -1, cseg = 0;
-      if (ci < ncand) {
+      if (ci < ncand && hybrid && a.s1) {
+        cid = key_id(reinterpret_cast<const uint64_t*>(w.slots)[ci]);
+        cseg = -1;  // the range test below uses the position
+      } else if (ci < ncand) {
         int slot;
         if (hybrid) {
           slot = hybrid_slot(ci, per, mask, a.M, &cseg);
@@ -261,7 +298,7 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
       __syncwarp();
       bool need = false;
       int pv = 0;
-      if (hybrid && l == 0 && cid >= 0 && !((full_mask >> cseg) & 1u)) {
+      if (hybrid && l == 0 && cid >= 0 && (cseg < 0 || !((full_mask >> cseg) & 1u))) {
         need = true;
         pv = __ldg(a.pos + cid);
       }
@@ -658,6 +695,7 @@ cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* 
   a.ef_h = p.ef;
   a.ef_p = p.ef_post;
   a.m = p.m;
+  a.s1 = p.selection == 1 ? 1 : 0;
   a.cand_cap = p.cand_cap;
   a.ann_cap = batch_ann_cap(p);
   a.vis_log2 = p.vis_log2;

@@ -412,3 +412,36 @@ def test_tensor_core_scan_wide_rows(U, c5_small_index):
         assert np.all(np.abs(r["dist"][i, :c] - d64) <= 1e-4 * np.maximum(d64, 1e-30))
     rec = oracle.recall(r["ids"], ex[0], ex[2], w.k)
     assert rec.mean() >= 0.99, rec.mean()
+
+
+@pytest.mark.parametrize("m", [4, 12, 40])
+def test_hybrid_s1_matches_oracle(U, c2_small_index, m):
+    """Selection S1 (the m neighbours nearest to the expanded object over all
+    intersected chunks). On integer data every owner distance is an exact integer in
+    float32, so the GPU selects the oracle's neighbours and follows its traversal:
+    ids, distances, counts and expansion counts identical on unflagged rows; BF16
+    storage (exact on this data) gives the same rows; m above 64 is refused."""
+    w, path = c2_small_index
+    ix = U.Index(path)
+    oi = oracle.OracleIndex(path)
+    p = U.Params.defaults(m=m, cand_cap=CAND, selection=1)
+    r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=50, strategy="hybrid", params=p, counters=True))
+    o = oi.search(w.queries, w.lo, w.hi, w.k, ef=50, m=m, strategy="hybrid", selection=1)
+    ok = (r["status"] & EXACT_BITS) == 0
+    _valid(w, r, w.lo, w.hi)
+    assert ok.mean() > 0.8
+    assert np.array_equal(r["ids"][ok], o["ids"][ok])
+    assert np.array_equal(r["count"][ok], o["count"][ok])
+    assert np.array_equal(r["counters"][ok, 1], o["n_exp"][ok])
+    fin = np.isfinite(o["dist"][ok])
+    assert np.array_equal(r["dist"][ok][fin].astype(np.float64), o["dist"][ok][fin])
+    # S1 differs from S2 on this data (the variant is really taken)
+    s2 = oi.search(w.queries, w.lo, w.hi, w.k, ef=50, m=m, strategy="hybrid", selection=2)
+    assert not np.array_equal(o["n_exp"], s2["n_exp"])
+    b = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=50, strategy="hybrid", counters=True,
+                      params=U.Params.defaults(m=m, cand_cap=CAND, selection=1, dtype=U.BF16, rerank_mult=4)))
+    for key in ("ids", "dist", "count", "status"):
+        assert np.array_equal(b[key], r[key]), key
+    with pytest.raises(U.UnifyError):
+        ix.search(w.queries, w.lo, w.hi, w.k, ef=50, strategy="hybrid",
+                  params=U.Params.defaults(m=65, selection=1))
