@@ -390,6 +390,17 @@ def main():
                 "kernel": "batch_kernel (route excluded)", "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": m32["alg"], "algorithmic_bytes_by_strategy": m32["parts"]}
 
+    # hybrid selection S1 (the m neighbours nearest to the expanded object) with the
+    # same parameters, beside the tuned selection (the comparison of Section 5.7)
+    other_sel = None
+    if params.m <= 64:
+        ps = U.Params.defaults(**{f: getattr(params, f) for f, _ in U.Params._fields_})
+        ps.selection = 3 - params.selection
+        rs = measure(ps, max(3, args.steps // 2), args.warmup)
+        other_sel = {"selection": f"S{ps.selection}", "value": rs["value"], "ms_per_step": rs["ms"],
+                     "recall_by_fraction": {f"{100 * f_:g}%": round(v_, 4) for f_, v_ in rs["recall"].items()},
+                     "note": "same parameters as the headline, other hybrid selection"}
+
     # BF16 and FP8 (per-vector scale) storage with FP32 re-rank of 4k candidates
     precision = {}
     if not args.no_precision:
@@ -466,7 +477,7 @@ def main():
                        "params": {"ef": params.ef, "ef_post": params.ef_post, "m": params.m,
                                   "cand_cap": params.cand_cap, "visited_cap": params.visited_cap,
                                   "warps_per_block": params.warps_per_block, "scan_rows": params.scan_rows,
-                                  "reg_budget": params.reg_budget,
+                                  "reg_budget": params.reg_budget, "selection": f"S{params.selection}",
                                   "tau_a": params.tau_a, "tau_b": params.tau_b}},
             "recall_by_fraction": {f"{100 * f_:g}%": round(r_, 4) for f_, r_ in m32["recall"].items()},
             "routed": {"pre": int(m32["routed"][0]), "hybrid": int(m32["routed"][1]), "post": int(m32["routed"][2])},
@@ -476,6 +487,7 @@ def main():
             "timeline_us": m32["timeline"],
             "roofline": roofline,
             "precision": precision,
+            "hybrid_selection_other": other_sel,
             "cuda_graph": {"ms_per_step": graph_ms, "value": world * nq / (graph_ms / 1000.0),
                            "same_ids_as_direct": graph_ok},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -149,6 +149,9 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
                   {"reg_budget": 80, "visited_cap": 1024, "cand_cap": 256},
                   {"reg_budget": 64, "visited_cap": 512, "cand_cap": 256},
                   {"reg_budget": 64, "visited_cap": 1024, "cand_cap": 128}]
+    if cur.m <= 64:
+        # hybrid selection S1 instead of S2 (Section 5.7 compares the two)
+        shapes.append({"selection": 1})
     if cur.dtype == U.BF16:
         # pre-filter queries on the tensor cores instead of the warp scan
         shapes.append({"tc_scan": 1 - cur.tc_scan})
