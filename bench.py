@@ -216,6 +216,7 @@ def main():
     ap.add_argument("--tau-b", type=int, default=-1)
     ap.add_argument("--scan-rows", type=int, default=8192)
     ap.add_argument("--reg-budget", type=int, default=128)
+    ap.add_argument("--selection", type=int, default=2, choices=[1, 2], help="hybrid selection S1 or S2")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the BF16/FP8 lines")
@@ -282,7 +283,8 @@ def main():
         tau_b = args.tau_b
     base = U.Params.defaults(tau_a=tau_a, tau_b=tau_b, scan_rows=args.scan_rows, ef=args.ef, ef_post=args.ef_post or args.ef, m=args.m,
                              cand_cap=args.cand_cap, visited_cap=args.visited_cap,
-                             warps_per_block=args.warps_per_block, reg_budget=args.reg_budget)
+                             warps_per_block=args.warps_per_block, reg_budget=args.reg_budget,
+                             selection=args.selection)
     route = ix.route(lo, hi, tau_a, tau_b)
     pa, pb = route["pa"].cpu().numpy().astype(np.int64), route["pb"].cpu().numpy().astype(np.int64)
     mask = route["mask"].cpu().numpy().astype(np.uint32)
