@@ -59,6 +59,11 @@ def _load():
             lib.orc_search_batch.restype = ctypes.c_int
             lib.orc_search_batch_sel.argtypes = lib.orc_search_batch.argtypes + [ctypes.c_int]
             lib.orc_search_batch_sel.restype = ctypes.c_int
+            lib.orc_search_batch_ex.argtypes = lib.orc_search_batch_sel.argtypes + [P, P, P]
+            lib.orc_search_batch_ex.restype = ctypes.c_int
+            lib.orc_exact_knn_batch2.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int, P, P, P, P, P,
+                                                 ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P, P]
+            lib.orc_exact_knn_batch2.restype = ctypes.c_int
             lib.orc_route_batch.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                             P, P, P, P, P]
             lib.orc_route_batch.restype = ctypes.c_int
@@ -82,8 +87,9 @@ def default_threads() -> int:
     return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count() or 1)
 
 
-def exact_knn(vectors, attrs, queries, lo, hi, k, threads=None):
-    """O1. Returns (ids int64 [nq,k], dist float64 [nq,k], count int64 [nq])."""
+def exact_knn(vectors, attrs, queries, lo, hi, k, threads=None, attr2=None, lo2=None, hi2=None):
+    """O1. Returns (ids int64 [nq,k], dist float64 [nq,k], count int64 [nq]). With
+    attr2 (one value per object) the range is lo <= attr <= hi AND lo2 <= attr2 <= hi2."""
     lib = _load()
     X, A = _c(vectors, np.float32), _c(attrs, np.int64)
     Q = _c(queries, np.float32).reshape(-1, X.shape[1])
@@ -92,8 +98,12 @@ def exact_knn(vectors, attrs, queries, lo, hi, k, threads=None):
     ids = np.empty((nq, k), np.int64)
     dist = np.empty((nq, k), np.float64)
     cnt = np.empty(nq, np.int64)
-    rc = lib.orc_exact_knn_batch(_p(X), _p(A), X.shape[0], X.shape[1], _p(Q), _p(lo), _p(hi), nq, k,
-                                 threads or default_threads(), _p(ids), _p(dist), _p(cnt))
+    A2 = _c(attr2, np.int64) if attr2 is not None else None
+    lo2 = _c(lo2, np.int64) if attr2 is not None else None
+    hi2 = _c(hi2, np.int64) if attr2 is not None else None
+    rc = lib.orc_exact_knn_batch2(_p(X), _p(A), _p(A2), X.shape[0], X.shape[1], _p(Q), _p(lo), _p(hi),
+                                  _p(lo2), _p(hi2), nq, k, threads or default_threads(), _p(ids), _p(dist),
+                                  _p(cnt))
     if rc != 0:
         raise RuntimeError(f"orc_exact_knn_batch failed: {rc}")
     return ids, dist, cnt
@@ -120,10 +130,11 @@ class OracleIndex:
         self.close()
 
     def search(self, queries, lo, hi, k, ef=100, m=16, ef_post=None, strategy="auto",
-               tau_a=0, tau_b=0, threads=None, selection=2):
+               tau_a=0, tau_b=0, threads=None, selection=2, attr2=None, lo2=None, hi2=None):
         """O2. Returns dict(ids, dist, count, strategy, n_dist, n_exp). selection: 2 = S2
         (first ceil(m/S') slots per intersected chunk), 1 = S1 (the m neighbours nearest
-        to the expanded object over all intersected chunks)."""
+        to the expanded object over all intersected chunks). attr2/lo2/hi2 add the
+        conjunctive predicate lo2 <= attr2 <= hi2 on a second attribute (R9)."""
         Q = _c(queries, np.float32)
         lo, hi = _c(lo, np.int64), _c(hi, np.int64)
         nq = lo.shape[0]
@@ -131,10 +142,14 @@ class OracleIndex:
                    count=np.empty(nq, np.int64), strategy=np.empty(nq, np.int32),
                    n_dist=np.empty(nq, np.int64), n_exp=np.empty(nq, np.int64))
         st = STRATEGY[strategy] if isinstance(strategy, str) else int(strategy)
-        rc = self._lib.orc_search_batch_sel(self._h, _p(Q), _p(lo), _p(hi), nq, k, ef, m, ef_post or ef, st,
-                                            tau_a, tau_b, threads or default_threads(), _p(out["ids"]),
-                                            _p(out["dist"]), _p(out["count"]), _p(out["strategy"]),
-                                            _p(out["n_dist"]), _p(out["n_exp"]), int(selection))
+        A2 = _c(attr2, np.int64) if attr2 is not None else None
+        l2 = _c(lo2, np.int64) if attr2 is not None else None
+        h2 = _c(hi2, np.int64) if attr2 is not None else None
+        rc = self._lib.orc_search_batch_ex(self._h, _p(Q), _p(lo), _p(hi), nq, k, ef, m, ef_post or ef, st,
+                                           tau_a, tau_b, threads or default_threads(), _p(out["ids"]),
+                                           _p(out["dist"]), _p(out["count"]), _p(out["strategy"]),
+                                           _p(out["n_dist"]), _p(out["n_exp"]), int(selection),
+                                           _p(A2), _p(l2), _p(h2))
         if rc != 0:
             raise RuntimeError(f"orc_search_batch failed: {rc}")
         return out

@@ -38,6 +38,13 @@
  *      k = ef_post on layer 0), then the range filter, then the first k.
  *   R8 A result holds min(k, found) entries sorted by (distance, id); the rest of
  *      the row is padded with id -1 and distance +inf.
+ *   R9 Conjunctive predicate on a second attribute (Section 5.8, "multiple
+ *      single-attribute indexes"): the index is built on A1; a query adds
+ *      lo2 <= A2 <= hi2. Algorithm 7's layer-0 ann test requires both ranges (the
+ *      paper's change of its push-to-ann line); by the same reading Strategy A
+ *      keeps only rows that satisfy both (rows failing A2 are skipped before any
+ *      distance) and Strategy B's final filter tests both. Segments, masks and the
+ *      router use A1 alone.
  */
 #include <math.h>
 #include <pthread.h>
@@ -250,16 +257,20 @@ static key_t_ heap_pop(heap_t* h) {
 /* Definition 1: R = {i : lo <= a_i <= hi}; rank R by (Gamma(q, x_i), i) in FP64;
  * return the first min(k, |R|). Returns the number written; the rest of the row is
  * padded (R8). */
-int64_t orc_exact_knn(const float* X, const int64_t* A, int64_t n, int d, const float* q,
-                      int64_t lo, int64_t hi, int k, int64_t* out_ids, double* out_dist) {
+/* O1 with the R9 predicate: objects with lo <= A <= hi and (A2 NULL or
+ * lo2 <= A2 <= hi2). */
+static int64_t exact_knn2(const float* X, const int64_t* A, const int64_t* A2, int64_t n, int d, const float* q,
+                          int64_t lo, int64_t hi, int64_t lo2, int64_t hi2, int k, int64_t* out_ids,
+                          double* out_dist) {
+#define IN_R(i) (lo <= A[i] && A[i] <= hi && (!A2 || (lo2 <= A2[i] && A2[i] <= hi2)))
   int64_t r = 0;
   for (int64_t i = 0; i < n; ++i)
-    if (lo <= A[i] && A[i] <= hi) ++r;
+    if (IN_R(i)) ++r;
   key_t_* all = (key_t_*)malloc((size_t)(r > 0 ? r : 1) * sizeof(key_t_));
   if (!all) return -1;
   int64_t m = 0;
   for (int64_t i = 0; i < n; ++i)
-    if (lo <= A[i] && A[i] <= hi) {
+    if (IN_R(i)) {
       all[m].d = gamma64(q, X + i * (int64_t)d, d);
       all[m].id = i;
       ++m;
@@ -272,6 +283,12 @@ int64_t orc_exact_knn(const float* X, const int64_t* A, int64_t n, int d, const 
   }
   free(all);
   return c;
+#undef IN_R
+}
+
+int64_t orc_exact_knn(const float* X, const int64_t* A, int64_t n, int d, const float* q,
+                      int64_t lo, int64_t hi, int k, int64_t* out_ids, double* out_dist) {
+  return exact_knn2(X, A, NULL, n, d, q, lo, hi, 0, 0, k, out_ids, out_dist);
 }
 
 /* ------------------------------------------------------------ O2 pieces */
@@ -347,6 +364,8 @@ typedef struct {
   heap_t cand, ann;
   unsigned char* visited;
   void* sel;  /* S1 selection buffer, S * M keys */
+  const int64_t* a2;  /* second attribute by id, or NULL (R9) */
+  int64_t lo2, hi2;
   int64_t n_dist, n_exp;
 } scratch_t;
 
@@ -366,6 +385,11 @@ static void sc_free(scratch_t* s) {
 
 /* Strategy A: descend the skip list to the first in-range object, then a linear
  * scan along the layer-0 chain while the attribute is <= hi, keeping the k best. */
+/* The second-attribute predicate of R9 (true without a second attribute). */
+static int pred2(const scratch_t* s, int64_t v) {
+  return !s->a2 || (s->lo2 <= s->a2[v] && s->a2[v] <= s->hi2);
+}
+
 static int64_t strategy_pre(const orc_index* ix, const float* q, int64_t lo, int64_t hi, int k,
                             scratch_t* s, key_t_* out) {
   heap_t* ann = &s->ann;
@@ -373,6 +397,10 @@ static int64_t strategy_pre(const orc_index* ix, const float* q, int64_t lo, int
   if (lo > hi) return 0;
   int32_t v = orc_skiplist_first(ix, lo);
   while (v >= 0 && ix->attr[v] <= hi) {
+    if (!pred2(s, v)) {
+      v = ix->skip_next0[v];
+      continue;
+    }
     key_t_ kv = {gamma64(q, ix->vectors + (int64_t)v * ix->d, ix->d), v};
     s->n_dist++;
     if (ann->n < k) {
@@ -454,7 +482,7 @@ static int alg7(const orc_index* ix, const float* q, int32_t ep, int l, int k, i
   if (Sp == 0) return 0;
   int per = (m + Sp - 1) / Sp;
   if (per > ix->M) per = ix->M;
-#define ANN_TEST(v) (l == 0 ? (lo <= ix->attr[v] && ix->attr[v] <= hi) \
+#define ANN_TEST(v) (l == 0 ? (lo <= ix->attr[v] && ix->attr[v] <= hi && pred2(s, v)) \
                             : ((mask >> segment_of(ix, ix->attr[v])) & 1u))
   key_t_ e = {gamma64(q, ix->vectors + (int64_t)ep * ix->d, ix->d), ep};
   s->n_dist++;
@@ -522,7 +550,7 @@ static int64_t strategy_post(const orc_index* ix, const float* q, int64_t lo, in
   for (int64_t t = c - 1; t >= 0; --t) tmp[t] = heap_pop(&s->ann);
   int64_t w = 0;
   for (int64_t t = 0; t < c && w < k; ++t)
-    if (lo <= ix->attr[tmp[t].id] && ix->attr[tmp[t].id] <= hi) out[w++] = tmp[t];
+    if (lo <= ix->attr[tmp[t].id] && ix->attr[tmp[t].id] <= hi && pred2(s, tmp[t].id)) out[w++] = tmp[t];
   free(tmp);
   return w;
 }
@@ -557,6 +585,7 @@ typedef struct {
   int64_t nq;
   int k, ef, m, ef_post, strategy, selection;
   int64_t tau_a, tau_b;
+  const int64_t *a2, *lo2, *hi2;
   int64_t* out_ids;
   double* out_dist;
   int64_t* out_count;
@@ -593,6 +622,11 @@ static void* search_worker(void* arg) {
     }
     s.n_dist = 0;
     s.n_exp = 0;
+    s.a2 = b->a2;
+    if (b->a2) {
+      s.lo2 = b->lo2[i];
+      s.hi2 = b->hi2[i];
+    }
     int64_t c;
     if (st == STRAT_A) c = strategy_pre(ix, q, lo, hi, b->k, &s, out);
     else if (st == STRAT_B) c = strategy_post(ix, q, lo, hi, b->k, b->ef_post, &s, out);
@@ -618,19 +652,21 @@ static void* search_worker(void* arg) {
 /* O2 over a batch of queries. strategy: 0 = A, 1 = C, 2 = B, -1 = range-aware (R3);
  * selection: 2 = S2, 1 = S1 (R6) for Strategy C.
  * Queries are independent; threads only split the batch. */
-int orc_search_batch_sel(const orc_index* ix, const float* Q, const int64_t* lo, const int64_t* hi,
-                         int64_t nq, int k, int ef, int m, int ef_post, int strategy, int64_t tau_a,
-                         int64_t tau_b, int threads, int64_t* out_ids, double* out_dist,
-                         int64_t* out_count, int32_t* out_strategy, int64_t* out_ndist, int64_t* out_nexp,
-                         int selection) {
+int orc_search_batch_ex(const orc_index* ix, const float* Q, const int64_t* lo, const int64_t* hi,
+                        int64_t nq, int k, int ef, int m, int ef_post, int strategy, int64_t tau_a,
+                        int64_t tau_b, int threads, int64_t* out_ids, double* out_dist,
+                        int64_t* out_count, int32_t* out_strategy, int64_t* out_ndist, int64_t* out_nexp,
+                        int selection, const int64_t* attr2, const int64_t* lo2, const int64_t* hi2) {
   if (!ix || !Q || !lo || !hi || nq < 0 || k < 1 || ef < 1 || m < 1 || ef_post < 1 || !out_ids ||
-      !out_dist || !out_count || strategy < -1 || strategy > 2 || (selection != 1 && selection != 2))
+      !out_dist || !out_count || strategy < -1 || strategy > 2 || (selection != 1 && selection != 2) ||
+      (attr2 && (!lo2 || !hi2)))
     return ORC_EARG;
   if (threads < 1) threads = 1;
   batch_t b;
   memset(&b, 0, sizeof(b));
   b.ix = ix; b.Q = Q; b.lo = lo; b.hi = hi; b.nq = nq; b.k = k; b.ef = ef; b.m = m;
   b.ef_post = ef_post; b.strategy = strategy; b.tau_a = tau_a; b.tau_b = tau_b; b.selection = selection;
+  b.a2 = attr2; b.lo2 = lo2; b.hi2 = hi2;
   b.out_ids = out_ids; b.out_dist = out_dist; b.out_count = out_count;
   b.out_strategy = out_strategy; b.out_ndist = out_ndist; b.out_nexp = out_nexp;
   pthread_mutex_init(&b.mu, NULL);
@@ -646,6 +682,16 @@ int orc_search_batch_sel(const orc_index* ix, const float* Q, const int64_t* lo,
   return b.failed ? ORC_ENOMEM : ORC_OK;
 }
 
+/* O2 with one attribute and the given selection. */
+int orc_search_batch_sel(const orc_index* ix, const float* Q, const int64_t* lo, const int64_t* hi,
+                         int64_t nq, int k, int ef, int m, int ef_post, int strategy, int64_t tau_a,
+                         int64_t tau_b, int threads, int64_t* out_ids, double* out_dist,
+                         int64_t* out_count, int32_t* out_strategy, int64_t* out_ndist, int64_t* out_nexp,
+                         int selection) {
+  return orc_search_batch_ex(ix, Q, lo, hi, nq, k, ef, m, ef_post, strategy, tau_a, tau_b, threads, out_ids,
+                             out_dist, out_count, out_strategy, out_ndist, out_nexp, selection, NULL, NULL, NULL);
+}
+
 /* O2 with selection S2. */
 int orc_search_batch(const orc_index* ix, const float* Q, const int64_t* lo, const int64_t* hi,
                      int64_t nq, int k, int ef, int m, int ef_post, int strategy, int64_t tau_a,
@@ -658,6 +704,7 @@ int orc_search_batch(const orc_index* ix, const float* Q, const int64_t* lo, con
 typedef struct {
   const float* X; const int64_t* A; int64_t n; int d;
   const float* Q; const int64_t *lo, *hi; int64_t nq; int k;
+  const int64_t *A2, *lo2, *hi2;
   int64_t* out_ids; double* out_dist; int64_t* out_count;
   int64_t next; int failed; pthread_mutex_t mu;
 } exact_t;
@@ -669,24 +716,28 @@ static void* exact_worker(void* arg) {
     int64_t i = b->next++;
     pthread_mutex_unlock(&b->mu);
     if (i >= b->nq) break;
-    int64_t c = orc_exact_knn(b->X, b->A, b->n, b->d, b->Q + i * (int64_t)b->d, b->lo[i], b->hi[i], b->k,
-                              b->out_ids + i * b->k, b->out_dist + i * b->k);
+    int64_t c = exact_knn2(b->X, b->A, b->A2, b->n, b->d, b->Q + i * (int64_t)b->d, b->lo[i], b->hi[i],
+                           b->A2 ? b->lo2[i] : 0, b->A2 ? b->hi2[i] : 0, b->k, b->out_ids + i * b->k,
+                           b->out_dist + i * b->k);
     if (c < 0) { pthread_mutex_lock(&b->mu); b->failed = 1; pthread_mutex_unlock(&b->mu); c = 0; }
     b->out_count[i] = c;
   }
   return NULL;
 }
 
-/* O1 over a batch of queries (threads only split the batch). */
-int orc_exact_knn_batch(const float* X, const int64_t* A, int64_t n, int d, const float* Q,
-                        const int64_t* lo, const int64_t* hi, int64_t nq, int k, int threads,
-                        int64_t* out_ids, double* out_dist, int64_t* out_count) {
-  if (!X || !A || n < 0 || d < 1 || !Q || !lo || !hi || nq < 0 || k < 1 || !out_ids || !out_dist || !out_count)
+/* O1 over a batch of queries (threads only split the batch); A2 (with lo2, hi2)
+ * adds the conjunctive predicate of R9, or is NULL. */
+int orc_exact_knn_batch2(const float* X, const int64_t* A, const int64_t* A2, int64_t n, int d, const float* Q,
+                         const int64_t* lo, const int64_t* hi, const int64_t* lo2, const int64_t* hi2, int64_t nq,
+                         int k, int threads, int64_t* out_ids, double* out_dist, int64_t* out_count) {
+  if (!X || !A || n < 0 || d < 1 || !Q || !lo || !hi || nq < 0 || k < 1 || !out_ids || !out_dist ||
+      !out_count || (A2 && (!lo2 || !hi2)))
     return ORC_EARG;
   if (threads < 1) threads = 1;
   exact_t b;
   memset(&b, 0, sizeof(b));
   b.X = X; b.A = A; b.n = n; b.d = d; b.Q = Q; b.lo = lo; b.hi = hi; b.nq = nq; b.k = k;
+  b.A2 = A2; b.lo2 = lo2; b.hi2 = hi2;
   b.out_ids = out_ids; b.out_dist = out_dist; b.out_count = out_count;
   pthread_mutex_init(&b.mu, NULL);
   pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)threads);
@@ -699,6 +750,14 @@ int orc_exact_knn_batch(const float* X, const int64_t* A, int64_t n, int d, cons
   free(th);
   pthread_mutex_destroy(&b.mu);
   return b.failed ? ORC_ENOMEM : ORC_OK;
+}
+
+/* O1 over a batch of queries with one attribute. */
+int orc_exact_knn_batch(const float* X, const int64_t* A, int64_t n, int d, const float* Q,
+                        const int64_t* lo, const int64_t* hi, int64_t nq, int k, int threads,
+                        int64_t* out_ids, double* out_dist, int64_t* out_count) {
+  return orc_exact_knn_batch2(X, A, NULL, n, d, Q, lo, hi, NULL, NULL, nq, k, threads, out_ids, out_dist,
+                              out_count);
 }
 
 /* Routing fields per query by their definitions (R2, R3) plus the skip-list
