@@ -400,3 +400,96 @@ def test_results_are_valid(c1_index):
             ex_cnt = np.minimum(w.k, np.array([((w.attrs >= a) & (w.attrs <= b)).sum() for a, b in zip(w.lo, w.hi)]))
             if st == "pre":
                 assert np.array_equal(r["count"], ex_cnt)
+
+
+def _conj(w, seed=11):
+    from workloads import second_attribute
+    fr = np.array([0.2, 0.5, 1.0])[np.arange(len(w.lo)) % 3]
+    return second_attribute(w.n, fr, seed)
+
+
+def test_conjunctive_exact_equals_bruteforce(c1_index):
+    """O1 with a second attribute (lo <= A1 <= hi AND lo2 <= A2 <= hi2) against a
+    numpy FP64 brute force with lexsort by (distance, id): ids equal, distances equal
+    up to the rounding of a different summation order."""
+    w, _ = c1_index
+    a2, lo2, hi2 = _conj(w)
+    ids, dist, cnt = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, w.k, attr2=a2, lo2=lo2, hi2=hi2)
+    X = w.vectors.astype(np.float64)
+    for i in range(len(w.lo)):
+        inr = np.flatnonzero((w.attrs >= w.lo[i]) & (w.attrs <= w.hi[i]) & (a2 >= lo2[i]) & (a2 <= hi2[i]))
+        d = ((X[inr] - w.queries[i].astype(np.float64)) ** 2).sum(1)
+        o = np.lexsort((inr, d))[:w.k]
+        c = len(o)
+        # same ids; FP64 sums in another order agree to rounding
+        assert cnt[i] == c and np.array_equal(ids[i, :c], inr[o])
+        assert np.allclose(dist[i, :c], d[o], rtol=1e-12, atol=0)
+        assert np.all(ids[i, c:] == -1)
+
+
+def test_conjunctive_pre_equals_exact(c1_index):
+    """Strategy A with the conjunctive predicate equals O1 with it."""
+    w, path = c1_index
+    a2, lo2, hi2 = _conj(w)
+    oi = oracle.OracleIndex(path)
+    ex = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, w.k, attr2=a2, lo2=lo2, hi2=hi2)
+    r = oi.search(w.queries, w.lo, w.hi, w.k, strategy="pre", attr2=a2, lo2=lo2, hi2=hi2)
+    assert np.array_equal(r["ids"], ex[0]) and np.array_equal(r["count"], ex[2])
+    assert np.array_equal(r["dist"], ex[1])
+
+
+def test_conjunctive_unbounded_beams_are_exact(c1_index, tmp_path):
+    """With the beam above n, hybrid (S2 edges of the A1 mask) and post-filter (bitmap
+    edges) reach their whole closure; the conjunctive result must be the exact top-k
+    of the closure's objects satisfying both ranges (scipy BFS + numpy sort)."""
+    w, path = c1_index
+    flat = str(tmp_path / "flat.idx")
+    ix = _flat_copy(path, flat)
+    n, S, M = ix["n"], ix["S"], ix["M"]
+    a2, lo2, hi2 = _conj(w)
+    oi = oracle.OracleIndex(flat)
+    sel = np.flatnonzero(w.fractions <= 0.10)[:30]
+    Q, lo, hi, l2, h2 = w.queries[sel], w.lo[sel], w.hi[sel], lo2[sel], hi2[sel]
+    m = 16
+    rh = oi.search(Q, lo, hi, w.k, ef=n, m=m, strategy="hybrid", attr2=a2, lo2=l2, hi2=h2)
+    rp = oi.search(Q, lo, hi, w.k, ef=100, ef_post=n, strategy="post", attr2=a2, lo2=l2, hi2=h2)
+    rt = oi.route(lo, hi)
+    ep = ix["entry_global"]
+    bits = np.unpackbits(ix["gmask0"].view(np.uint8), axis=1, bitorder="little")[:, :S * M].astype(bool)
+    adj = ix["adj0"].reshape(n, S * M)
+    vv, pp = np.nonzero(bits & (adj >= 0))
+    reach_b = _closure(n, vv, adj[vv, pp], ep)
+    nonempty = 0
+    for i in range(len(sel)):
+        mask = int(rt["mask"][i])
+        segs = [j for j in range(S) if (mask >> j) & 1]
+        per = min(M, -(-m // len(segs)))
+        src, dst = [], []
+        for j in segs:
+            ch = ix["adj0"][:, j, :per]
+            v_, s_ = np.nonzero(ch >= 0)
+            src.append(v_)
+            dst.append(ch[v_, s_])
+        for reach, r in ((_closure(n, np.concatenate(src), np.concatenate(dst), ep), rh), (reach_b, rp)):
+            ok = (w.attrs[reach] >= lo[i]) & (w.attrs[reach] <= hi[i]) & (a2[reach] >= l2[i]) & (a2[reach] <= h2[i])
+            want = _topk_fp64(w.vectors, Q[i], reach[ok], w.k)
+            nonempty += len(want) > 0
+            assert int(r["count"][i]) == len(want), i
+            assert np.array_equal(r["ids"][i, :len(want)], want), i
+    assert nonempty >= 30
+
+
+def test_conjunctive_full_second_range_is_single_attribute(c1_index):
+    """A second range that holds every object leaves every strategy's result, and its
+    distance and expansion counts, as without the second attribute."""
+    w, path = c1_index
+    oi = oracle.OracleIndex(path)
+    a2, _, _ = _conj(w)
+    lo2 = np.full(len(w.lo), -1, np.int64)
+    hi2 = np.full(len(w.lo), 10**6, np.int64)
+    for st in ("pre", "hybrid", "post", "auto"):
+        a = oi.search(w.queries, w.lo, w.hi, w.k, ef=40, strategy=st, tau_a=100, tau_b=5000)
+        b = oi.search(w.queries, w.lo, w.hi, w.k, ef=40, strategy=st, tau_a=100, tau_b=5000,
+                      attr2=a2, lo2=lo2, hi2=hi2)
+        for key in ("ids", "dist", "count", "n_dist", "n_exp", "strategy"):
+            assert np.array_equal(a[key], b[key]), (st, key)

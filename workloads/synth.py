@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "Workload", "CONFIGS", "make_workload", "gaussian_iid", "int_mixture",
-    "unit_mixture", "nonneg_mixture", "make_ranges", "log_uniform_fractions",
+    "unit_mixture", "nonneg_mixture", "make_ranges", "log_uniform_fractions", "second_attribute",
 ]
 
 
@@ -131,6 +131,16 @@ CONFIGS = {
                attr="uniform", domain=1_000_000, S=8, M=16, efc=100, nq=5_000,
                frac=[0.005, 0.02, 0.10], k=10),
 }
+
+
+def second_attribute(n: int, fractions, seed: int, domain: int = 1000):
+    """A second integer attribute, uniform in [0, domain), and one range per query on
+    it (width max(1, round(f * domain)) for each fraction f, start uniform), for
+    conjunctive queries. Returns (attr2 int64 [n], lo2 int64 [nq], hi2 int64 [nq])."""
+    rng = np.random.default_rng([seed, 5])
+    attr2 = rng.integers(0, domain, size=n, dtype=np.int64)
+    lo2, hi2 = make_ranges(rng, np.asarray(fractions, dtype=np.float64), domain)
+    return attr2, lo2, hi2
 
 
 def make_workload(name: str, seed: int = 1234, **overrides) -> Workload:
