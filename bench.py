@@ -393,7 +393,7 @@ def main():
                 "algorithmic_bytes_per_launch": m32["alg"], "algorithmic_bytes_by_strategy": m32["parts"]}
 
     # hybrid selection S1 (the m neighbours nearest to the expanded object) with the
-    # same parameters, beside the tuned selection (the comparison of Section 5.7)
+    # same parameters, beside the tuned selection (the comparison of Section 5.6)
     other_sel = None
     if params.m <= 64:
         ps = U.Params.defaults(**{f: getattr(params, f) for f, _ in U.Params._fields_})

@@ -102,7 +102,7 @@ typedef struct {
                           queries, top rerank_mult * k by bf16 distance, FP32 re-rank) when
                           d is a multiple of 8, d <= 1024 and rerank_mult * k <= 64;
                           0 (default): warp scan */
-  int selection;       /* hybrid neighbour selection (Section 4.2; Section 5.7 compares the two):
+  int selection;       /* hybrid neighbour selection (Section 4.2; Section 5.6 compares the two):
                           2 (default) = S2, the first ceil(m / S') slots of every intersected
                           chunk; 1 = S1, the m neighbours nearest to the expanded object among
                           all slots of the intersected chunks (m <= 64) */

@@ -30,7 +30,7 @@
  *      If ann stays empty on a layer, the entry point is kept.
  *   R6 Selection S2 (default): the first ceil(m / S') slots of every intersected
  *      chunk, S' = number of intersected segments, chunks visited in ascending
- *      segment id. Selection S1 (Section 4.2, first strategy; Section 5.7): every
+ *      segment id. Selection S1 (Section 4.2, first strategy; Section 5.6): every
  *      neighbour in the intersected chunks, ordered by (distance to the expanded
  *      object, id) with distances in FP64, and the first m of them. Only distances
  *      to the query count as distance evaluations.
@@ -38,7 +38,7 @@
  *      k = ef_post on layer 0), then the range filter, then the first k.
  *   R8 A result holds min(k, found) entries sorted by (distance, id); the rest of
  *      the row is padded with id -1 and distance +inf.
- *   R9 Conjunctive predicate on a second attribute (Section 5.8, "multiple
+ *   R9 Conjunctive predicate on a second attribute (Section 5.9, "multiple
  *      single-attribute indexes"): the index is built on A1; a query adds
  *      lo2 <= A2 <= hi2. Algorithm 7's layer-0 ann test requires both ranges (the
  *      paper's change of its push-to-ann line); by the same reading Strategy A

@@ -150,7 +150,7 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
                   {"reg_budget": 64, "visited_cap": 512, "cand_cap": 256},
                   {"reg_budget": 64, "visited_cap": 1024, "cand_cap": 128}]
     if cur.m <= 64:
-        # hybrid selection S1 instead of S2 (Section 5.7 compares the two)
+        # hybrid selection S1 instead of S2 (Section 5.6 compares the two)
         shapes.append({"selection": 1})
     if cur.dtype == U.BF16:
         # pre-filter queries on the tensor cores instead of the warp scan
