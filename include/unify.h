@@ -157,6 +157,25 @@ UNIFY_API int unify_search(unify_index_t* idx, const float* q, const int64_t* lo
                  float* out_dist, int32_t* out_count, uint32_t* out_status, int32_t* out_counters,
                  void* stream);
 
+/* unify_search with a conjunctive predicate on a second attribute (Section 5.9,
+ * "multiple single-attribute indexes": the index is built on its own attribute A1,
+ * and Algorithm 7's push-to-ann test requires both ranges). Query i returns the
+ * nearest objects with lo[i] <= A1 <= hi[i] AND lo2[i] <= attr2[id] <= hi2[i]:
+ * Strategy A scans the A1 range and keeps the rows that pass A2; Strategy C's
+ * layer-0 ann test and entry point test both ranges; Strategy B's final filter tests
+ * both. Segments, masks and the router use A1 alone.
+ *   attr2      n int64, device: the second attribute of every object, by id; read
+ *              during the call (caller-owned, must stay valid until the stream reaches
+ *              the end of the search)
+ *   lo2, hi2   nq int64, device, inclusive ranges on attr2 (lo2 > hi2 selects nothing)
+ * Other arguments and results as unify_search. Returns UNIFY_E_ARG when attr2, lo2 or
+ * hi2 is NULL (nq > 0). The tensor-core scan (tc_scan) is not used by this call. */
+UNIFY_API int unify_search_conj(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,
+                                const int64_t* attr2, const int64_t* lo2, const int64_t* hi2, int64_t nq, int k,
+                                int ef, unify_strategy_t strategy, const unify_params_t* p, int64_t* out_ids,
+                                float* out_dist, int32_t* out_count, uint32_t* out_status, int32_t* out_counters,
+                                void* stream);
+
 /* unify_search with strategy UNIFY_AUTO (range-aware selection). */
 UNIFY_API int unify_search_auto(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,
                       int64_t nq, int k, int ef, const unify_params_t* p, int64_t* out_ids,

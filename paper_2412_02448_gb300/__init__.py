@@ -77,6 +77,9 @@ def lib():
             L.unify_search.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]
             L.unify_search.restype = ctypes.c_int
+            L.unify_search_conj.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]
+            L.unify_search_conj.restype = ctypes.c_int
             L.unify_search_auto.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                             _P, _P, _P, _P, _P, _P]
             L.unify_search_auto.restype = ctypes.c_int
@@ -158,10 +161,12 @@ class Index:
         return out
 
     def search(self, q, lo, hi, k: int, ef: int = 0, strategy="auto", params: Params | None = None,
-               out=None, counters: bool = False):
+               out=None, counters: bool = False, attr2=None, lo2=None, hi2=None):
         """Returns dict(ids int64 [nq,k], dist float32 [nq,k], count int32 [nq], status int32 [nq]
         [, counters int32 [nq,4]: distance evaluations, expansions, start and end in microseconds])
-        as device tensors. ``out`` may pass preallocated tensors."""
+        as device tensors. ``out`` may pass preallocated tensors. With ``attr2`` (one value per
+        object) and ``lo2``/``hi2`` (one range per query) the search is conjunctive
+        (unify_search_conj)."""
         torch = self._torch
         q = self._dev(q, torch.float32).reshape(-1, self.d)
         lo, hi = self._dev(lo, torch.int64), self._dev(hi, torch.int64)
@@ -177,6 +182,17 @@ class Index:
             if counters:
                 out["counters"] = torch.empty((nq, 4), dtype=torch.int32, device=self.device)
         p = ctypes.byref(params) if params is not None else None
+        if attr2 is not None:
+            a2 = self._dev(attr2, torch.int64)
+            l2, h2 = self._dev(lo2, torch.int64), self._dev(hi2, torch.int64)
+            if a2.numel() != self.n or l2.numel() != nq or h2.numel() != nq:
+                raise ValueError("attr2 needs one value per object, lo2 and hi2 one per query")
+            _check(lib().unify_search_conj(self._h, _ptr(q), _ptr(lo), _ptr(hi), _ptr(a2), _ptr(l2), _ptr(h2), nq,
+                                           k, ef, st, p, _ptr(out["ids"]), _ptr(out["dist"]), _ptr(out["count"]),
+                                           _ptr(out.get("status")), _ptr(out.get("counters")),
+                                           _stream_handle(torch, self.device)),
+                   "unify_search_conj")
+            return out
         _check(lib().unify_search(self._h, _ptr(q), _ptr(lo), _ptr(hi), nq, k, ef, st, p, _ptr(out["ids"]),
                                   _ptr(out["dist"]), _ptr(out["count"]), _ptr(out.get("status")),
                                   _ptr(out.get("counters")), _stream_handle(torch, self.device)),

@@ -215,7 +215,8 @@ struct PhaseTimer {
 
 int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi, int64_t nq, int k,
                int ef, int strategy, const unify_params_t* up, int64_t* out_ids, float* out_dist,
-               int32_t* out_count, uint32_t* out_status, int32_t* out_counters, cudaStream_t st) {
+               int32_t* out_count, uint32_t* out_status, int32_t* out_counters, cudaStream_t st,
+               const Conj* cj = nullptr) {
   if (!idx) return fail(UNIFY_E_ARG, "null index");
   if (nq < 0 || nq >= (1ll << 31) / kMaxScanBlocks) return fail(UNIFY_E_ARG, "nq out of range");
   if (strategy < -1 || strategy > 2) return fail(UNIFY_E_ARG, "bad strategy");
@@ -242,7 +243,8 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
                      sc.strat, &o, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "route kernel");
-  const bool tc = (strategy == UNIFY_PRE || strategy == UNIFY_AUTO) && tc_scan_available(idx->ix, p);
+  // the tensor-core scan has no second-attribute predicate: conjunctive queries use the warp scan
+  const bool tc = !cj && (strategy == UNIFY_PRE || strategy == UNIFY_AUTO) && tc_scan_available(idx->ix, p);
   if (tc) {
     PhaseTimer t(idx->tm, 2, st);
     e = launch_tcscan(idx->ix, sc, q, p, o, st);
@@ -250,7 +252,7 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
   }
   {
     PhaseTimer t(idx->tm, 1, st);
-    e = launch_batch(idx->ix, sc, q, p, o, st, tc);
+    e = launch_batch(idx->ix, sc, q, p, o, st, tc, cj);
   }
   if (e != cudaSuccess) return cuda_fail(e, "search kernel");
   return UNIFY_OK;
@@ -422,6 +424,21 @@ extern "C" int unify_search(unify_index_t* idx, const float* q, const int64_t* l
                             void* stream) {
   return run_search(idx, q, lo, hi, nq, k, ef, (int)strategy, p, out_ids, out_dist, out_count, out_status,
                     out_counters, (cudaStream_t)stream);
+}
+
+extern "C" int unify_search_conj(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,
+                                 const int64_t* attr2, const int64_t* lo2, const int64_t* hi2, int64_t nq, int k,
+                                 int ef, unify_strategy_t strategy, const unify_params_t* p, int64_t* out_ids,
+                                 float* out_dist, int32_t* out_count, uint32_t* out_status, int32_t* out_counters,
+                                 void* stream) {
+  if (nq > 0 && (!attr2 || !lo2 || !hi2))
+    return fail(UNIFY_E_ARG, "unify_search_conj: null second-attribute pointer");
+  Conj cj;
+  cj.attr2 = attr2;
+  cj.lo2 = lo2;
+  cj.hi2 = hi2;
+  return run_search(idx, q, lo, hi, nq, k, ef, (int)strategy, p, out_ids, out_dist, out_count, out_status,
+                    out_counters, (cudaStream_t)stream, &cj);
 }
 
 extern "C" int unify_search_auto(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi,

@@ -107,6 +107,15 @@ struct Params {
   unify_dtype_t dtype;
 };
 
+// Conjunctive predicate on a second attribute: attr2 holds one value per object
+// (by id); query i also requires lo2[i] <= attr2[id] <= hi2[i]. attr2 == nullptr:
+// no second attribute.
+struct Conj {
+  const int64_t* attr2 = nullptr;
+  const int64_t* lo2 = nullptr;
+  const int64_t* hi2 = nullptr;
+};
+
 struct Outputs {
   int64_t* ids;
   float* dist;
@@ -121,7 +130,7 @@ cudaError_t launch_route(const DeviceIndex& ix, const Scratch& sc, const int64_t
                          int build_queues, int32_t* out_pa, int32_t* out_pb, uint32_t* out_mask,
                          int32_t* out_strat, const Outputs* outs, cudaStream_t st);
 cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
-                         const Outputs& o, cudaStream_t st, bool skip_scan = false);
+                         const Outputs& o, cudaStream_t st, bool skip_scan = false, const Conj* cj = nullptr);
 bool tc_scan_available(const DeviceIndex& ix, const Params& p);
 cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
                           const Outputs& o, cudaStream_t st);

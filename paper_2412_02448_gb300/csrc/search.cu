@@ -78,6 +78,7 @@ struct BatchArgs {
   uint64_t* part;
   int32_t* counters;
   int k, ef_h, ef_p, m, cand_cap, ann_cap, vis_log2, max_exp;
+  Conj cj;  // second-attribute predicate (attr2 == nullptr: none)
   int s1;  // hybrid selection S1 (the m neighbours nearest to the expanded object) instead of S2
   int warp_bytes;
   int skip_scan;  // the pre-filter queries were searched by the tensor-core scan
@@ -140,6 +141,13 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// The second-attribute predicate for object id (true without a second attribute).
+__device__ __forceinline__ bool conj_ok(const BatchArgs& a, int id, int64_t l2, int64_t h2) {
+  if (!a.cj.attr2) return true;
+  const int64_t v = __ldg(a.cj.attr2 + id);
+  return v >= l2 && v <= h2;
+}
+
 // Slot (segment * M + s) of the ci-th selected neighbour (hybrid, S2 selection).
 __device__ __forceinline__ int hybrid_slot(int ci, int per, uint32_t mask, int M, int* seg) {
   const int kseg = ci / per;
@@ -155,7 +163,7 @@ __device__ __forceinline__ int hybrid_slot(int ci, int per, uint32_t mask, int M
 template <class T, int CH, int G>
 __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (&q)[CH], bool hybrid, int l,
                             int efl, uint64_t ep_key, bool ep_in, uint32_t mask, uint32_t full_mask, int per,
-                            int pa, int pb, int& n_dist, int& n_exp, uint32_t& status) {
+                            int pa, int pb, int64_t l2, int64_t h2, int& n_dist, int& n_exp, uint32_t& status) {
   const int lane = lane_id();
   const int H = 1 << a.vis_log2;
   uint64_t* E = hybrid ? w.E : w.ann;  // candidate buffer
@@ -303,7 +311,10 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
         pv = __ldg(a.pos + cid);
       }
       const float dist = batch_dist<T, CH, G>(q, cid, a.vt, a.row_bytes, a.scale, a.dp4, w.clist);
-      const bool inr = need ? (pv >= pa && pv < pb) : true;
+      // layer 0 of a hybrid query: the range (by position where the segment is only
+      // partly inside) and the second-attribute predicate
+      const bool inr = (need ? (pv >= pa && pv < pb) : true) &&
+                       (!(hybrid && l == 0 && cid >= 0) || conj_ok(a, cid, l2, h2));
       n_dist += __popc(__ballot_sync(kFull, cid >= 0));
       const uint64_t key = cid >= 0 ? make_key(dist, cid) : kKeyMax;
       const uint64_t thr = nA >= efl ? (hybrid ? w.ann[efl - 1] : E[efl - 1]) : kKeyMax;
@@ -375,6 +386,7 @@ __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool h
   if (a.o.counters && lane == 0) t_start = us_since_start(a.counters);
   const uint32_t mask = a.mask[qi];
   const int pa = a.pa[qi], pb = a.pb[qi];
+  const int64_t l2 = a.cj.attr2 ? a.cj.lo2[qi] : 0, h2 = a.cj.attr2 ? a.cj.hi2[qi] : 0;
   uint32_t status = 0;
   int n_dist = 0, n_exp = 0, cnt = 0;
   if (hybrid ? mask != 0 : pb > pa) {  // nothing can be in range otherwise
@@ -400,7 +412,7 @@ __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool h
       if (hybrid) {
         const int p = __ldg(a.pos + ep);
         if (l == 0) {
-          ep_in = p >= pa && p < pb;
+          ep_in = p >= pa && p < pb && conj_ok(a, ep, l2, h2);
         } else {
           int seg = 0;
           for (int j = 1; j < a.S; ++j)
@@ -409,7 +421,7 @@ __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool h
         }
       }
       nA = search_layer<T, CH, G>(a, w, q, hybrid, l, l > 0 ? 1 : efl0, ep_key, ep_in, mask, full_mask, per, pa, pb,
-                               n_dist, n_exp, status);
+                               l2, h2, n_dist, n_exp, status);
       if (l > 0 && nA > 0) ep_key = w.ann[0];
     }
     if (a.rerank > 0) {
@@ -426,7 +438,7 @@ __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool h
           if (t < nA) {
             key = w.ann[t];
             const int p = __ldg(a.pos + key_id(key));
-            inr = p >= pa && p < pb;
+            inr = p >= pa && p < pb && conj_ok(a, key_id(key), l2, h2);
           }
           const unsigned bal = __ballot_sync(kFull, inr);
           const int dst = nc + __popc(bal & lanemask_lt());
@@ -450,7 +462,7 @@ __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool h
         if (t < nA) {
           key = w.ann[t];
           const int p = __ldg(a.pos + key_id(key));
-          inr = p >= pa && p < pb;
+          inr = p >= pa && p < pb && conj_ok(a, key_id(key), l2, h2);
         }
         const unsigned bal = __ballot_sync(kFull, inr);
         const int dst = cnt + __popc(bal & lanemask_lt());
@@ -495,6 +507,7 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
   const int rpb = (Y + nb - 1) / (nb > 0 ? nb : 1);
   const int r0 = pa + b * rpb;
   const int r1 = min(pb, r0 + rpb);
+  const int64_t l2 = a.cj.attr2 ? a.cj.lo2[qi] : 0, h2 = a.cj.attr2 ? a.cj.hi2[qi] : 0;
   float4 q[CH];
   load_query<CH>(q, a.q + (int64_t)qi * a.d, a.d);
   constexpr int RB = (16 / CH) > 2 ? (16 / CH) : 2;  // rows per load batch
@@ -533,7 +546,10 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
     const float dist = warp_transpose_reduce<32>(part);
     const int row = base + lane;
     uint64_t key = kKeyMax;
-    if (row < r1) key = make_key(dist, __ldg(a.sorted_ids + row));
+    if (row < r1) {
+      const int32_t id = __ldg(a.sorted_ids + row);
+      if (conj_ok(a, id, l2, h2)) key = make_key(dist, id);
+    }
     nt = topk_offer(topk, nt, kk, key, w.R);
   }
   if (nb > 1) {
@@ -642,8 +658,9 @@ int batch_ann_cap(const Params& p) {
 int batch_smem_per_warp(const Params& p) { return batch_warp_bytes(p.cand_cap, batch_ann_cap(p), p.vis_log2); }
 
 cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
-                         const Outputs& o, cudaStream_t st, bool skip_scan) {
+                         const Outputs& o, cudaStream_t st, bool skip_scan, const Conj* cj) {
   BatchArgs a;
+  a.cj = cj ? *cj : Conj{};
   a.skip_scan = skip_scan ? 1 : 0;
   a.vec = ix.vec;
   a.dp4 = ix.dp / 4;

@@ -445,3 +445,48 @@ def test_hybrid_s1_matches_oracle(U, c2_small_index, m):
     with pytest.raises(U.UnifyError):
         ix.search(w.queries, w.lo, w.hi, w.k, ef=50, strategy="hybrid",
                   params=U.Params.defaults(m=65, selection=1))
+
+
+def test_conjunctive_second_attribute_matches_oracle(U, c2_small_index):
+    """Conjunctive queries (a second attribute, Section 5.9): the pre-filter equals the
+    exact conjunctive answer; hybrid and post-filter follow the oracle's traversal
+    (ids, distances, counts and expansion counts on unflagged rows); auto routing
+    agrees; a second range that holds every object gives the plain search's rows."""
+    from workloads import second_attribute
+    w, path = c2_small_index
+    ix = U.Index(path)
+    oi = oracle.OracleIndex(path)
+    fr = np.array([0.2, 0.5, 1.0])[np.arange(len(w.lo)) % 3]
+    a2, lo2, hi2 = second_attribute(w.n, fr, 11)
+    ex = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, w.k, attr2=a2, lo2=lo2, hi2=hi2)
+    r = _np(ix.search(w.queries, w.lo, w.hi, w.k, strategy="pre", attr2=a2, lo2=lo2, hi2=hi2))
+    assert np.array_equal(r["ids"], ex[0]) and np.array_equal(r["count"], ex[2])
+    assert np.array_equal(r["dist"].astype(np.float64)[np.isfinite(ex[1])], ex[1][np.isfinite(ex[1])])
+    ta, tb = w.n // 100, w.n // 2
+    for strategy in ("hybrid", "post", "auto"):
+        p = U.Params.defaults(cand_cap=CAND, tau_a=ta, tau_b=tb)
+        r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy=strategy, params=p, counters=True,
+                          attr2=a2, lo2=lo2, hi2=hi2))
+        o = oi.search(w.queries, w.lo, w.hi, w.k, ef=64, m=16, strategy=strategy, tau_a=ta, tau_b=tb,
+                      attr2=a2, lo2=lo2, hi2=hi2)
+        ok = (r["status"] & EXACT_BITS) == 0
+        assert ok.mean() > 0.8, strategy
+        for i in np.flatnonzero(ok)[:50]:
+            c = int(r["count"][i])
+            ids = r["ids"][i, :c]
+            assert np.all((w.attrs[ids] >= w.lo[i]) & (w.attrs[ids] <= w.hi[i]))
+            assert np.all((a2[ids] >= lo2[i]) & (a2[ids] <= hi2[i]))
+        assert np.array_equal(r["ids"][ok], o["ids"][ok]), strategy
+        assert np.array_equal(r["count"][ok], o["count"][ok]), strategy
+        graph = ok & (o["strategy"] != 0)
+        assert np.array_equal(r["counters"][graph, 1], o["n_exp"][graph]), strategy
+        fin = np.isfinite(o["dist"][ok])
+        assert np.array_equal(r["dist"][ok][fin].astype(np.float64), o["dist"][ok][fin]), strategy
+    full_lo = np.full(len(w.lo), -1, np.int64)
+    full_hi = np.full(len(w.lo), 10**6, np.int64)
+    p = U.Params.defaults(cand_cap=CAND, tau_a=ta, tau_b=tb)
+    plain = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy="auto", params=p))
+    conj = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy="auto", params=p, attr2=a2, lo2=full_lo,
+                         hi2=full_hi))
+    for key in ("ids", "dist", "count", "status"):
+        assert np.array_equal(plain[key], conj[key]), key
