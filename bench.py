@@ -198,6 +198,77 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def scan_compare(args):
+    """Pre-filter scans compared on the c5 shape (d = 960, ranges 0.5/2/10 %, every query
+    forced to Strategy A): FP32 warp scan, BF16 warp scan and BF16 tensor-core scan (both
+    BF16 paths re-rank 4k candidates in FP32). Prints its own JSON line; not part of the
+    default run."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import hsig_build
+    import paper_2412_02448_gb300 as U
+    from paper_2412_02448_gb300 import autotune
+    from workloads import make_workload
+    n = args.n or 200_000
+    w = make_workload("c5", seed=args.seed, n=n, nq=args.nq or 5000, efc=16)
+    # the graph is not used by forced pre-filtering: a light build (efCons 16)
+    path = hsig_build.cached_index_path(cache_dir(), "c5scan", w.n, w.seed)
+    if not os.path.exists(path):
+        t = time.time()
+        hsig_build.build_index(w.vectors, w.attrs, path, w.S, w.M, w.efc, seed=w.seed)
+        log(f"built index {path} in {time.time() - t:.1f} s")
+    ix = U.Index(path)
+    dev = torch.device("cuda", 0)
+    q = torch.from_numpy(w.queries).to(dev)
+    lo = torch.from_numpy(w.lo).to(dev)
+    hi = torch.from_numpy(w.hi).to(dev)
+    k, nq = w.k, len(w.lo)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    variants = {"fp32_warp": U.Params.defaults(),
+                "bf16_warp": U.Params.defaults(dtype=U.BF16, rerank_mult=4),
+                "bf16_tensor_core": U.Params.defaults(dtype=U.BF16, rerank_mult=4, tc_scan=1)}
+    steps = max(3, min(args.steps, 20))
+    res, rows = {}, {}
+    for name, p in variants.items():
+        out = ix.search(q, lo, hi, k, strategy="pre", params=p)
+        for _ in range(max(3, args.warmup)):
+            flush.fill_(1)
+            out = ix.search(q, lo, hi, k, strategy="pre", params=p, out=out)
+        ix.collect_timing()
+        ix.timing(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for s_ in range(steps):
+            flush.fill_(s_ & 0xFF)
+            evs[s_][0].record(stream)
+            out = ix.search(q, lo, hi, k, strategy="pre", params=p, out=out)
+            evs[s_][1].record(stream)
+        torch.cuda.synchronize()
+        ix.timing(False)
+        ph = ix.collect_timing()
+        ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in evs]))
+        rows[name] = {kk: v.cpu().numpy() for kk, v in out.items()}
+        res[name] = {"ms_per_step": ms, "value": nq / (ms / 1000.0),
+                     "phase_ms_per_step": {kk: round(v[0] / max(1, v[1]), 4) for kk, v in ph.items()
+                                           if not kk.startswith("unused")}}
+    ref = rows["fp32_warp"]
+    for name in ("bf16_warp", "bf16_tensor_core"):
+        rec = autotune.recall_rows(rows[name]["ids"], ref["ids"], ref["count"], k)
+        res[name]["recall_vs_fp32_scan"] = autotune.group_recall(rec, w.fractions)
+        res[name]["recall_vs_fp32_scan"] = {f"{100 * f_:g}%": round(v_, 4) for f_, v_ in
+                                            res[name]["recall_vs_fp32_scan"].items()}
+    same = np.all(rows["bf16_warp"]["ids"] == rows["bf16_tensor_core"]["ids"], axis=1)
+    Y = np.searchsorted(np.sort(w.attrs), w.hi, side="right") - np.searchsorted(np.sort(w.attrs), w.lo)
+    print(json.dumps({"mode": "scan_compare", "unit": "queries/s",
+                      "workload": f"c5 shape: n={w.n} d={w.d} nonneg mixture, {nq} queries, ranges "
+                                  "0.5/2/10%, k=10, every query Strategy A",
+                      "mean_rows_per_query": float(Y.mean()), "steps": steps,
+                      "l2": "flushed between steps (256 MiB write)",
+                      "rows_equal_bf16_warp_vs_tensor_core": float(same.mean()), **res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -223,7 +294,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--n", type=int, default=0, help="smaller base set (profiling captures only)")
     ap.add_argument("--nq", type=int, default=0, help="smaller batch (profiling captures only)")
+    ap.add_argument("--scan-compare", action="store_true",
+                    help="only compare the pre-filter scans on the c5 shape (its own JSON line)")
     args = ap.parse_args()
+    if args.scan_compare:
+        scan_compare(args)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
