@@ -33,7 +33,10 @@
 //
 // Roles in a CTA of 6 warps: warps 0-3 epilogue (warp w reads tensor-memory
 // lanes 32w..32w+31), warp 4 lane 0 issues TMA loads, warp 5 lane 0 issues the
-// MMAs and owns the tensor-memory allocation. Stages of shared memory (query
+// MMAs and owns the tensor-memory allocation. Work units are claimed dynamically:
+// the producer takes the next unit from a global counter and hands its index to the
+// MMA issuer and the epilogue through a small ring in shared memory (index -1 ends
+// the kernel), so CTAs that drew cheap units take more of them. Stages of shared memory (query
 // slice 16 KB + row slice 32 KB per 64 columns of K) are handed over with
 // mbarriers. Every wait is bounded (a number of polls and an elapsed time); a
 // timeout sets an error flag instead of hanging, the waiting warp stops, and the
@@ -62,6 +65,7 @@ constexpr int kTcRows = 256;        // rows per block (MMA N = tensor-memory col
 constexpr int kTcKc = 64;           // K elements per stage (one 128-byte swizzle row)
 constexpr int kTcStages = 2;
 constexpr int kTcQueue = 32;        // keys queued per query before they replace the heap top
+constexpr int kUnitRing = 4;        // claimed work units handed from the producer to the other roles
 constexpr int kTcRMax = 64;         // candidates kept per query for the re-rank
 constexpr int kBuckets = 1024;
 constexpr int kStageA = kTcQ * kTcKc * 2;     // 16 KB of queries
@@ -76,6 +80,8 @@ struct TcSmem {
   uint64_t heap[kTcRMax][kTcQ];  // column q: the max-heap of query q
   uint64_t qk[kTcQueue][kTcQ];   // column q: keys waiting for the heap of query q
   uint64_t full[kTcStages], empty[kTcStages], accf[2], acce[2], drain;
+  uint64_t ufull[kUnitRing], uempty[kUnitRing];
+  int uring[kUnitRing];  // claimed unit (-1: no more units)
   uint32_t tmem;
 };
 
@@ -304,6 +310,10 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       mbar_init(&s.acce[i], 4 * 32);
     }
     mbar_init(&s.drain, 1);
+    for (int i = 0; i < kUnitRing; ++i) {
+      mbar_init(&s.ufull[i], 1);
+      mbar_init(&s.uempty[i], 1 + 4 * 32);  // the MMA issuer and the 128 epilogue threads
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 5) {
@@ -322,7 +332,19 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
     if (lane == 0) {
       bool ok = true;
       long long it = 0;
-      for (int x = blockIdx.x; x < nunits && ok; x += gridDim.x) {
+      for (long long useq = 0; ok; ++useq) {
+        // claim the next unit and hand it to the other roles
+        const int us = (int)(useq % kUnitRing);
+        const long long uu = useq / kUnitRing;
+        if (uu > 0 && !mbar_wait(&s.uempty[us], (uint32_t)((uu - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        int x = atomicAdd(a.counters + CNT_TC_TAKE, 1);
+        if (x >= nunits) x = -1;
+        s.uring[us] = x;
+        mbar_arrive(&s.ufull[us]);
+        if (x < 0) break;
         const int t = unit_tile(a, ntiles, x);
         int r0, r1;
         tile_unit_rows(a, t, x - a.unit_off[t], &r0, &r1);
@@ -355,7 +377,15 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       bool ok = true;
       const uint32_t idesc = idesc_bf16();
       long long it = 0, g = 0;
-      for (int x = blockIdx.x; x < nunits && ok; x += gridDim.x) {
+      for (long long useq = 0; ok; ++useq) {
+        const int us = (int)(useq % kUnitRing);
+        if (!mbar_wait(&s.ufull[us], (uint32_t)((useq / kUnitRing) & 1))) {
+          ok = false;
+          break;
+        }
+        const int x = *reinterpret_cast<volatile int*>(&s.uring[us]);
+        mbar_arrive(&s.uempty[us]);
+        if (x < 0) break;
         const int t = unit_tile(a, ntiles, x);
         int r0, r1;
         tile_unit_rows(a, t, x - a.unit_off[t], &r0, &r1);
@@ -399,7 +429,15 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
     const int tq = threadIdx.x;
     bool failed = false;
     long long g = 0;
-    for (int x = blockIdx.x; x < nunits && !failed; x += gridDim.x) {
+    for (long long useq = 0; !failed; ++useq) {
+      const int us = (int)(useq % kUnitRing);
+      if (!__all_sync(kFull, mbar_wait(&s.ufull[us], (uint32_t)((useq / kUnitRing) & 1)))) {
+        failed = true;
+        break;
+      }
+      const int x = *reinterpret_cast<volatile int*>(&s.uring[us]);
+      mbar_arrive(&s.uempty[us]);
+      if (x < 0) break;
       const int t = unit_tile(a, ntiles, x);
       int r0, r1;
       tile_unit_rows(a, t, x - a.unit_off[t], &r0, &r1);
@@ -539,7 +577,7 @@ __global__ void tc_tile_prep(TcArgs a) {
 }
 
 // One CTA of 1024 threads: splits every tile into work units of about equal
-// length, about two units per SM over the whole batch (at least one per tile
+// length, about four units per SM over the whole batch (at least one per tile
 // with rows, at most kTcUnitsPerTile and at most one per block), and writes the
 // exclusive prefix of the units per tile; the total goes to the counters.
 __global__ void tc_unit_plan(TcArgs a) {
@@ -559,7 +597,7 @@ __global__ void tc_unit_plan(TcArgs a) {
   if ((threadIdx.x & 31) == 0) atomicAdd(&tot, mine);
   __syncthreads();
   const long long total = tot > 0 ? (long long)tot : 1;
-  const long long target = 2ll * a.num_sms;
+  const long long target = 4ll * a.num_sms;
   for (int base = 0; base < ntiles; base += 1024) {
     const int t = base + threadIdx.x;
     int v = 0;
