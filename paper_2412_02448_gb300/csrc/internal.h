@@ -98,7 +98,8 @@ enum {
   CNT_T0 = 8,                          // counters[8..9]: 64-bit global-timer origin of the search kernel
   CNT_TC_ERR = 10,                     // the tensor-core scan timed out on a wait
   CNT_TC_UNITS = 11,                   // work units of the tensor-core scan
-  CNT_TC_TAKE = 12,                    // next work unit to claim (tensor-core scan)
+  CNT_TC_TAKE = 12,                    // next work unit to claim (tensor-core scan pass)
+  CNT_TC_TAKE_B = 13,                  // next work unit to claim (tensor-core bounding pass)
   kNumCounters = 16
 };
 

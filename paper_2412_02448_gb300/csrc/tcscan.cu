@@ -290,6 +290,13 @@ __device__ __forceinline__ void tile_unit_rows(const TcArgs& a, int t, int u, in
   *r1 = a.tile_lo[t] + b1 * kTcRows;
 }
 
+// kBound = true: the bounding pass. Its epilogue keeps, per query, the minimum
+// distance of 64 disjoint groups of the query's rows in the unit (group = chunk
+// parity x column within the chunk, registers with static indices). The largest of
+// those 64 minima is at least the query's 64th-smallest distance in the unit, so
+// key(T, INT_MAX) is above every key of the query's top R (R <= 64): it is published
+// into the shared threshold with atomicMin before the scan pass starts.
+template <bool kBound>
 __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__ CUtensorMap tmX,
                                                           const __grid_constant__ CUtensorMap tmQ, TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -340,7 +347,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
           ok = false;
           break;
         }
-        int x = atomicAdd(a.counters + CNT_TC_TAKE, 1);
+        int x = atomicAdd(a.counters + (kBound ? CNT_TC_TAKE_B : CNT_TC_TAKE), 1);
         if (x >= nunits) x = -1;
         s.uring[us] = x;
         mbar_arrive(&s.ufull[us]);
@@ -422,6 +429,78 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       if (!ok) atomicExch(err, 1);
     }
     __syncwarp();
+  } else if (kBound) {
+    // ---- bounding epilogue (warps 0-3): group minima per query
+    const int tq = threadIdx.x;
+    bool failed = false;
+    long long g = 0;
+    for (long long useq = 0; !failed; ++useq) {
+      const int us = (int)(useq % kUnitRing);
+      if (!__all_sync(kFull, mbar_wait(&s.ufull[us], (uint32_t)((useq / kUnitRing) & 1)))) {
+        failed = true;
+        break;
+      }
+      const int x = *reinterpret_cast<volatile int*>(&s.uring[us]);
+      mbar_arrive(&s.uempty[us]);
+      if (x < 0) break;
+      const int t = unit_tile(a, ntiles, x);
+      int r0, r1;
+      tile_unit_rows(a, t, x - a.unit_off[t], &r0, &r1);
+      const int qpos = t * kTcQ + tq;
+      const bool qv = qpos < nA;
+      int pa = 0, pb = 0;
+      float qn = 0.f;
+      if (qv) {
+        const int qi = a.aq[qpos];
+        pa = a.pa[qi];
+        pb = a.pb[qi];
+        qn = a.aqn[qpos];
+      }
+      float gm0[32], gm1[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) gm0[j] = gm1[j] = __int_as_float(0x7f800000);
+      for (int row0 = r0; row0 < r1; row0 += kTcRows, ++g) {
+        const int ab = (int)(g & 1);
+        float xr[kTcRows / 32];
+#pragma unroll
+        for (int c = 0; c < kTcRows / 32; ++c) {
+          const int64_t row = (int64_t)row0 + c * 32 + lane;
+          xr[c] = row < a.n ? __ldg(a.xn + row) : 0.f;
+        }
+        const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);
+        if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1)))) {
+          failed = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * kTcRows);
+#pragma unroll
+        for (int c = 0; c < kTcRows / 32; ++c) {
+          const bool need = c1 > c * 32 && c0 < c * 32 + 32;
+          if (!__any_sync(kFull, need)) continue;
+          float v[32];
+          tmem_ld32(taddr + (uint32_t)(c * 32), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = c * 32 + j;
+            const float xv = __shfl_sync(kFull, xr[c], j);
+            const float dist = fmaxf(xv + qn - 2.f * v[j], 0.f);
+            const bool in = col >= c0 && col < c1;
+            if (c & 1) gm1[j] = in ? fminf(gm1[j], dist) : gm1[j];
+            else gm0[j] = in ? fminf(gm0[j], dist) : gm0[j];
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&s.acce[ab]);
+      }
+      if (failed) break;
+      float T = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) T = fmaxf(T, fmaxf(gm0[j], gm1[j]));
+      if (qv && T < __int_as_float(0x7f800000))
+        atomicMin(a.qthr + qpos, (unsigned long long)make_key(T, 0x7fffffff));
+    }
+    if (failed) atomicExch(err, 1);
   } else {
     // ---- epilogue warps 0-3: thread q = query q of the tile = tensor-memory lane q.
     // The warps run independently (no block-wide barrier); a timed-out wait ends
@@ -821,9 +900,17 @@ cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float*
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = tc_smem_bytes();
-  e = cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(tc_scan_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_scan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  tc_scan_kernel<<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
+  // bounding pass (shared thresholds), then the scan pass
+  if (p.rerank_mult * p.k <= 64) {
+    tc_scan_kernel<true><<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  tc_scan_kernel<false><<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // FP32 re-rank with the row-width variants of the search kernel
