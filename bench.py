@@ -148,10 +148,18 @@ def cpu_baseline(path, w, params, k, budget_s, per_fraction):
         if time.perf_counter() - t >= budget_s * 0.5:
             break
     dt = time.perf_counter() - t
+    # the same search on one core, on a smaller stratified sample (about 2 s)
+    per1 = max(2, min(per, int(2.0 * (done / dt) / cores / len(fr))))
+    idx1 = np.concatenate([np.flatnonzero(w.fractions == f)[:per1] for f in fr])
+    t1 = time.perf_counter()
+    oi.search(w.queries[idx1], w.lo[idx1], w.hi[idx1], k, **dict(kw, threads=1))
+    dt1 = time.perf_counter() - t1
     oi.close()
     return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{len(idx)} queries stratified over the range fractions of the batch, {passes} pass(es), "
-                      f"{dt:.1f} s (literal HSIG search, FP64, same ef/m/tau)"}
+                      f"{dt:.1f} s (literal HSIG search, FP64, same ef/m/tau)",
+            "one_core": {"value": len(idx1) / dt1, "unit": UNIT, "cores": 1,
+                         "sample": f"{len(idx1)} queries, same strata, {dt1:.1f} s"}}
 
 
 def reference_arm(args, rank, world):
@@ -261,10 +269,30 @@ def scan_compare(args):
                                             res[name]["recall_vs_fp32_scan"].items()}
     same = np.all(rows["bf16_warp"]["ids"] == rows["bf16_tensor_core"]["ids"], axis=1)
     Y = np.searchsorted(np.sort(w.attrs), w.hi, side="right") - np.searchsorted(np.sort(w.attrs), w.lo)
+    # useful work of the scan: 2 d flops per (query, in-range row); the tensor-core
+    # phase against the measured bf16 peak, the warp scans against HBM as bytes per row
+    flops = float(2.0 * w.d * Y.sum())
+    pk = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+    except OSError:
+        pass
+    tc_ms = res["bf16_tensor_core"]["phase_ms_per_step"].get("tcscan", 0.0)
+    if tc_ms > 0:
+        tf = flops / (tc_ms / 1000.0) / 1e12
+        res["bf16_tensor_core"]["useful_tflops"] = tf
+        if pk.get("bf16_tflops"):
+            res["bf16_tensor_core"]["tensor_frac_of_measured_bf16"] = tf / pk["bf16_tflops"]
+    for name, row_bytes in (("fp32_warp", 4 * w.d + 4), ("bf16_warp", 2 * w.d + 4)):
+        gbs = float(row_bytes * Y.sum()) / (res[name]["ms_per_step"] / 1000.0) / 1e9
+        res[name]["row_bytes_gbs"] = gbs
+        if pk.get("hbm_gbs"):
+            res[name]["hbm_frac_of_measured"] = gbs / pk["hbm_gbs"]
     print(json.dumps({"mode": "scan_compare", "unit": "queries/s",
                       "workload": f"c5 shape: n={w.n} d={w.d} nonneg mixture, {nq} queries, ranges "
                                   "0.5/2/10%, k=10, every query Strategy A",
-                      "mean_rows_per_query": float(Y.mean()), "steps": steps,
+                      "mean_rows_per_query": float(Y.mean()), "useful_flops_per_step": flops, "steps": steps,
                       "l2": "flushed between steps (256 MiB write)",
                       "rows_equal_bf16_warp_vs_tensor_core": float(same.mean()), **res}), flush=True)
 
