@@ -490,3 +490,36 @@ def test_conjunctive_second_attribute_matches_oracle(U, c2_small_index):
                          hi2=full_hi))
     for key in ("ids", "dist", "count", "status"):
         assert np.array_equal(plain[key], conj[key]), key
+
+
+def test_tensor_core_scan_partial_slices_and_empty_ranges(U, c3_small_index, c2_small_index):
+    """d = 96 (the second 64-column slice is half outside the rows; TMA fills it with
+    zeros): every returned distance is the float32 distance of its id, counts are
+    exact and recall is near 1. Tiles that mix empty, reversed and one-row ranges with
+    ordinary ones give the warp scan's rows on integer data."""
+    w, path = c3_small_index
+    ix = U.Index(path)
+    X = w.vectors.astype(np.float64)
+    ex = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, w.k)
+    r = _np(ix.search(w.queries, w.lo, w.hi, w.k, strategy="pre",
+                      params=U.Params.defaults(dtype=U.BF16, rerank_mult=4, tc_scan=1)))
+    _valid(w, r, w.lo, w.hi)
+    assert np.array_equal(r["count"], np.minimum(ex[2], w.k)) and np.all(r["status"] == 0)
+    for i in range(len(w.lo)):
+        c = r["count"][i]
+        ids = r["ids"][i, :c]
+        d64 = ((X[ids] - w.queries[i].astype(np.float64)) ** 2).sum(1)
+        assert np.all(np.abs(r["dist"][i, :c] - d64) <= 1e-5 * np.maximum(d64, 1e-30))
+    assert oracle.recall(r["ids"], ex[0], ex[2], w.k).mean() >= 0.99
+    w, path = c2_small_index
+    ix = U.Index(path)
+    lo, hi = w.lo.copy(), w.hi.copy()
+    lo[::7], hi[::7] = hi[::7] + 1, hi[::7]   # reversed: empty
+    lo[3::11] = hi[3::11]                      # a single value
+    lo[5::13], hi[5::13] = -10, -1             # below every attribute
+    ref = _np(ix.search(w.queries, lo, hi, w.k, strategy="pre"))
+    tc = _np(ix.search(w.queries, lo, hi, w.k, strategy="pre",
+                       params=U.Params.defaults(dtype=U.BF16, rerank_mult=4, tc_scan=1)))
+    for key in ("ids", "dist", "count", "status"):
+        assert np.array_equal(tc[key], ref[key]), key
+    assert (ref["count"] == 0).sum() >= len(lo) // 7
