@@ -48,6 +48,7 @@ void free_core(Scratch& sc) {
   release(sc.tc_tile);
   release(sc.tc_part);
   release(sc.tc_thr);
+  release(sc.tc_pcnt);
   sc.tc_rows = 0;
   sc.tc_dpq = 0;
   sc.cap_nq = 0;
@@ -98,8 +99,9 @@ cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k, int d) {
   if (e == cudaSuccess) e = alloc(sc.tc_aqn, rows);
   if (e == cudaSuccess) e = cudaMalloc(&sc.tc_qb, (size_t)rows * dpq * 2);
   if (e == cudaSuccess) e = alloc(sc.tc_tile, 4 * (rows / kTcQueryTile) + 1);
-  // at most kTcUnitsPerTile units per tile, one list of at most 64 keys per query and unit
-  if (e == cudaSuccess) e = alloc(sc.tc_part, (size_t)rows * kTcUnitsPerTile * 64);
+  // at most kTcUnitsPerTile units per tile, one list of kTcCandCap keys per query and unit
+  if (e == cudaSuccess) e = alloc(sc.tc_part, (size_t)rows * kTcUnitsPerTile * kTcCandCap);
+  if (e == cudaSuccess) e = alloc(sc.tc_pcnt, (size_t)rows * kTcUnitsPerTile);
   if (e == cudaSuccess) e = alloc(sc.tc_thr, rows);
   if (e != cudaSuccess) {
     free_core(sc);

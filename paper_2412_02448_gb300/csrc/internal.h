@@ -71,7 +71,8 @@ struct Scratch {
   float* tc_aqn = nullptr;       // squared norms of their bfloat16 vectors
   void* tc_qb = nullptr;         // their bfloat16 vectors, tc_rows x tc_dpq
   int32_t* tc_tile = nullptr;    // per tile: first row, row blocks, units, unit offsets (4 x tiles + 1)
-  uint64_t* tc_part = nullptr;   // per work unit: kTcQueryTile lists of up to 64 candidate keys
+  uint64_t* tc_part = nullptr;   // per work unit: kTcQueryTile lists of up to kTcCandCap candidate keys
+  int32_t* tc_pcnt = nullptr;    // per work unit and query: candidates found
   unsigned long long* tc_thr = nullptr;  // per pre-filter query: threshold key shared by its units
   int64_t tc_rows = 0;
   int tc_dpq = 0;
@@ -89,6 +90,7 @@ struct Scratch {
 
 constexpr int kTcQueryTile = 128;   // pre-filter queries per tensor-core tile
 constexpr int kTcUnitsPerTile = 16;  // at most this many work units per tile
+constexpr int kTcCandCap = 128;      // candidate slots per query and work unit
 
 // counters[] layout
 enum {

@@ -4,30 +4,31 @@
 // The pre-filter queries of a batch are bucketed by the first position pa of
 // their range in the attribute order and converted to bfloat16, so that 128
 // consecutive queries (a tile) cover neighbouring rows. The rows of the union of
-// a tile's ranges are split into work units of whole 256-row blocks, spread over
-// all SMs. For a block, TMA stages 64-column slices of the tile's queries and of
-// the block's attribute-ordered bfloat16 rows (128-byte swizzled) and tcgen05.mma
-// forms D = Q X^T (M = 128 queries, N = 256 rows, K = 16 per instruction, float32
+// a tile's ranges are split into work units of whole 256-row blocks. For a block,
+// TMA stages 64-column slices of the tile's queries and of the block's
+// attribute-ordered bfloat16 rows (128-byte swizzled), and tcgen05.mma forms
+// D = Q X^T (M = 128 queries, N = 256 rows, K = 16 per instruction, float32
 // accumulation in tensor memory, two accumulators so that the epilogue of one
-// block overlaps the products of the next).
+// block overlaps the products of the next). Tensor-memory lane q is query q of
+// the tile: thread q turns its query's dot products into squared distances
+// ||x||^2 + ||q||^2 - 2 x.q (norms of the bfloat16 values) and keeps the rows of
+// its range [pa, pb).
 //
-// Epilogue: tensor-memory lane q is query q of the tile, so thread q reads its
-// own query's 256 dot products, turns each into the squared distance
-// ||x||^2 + ||q||^2 - 2 x.q (norms of the bfloat16 values) and keeps, among the
-// rows inside its range [pa, pb), the rerank_mult * k = R smallest keys
-// (distance, id) of the unit in a private max-heap in shared memory. The first R
-// keys fill the heap unordered (a predicated store per column); the warp then
-// sorts that heap into descending order (a max-heap) in one cooperative pass;
-// later keys that beat the heap's top wait in a short queue and replace the top,
-// one per lane per round. Every query also has a threshold shared by all units
-// of its tile in global memory (the smallest heap top published so far): a unit
-// holding R keys at or below it rules out every larger key everywhere, so each
-// unit filters with the smaller of its own top and the shared one.
-//
-// A unit's lists go to global memory; a last kernel merges the lists of every
-// query's units, re-ranks the candidates with exact float32 direct-difference
-// distances against the float32 vectors, as the other reduced-precision paths
-// do, and writes the result row. On integer-valued vectors of at most 8 bits and
+// Two passes over the same tiles select, for every query, the R = rerank_mult * k
+// smallest keys (distance, id) without any per-query heap:
+//   1. bounding pass: per query and unit, the minimum distance of each of 64
+//      disjoint row groups (group = chunk parity x column, in registers); the R-th
+//      smallest of those 64 minima has R distinct rows at or below it, so it bounds
+//      the query's R-th smallest key (R <= 64). The smallest bound over the units
+//      is published with atomicMin as the query's threshold;
+//   2. collecting pass: every in-range row whose key is below the threshold is
+//      appended to the (unit, query) list in global memory (a predicated store,
+//      thread-private count). Typically only about R rows per query qualify.
+// A finishing kernel merges each query's lists into the R smallest keys and
+// re-ranks them with exact float32 direct-difference distances against the
+// float32 vectors, as the other reduced-precision paths do. A list that overflowed
+// (more than kTcCap rows below the bound) sends that query through an exact warp
+// scan of its range instead. On integer-valued vectors of at most 8 bits and
 // d <= 128 every term is an exact integer below 2^24, so the result equals the
 // exact float32 scan.
 //
@@ -36,9 +37,9 @@
 // MMAs and owns the tensor-memory allocation. Work units are claimed dynamically:
 // the producer takes the next unit from a global counter and hands its index to the
 // MMA issuer and the epilogue through a small ring in shared memory (index -1 ends
-// the kernel), so CTAs that drew cheap units take more of them. Stages of shared memory (query
-// slice 16 KB + row slice 32 KB per 64 columns of K) are handed over with
-// mbarriers. Every wait is bounded (a number of polls and an elapsed time); a
+// the kernel), so CTAs that drew cheap units take more of them. Stages of shared
+// memory (query slice 16 KB + row slice 32 KB per 64 columns of K) are handed over
+// with mbarriers. Every wait is bounded (a number of polls and an elapsed time); a
 // timeout sets an error flag instead of hanging, the waiting warp stops, and the
 // copies and products in flight are drained before the CTA releases its tensor
 // memory and exits.
@@ -46,9 +47,8 @@
 // Bounds (checked against the buffers each launch receives): a unit's rows lie
 // in [tile_lo, tile_lo + 256 nb) and loads past n are zero-filled by TMA (rows)
 // or guarded (norms, ids); the query tile's TMA rows end at tc_rows (a multiple
-// of 128); part holds at most kTcUnitsPerTile units per tile; heap and queue
-// columns are indexed by the thread's own query (< 128) and slot (< R <= 64,
-// < kTcQueue).
+// of 128); part holds at most kTcUnitsPerTile units per tile and kTcCap keys per
+// (unit, query) list, and stores stop at kTcCap while the count goes on.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -63,8 +63,8 @@ namespace {
 constexpr int kTcQ = kTcQueryTile;  // queries per tile (MMA M = tensor-memory lanes)
 constexpr int kTcRows = 256;        // rows per block (MMA N = tensor-memory columns per accumulator)
 constexpr int kTcKc = 64;           // K elements per stage (one 128-byte swizzle row)
-constexpr int kTcStages = 2;
-constexpr int kTcQueue = 32;        // keys queued per query before they replace the heap top
+constexpr int kTcStages = 4;
+constexpr int kTcCap = kTcCandCap;  // candidate slots per query and work unit
 constexpr int kUnitRing = 4;        // claimed work units handed from the producer to the other roles
 constexpr int kTcRMax = 64;         // candidates kept per query for the re-rank
 constexpr int kBuckets = 1024;
@@ -77,8 +77,6 @@ struct TcSmem {
   // 1024-byte aligned stages first
   uint8_t a[kTcStages][kStageA];
   uint8_t b[kTcStages][kStageB];
-  uint64_t heap[kTcRMax][kTcQ];  // column q: the max-heap of query q
-  uint64_t qk[kTcQueue][kTcQ];   // column q: keys waiting for the heap of query q
   uint64_t full[kTcStages], empty[kTcStages], accf[2], acce[2], drain;
   uint64_t ufull[kUnitRing], uempty[kUnitRing];
   int uring[kUnitRing];  // claimed unit (-1: no more units)
@@ -193,66 +191,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Replaces the largest key of the full max-heap in column c of h (R keys) by
-// key and restores the heap order.
-__device__ __forceinline__ void heap_replace_top(uint64_t (*h)[kTcQ], int c, int R, uint64_t key) {
-  int i = 0;
-  for (;;) {
-    int ch = 2 * i + 1;
-    if (ch >= R) break;
-    uint64_t ck = h[ch][c];
-    if (ch + 1 < R) {
-      const uint64_t c2 = h[ch + 1][c];
-      if (c2 > ck) {
-        ck = c2;
-        ++ch;
-      }
-    }
-    if (ck <= key) break;
-    h[i][c] = ck;
-    i = ch;
-  }
-  h[i][c] = key;
-}
-
-// The whole warp sorts the R <= 64 keys of column c of h into descending order,
-// which is a max-heap (bitonic network over 64 positions, lane l holding
-// positions l and l + 32; the missing positions are filled with 0, the smallest
-// key, and sort to the end).
-__device__ __forceinline__ void warp_heapify_col(uint64_t (*h)[kTcQ], int c, int R) {
-  const int lane = lane_id();
-  uint64_t e0 = lane < R ? h[lane][c] : 0ull;
-  uint64_t e1 = lane + 32 < R ? h[lane + 32][c] : 0ull;
+// Ascending bitonic sort of 64 values held in registers (static indices only).
+__device__ __forceinline__ void sort64(float (&v)[64]) {
 #pragma unroll
   for (int k = 2; k <= 64; k <<= 1) {
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j == 32) {
-        // positions l and l + 32, one direction for the whole sequence
-        const uint64_t mx = e0 > e1 ? e0 : e1, mn = e0 > e1 ? e1 : e0;
-        e0 = mx;
-        e1 = mn;
-      } else {
-        const uint64_t y0 = __shfl_xor_sync(kFull, e0, j);
-        const uint64_t y1 = __shfl_xor_sync(kFull, e1, j);
-        const bool lower = (lane & j) == 0;
-        // descending blocks where (position & k) == 0, ascending elsewhere
-        const bool d0 = (lane & k) == 0, d1 = ((lane + 32) & k) == 0;
-        const bool big0 = lower == d0, big1 = lower == d1;
-        e0 = big0 ? (e0 > y0 ? e0 : y0) : (e0 < y0 ? e0 : y0);
-        e1 = big1 ? (e1 > y1 ? e1 : y1) : (e1 < y1 ? e1 : y1);
+#pragma unroll
+      for (int i = 0; i < 64; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const float x = v[i], y = v[l];
+          const bool sw = up ? (x > y) : (x < y);
+          v[i] = sw ? y : x;
+          v[l] = sw ? x : y;
+        }
       }
     }
   }
-  if (lane < R) h[lane][c] = e0;
-  if (lane + 32 < R) h[lane + 32][c] = e1;
-  __syncwarp();
 }
 
 struct TcArgs {
   const int32_t* sorted_ids;
   const float* xn;     // ||bf16(x)||^2 in attribute order
   const float* vec;    // float32 rows by id (re-rank)
+  const unsigned char* vt_bf16;  // bfloat16 rows by id (scan of an overflowed query)
   const float* q;      // float32 queries (re-rank)
   int dp4, d, KC, num_sms;
   int64_t n;
@@ -264,7 +228,8 @@ struct TcArgs {
   int32_t* tile_nb;     // 256-row blocks of the union range
   int32_t* tile_units;  // work units the range is split into
   int32_t* unit_off;    // exclusive prefix of tile_units (ntiles + 1)
-  uint64_t* part;       // per unit and query of its tile: R candidate keys
+  uint64_t* part;       // per unit and query of its tile: kTcCap candidate slots
+  int32_t* pcnt;        // per unit and query: candidates found (above kTcCap: overflow)
   unsigned long long* qthr;  // per query (bucketed order): smallest key known to have R keys at or below it
   int32_t* counters;
   int k, R;
@@ -494,17 +459,28 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         mbar_arrive(&s.acce[ab]);
       }
       if (failed) break;
-      float T = 0.f;
+      // the R-th smallest of the 64 group minima: R distinct rows lie at or below it
+      float v64[64];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) T = fmaxf(T, fmaxf(gm0[j], gm1[j]));
+      for (int j = 0; j < 32; ++j) {
+        v64[j] = gm0[j];
+        v64[32 + j] = gm1[j];
+      }
+      sort64(v64);
+      float T = __int_as_float(0x7f800000);
+#pragma unroll
+      for (int i = 0; i < 64; ++i)
+        if (i == a.R - 1) T = v64[i];
       if (qv && T < __int_as_float(0x7f800000))
         atomicMin(a.qthr + qpos, (unsigned long long)make_key(T, 0x7fffffff));
     }
     if (failed) atomicExch(err, 1);
   } else {
-    // ---- epilogue warps 0-3: thread q = query q of the tile = tensor-memory lane q.
-    // The warps run independently (no block-wide barrier); a timed-out wait ends
-    // the warp's loop (decided warp-wide) and the issuers time out in turn.
+    // ---- collecting epilogue (warps 0-3): thread q = query q of the tile =
+    // tensor-memory lane q. Every in-range row whose key is below the query's bound
+    // is appended to the (unit, query) list in global memory; the count goes on past
+    // kTcCap so that the finishing kernel can see an overflow. The warps run
+    // independently; a timed-out wait ends the warp's loop (decided warp-wide).
     const int tq = threadIdx.x;
     bool failed = false;
     long long g = 0;
@@ -524,15 +500,16 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       const bool qv = qpos < nA;
       int pa = 0, pb = 0;
       float qn = 0.f;
+      uint64_t thr = kKeyMax;
       if (qv) {
         const int qi = a.aq[qpos];
         pa = a.pa[qi];
         pb = a.pb[qi];
         qn = a.aqn[qpos];
+        thr = *reinterpret_cast<volatile unsigned long long*>(a.qthr + qpos);
       }
-      int cnt = 0;                 // keys in the heap column of this query
-      bool heaped = false;         // the column holds R keys in heap order
-      uint64_t thr_own = kKeyMax;  // largest key of the full heap of this unit
+      uint64_t* list = a.part + ((int64_t)x * kTcQ + tq) * kTcCap;
+      int cnt = 0;
       for (int row0 = r0; row0 < r1; row0 += kTcRows, ++g) {
         const int ab = (int)(g & 1);
         // squared norms and ids of the block's rows: lane j holds row row0 + 32c + j
@@ -545,17 +522,12 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
           xr[c] = row < a.n ? __ldg(a.xn + row) : 0.f;
           ir[c] = row < a.n ? __ldg(a.sorted_ids + row) : 0;
         }
-        // the query's threshold so far over every unit of its tile; it only
-        // decreases, so a stale value is still valid
-        const uint64_t tg = qv ? *reinterpret_cast<volatile unsigned long long*>(a.qthr + qpos) : kKeyMax;
         const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);  // this query's columns
-        const bool ok = __all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1)));
-        if (!ok) {
+        if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1)))) {
           failed = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        uint64_t thr = thr_own < tg ? thr_own : tg;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * kTcRows);
 #pragma unroll
         for (int c = 0; c < kTcRows / 32; ++c) {
@@ -563,9 +535,6 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
           if (!__any_sync(kFull, need)) continue;
           float v[32];
           tmem_ld32(taddr + (uint32_t)(c * 32), v);
-          // keys below the threshold: the first R fill the column unordered, later
-          // ones wait in the queue
-          int nq = 0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = c * 32 + j;
@@ -573,48 +542,16 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
             const int32_t idj = __shfl_sync(kFull, ir[c], j);
             const uint64_t key = make_key(fmaxf(xv + qn - 2.f * v[j], 0.f), idj);
             if (col >= c0 && col < c1 && key < thr) {
-              if (cnt < a.R) {
-                s.heap[cnt][tq] = key;
-                ++cnt;
-              } else {
-                s.qk[nq][tq] = key;
-                ++nq;
-              }
-            }
-          }
-          // columns that just reached R keys become heaps (one warp-wide sort each)
-          const bool fresh = cnt == a.R && !heaped;
-          unsigned fill = __ballot_sync(kFull, fresh);
-          while (fill) {
-            const int l = __ffs(fill) - 1;
-            fill &= fill - 1;
-            warp_heapify_col(s.heap, warp * 32 + l, a.R);
-          }
-          if (fresh) {
-            heaped = true;
-            thr_own = s.heap[0][tq];
-            thr = thr_own < tg ? thr_own : tg;
-          }
-          // queued keys replace the heap top, one per lane per round
-          while (__any_sync(kFull, nq > 0)) {
-            if (nq > 0) {
-              const uint64_t key = s.qk[--nq][tq];
-              if (key < thr) {
-                heap_replace_top(s.heap, tq, a.R, key);
-                thr_own = s.heap[0][tq];
-                thr = thr_own < tg ? thr_own : tg;
-              }
+              if (cnt < kTcCap) list[cnt] = key;
+              ++cnt;
             }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(&s.acce[ab]);
-        if (qv && thr_own < tg) atomicMin(a.qthr + qpos, (unsigned long long)thr_own);
       }
       if (failed) break;
-      // this unit's list for the query (unsorted, padded with the largest key)
-      uint64_t* dst = a.part + ((int64_t)x * kTcQ + tq) * a.R;
-      for (int r = 0; r < a.R; ++r) dst[r] = r < cnt ? s.heap[r][tq] : kKeyMax;
+      a.pcnt[(int64_t)x * kTcQ + tq] = cnt;
     }
     if (failed) atomicExch(err, 1);
   }
@@ -706,9 +643,13 @@ __global__ void tc_unit_plan(TcArgs a) {
   }
 }
 
-// One warp per pre-filter query: merges the lists of the units of its tile that
-// overlap its range, re-ranks the candidates with exact float32 distances and
-// writes the result row. After a timed-out wait the rows are empty and flagged.
+// One warp per pre-filter query: merges the candidate lists of the units of its
+// tile that overlap its range into the R smallest keys, re-ranks them with exact
+// float32 distances and writes the result row. A list that overflowed (more than
+// kTcCap candidates below the bound) sends the query through an exact warp scan of
+// its range instead: bfloat16 rows against the float32 query, direct differences,
+// the same selection as the warp scan of the search kernel. After a timed-out wait
+// the rows are empty and flagged.
 template <int CH, int G>
 __global__ void __launch_bounds__(128) tc_finish(TcArgs a) {
   __shared__ uint64_t top[4][kTcRMax];
@@ -724,19 +665,38 @@ __global__ void __launch_bounds__(128) tc_finish(TcArgs a) {
     const int qi = a.aq[pos];
     const int pa = a.pa[qi], pb = a.pb[qi];
     const int u0 = a.unit_off[t], U = a.tile_units[t];
-    int nt = 0;
+    float4 qv[CH];
+    load_query<CH>(qv, a.q + (int64_t)qi * a.d, a.d);
+    bool overflow = false;
     for (int u = 0; u < U && pb > pa && !failed; ++u) {
       int r0, r1;
       tile_unit_rows(a, t, u, &r0, &r1);
       if (r1 <= pa || r0 >= pb) continue;
-      const uint64_t* src = a.part + ((int64_t)(u0 + u) * kTcQ + j) * a.R;
-      for (int off = 0; off < a.R; off += 32) {
-        const uint64_t key = off + lane < a.R ? src[off + lane] : kKeyMax;
-        nt = topk_offer(top[warp], nt, a.R, key, R[warp]);
+      overflow = overflow || a.pcnt[(int64_t)(u0 + u) * kTcQ + j] > kTcCap;
+    }
+    int nt = 0;
+    if (failed || pb <= pa) {
+      nt = 0;
+    } else if (!overflow) {
+      for (int u = 0; u < U; ++u) {
+        int r0, r1;
+        tile_unit_rows(a, t, u, &r0, &r1);
+        if (r1 <= pa || r0 >= pb) continue;
+        const int64_t li = (int64_t)(u0 + u) * kTcQ + j;
+        const int c = a.pcnt[li];
+        const uint64_t* src = a.part + li * kTcCap;
+        for (int off = 0; off < c; off += 32) {
+          const uint64_t key = off + lane < c ? src[off + lane] : kKeyMax;
+          nt = topk_offer(top[warp], nt, a.R, key, R[warp]);
+        }
+      }
+    } else {
+      for (int base = pa; base < pb; base += 32) {
+        int cid = base + lane < pb ? __ldg(a.sorted_ids + base + lane) : -1;
+        const float dist = batch_dist<StoreBF16, CH, G>(qv, cid, a.vt_bf16, a.dp4 * 8, nullptr, a.dp4, clist[warp]);
+        nt = topk_offer(top[warp], nt, a.R, cid >= 0 ? make_key(dist, cid) : kKeyMax, R[warp]);
       }
     }
-    float4 qv[CH];
-    load_query<CH>(qv, a.q + (int64_t)qi * a.d, a.d);
     int no = 0;
     for (int off = 0; off < nt; off += 32) {
       int cid = off + lane < nt ? key_id(top[warp][off + lane]) : -1;
@@ -875,6 +835,7 @@ cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float*
   a.sorted_ids = ix.sorted_ids;
   a.xn = ix.xn_bf16_sorted;
   a.vec = ix.vec;
+  a.vt_bf16 = ix.vt_bf16;
   a.q = q;
   a.dp4 = ix.dp / 4;
   a.d = ix.d;
@@ -891,6 +852,7 @@ cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float*
   a.unit_off = sc.tc_tile + 3 * tiles;
   a.part = sc.tc_part;
   a.qthr = sc.tc_thr;
+  a.pcnt = sc.tc_pcnt;
   a.counters = sc.counters;
   a.k = p.k;
   a.R = rerank_count(p);
@@ -904,14 +866,10 @@ cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float*
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(tc_scan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // bounding pass (shared thresholds), then the scan pass. The bound pays for its
-  // second sweep of the row tiles only for short rows: measured on GB300, it cut the
-  // scan of 4,000 queries at d = 128 by 10 % and slowed d = 960 by 13 %.
-  if (a.KC <= 2) {
-    tc_scan_kernel<true><<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  // bounding pass (each query's bound), then the collecting pass
+  tc_scan_kernel<true><<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   tc_scan_kernel<false><<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
