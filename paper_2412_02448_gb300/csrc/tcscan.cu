@@ -512,25 +512,32 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       int cnt = 0;
       for (int row0 = r0; row0 < r1; row0 += kTcRows, ++g) {
         const int ab = (int)(g & 1);
-        // squared norms and ids of the block's rows: lane j holds row row0 + 32c + j
-        // of chunk c (loads in flight while the accumulator is awaited)
-        float xr[kTcRows / 32];
-        int32_t ir[kTcRows / 32];
-#pragma unroll
-        for (int c = 0; c < kTcRows / 32; ++c) {
-          const int64_t row = (int64_t)row0 + c * 32 + lane;
-          xr[c] = row < a.n ? __ldg(a.xn + row) : 0.f;
-          ir[c] = row < a.n ? __ldg(a.sorted_ids + row) : 0;
-        }
+        // squared norms and ids of the block's rows, one 32-row chunk at a time: lane j
+        // holds row row0 + 32c + j of chunk c; the next chunk's loads are issued before
+        // the current chunk is processed (the chunk loop stays rolled: a compact body)
         const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);  // this query's columns
+        float xnext;
+        int32_t inext;
+        {
+          const int64_t row = (int64_t)row0 + lane;
+          xnext = row < a.n ? __ldg(a.xn + row) : 0.f;
+          inext = row < a.n ? __ldg(a.sorted_ids + row) : 0;
+        }
         if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1)))) {
           failed = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * kTcRows);
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < kTcRows / 32; ++c) {
+          const float xc = xnext;
+          const int32_t ic = inext;
+          if (c + 1 < kTcRows / 32) {
+            const int64_t row = (int64_t)row0 + (c + 1) * 32 + lane;
+            xnext = row < a.n ? __ldg(a.xn + row) : 0.f;
+            inext = row < a.n ? __ldg(a.sorted_ids + row) : 0;
+          }
           const bool need = c1 > c * 32 && c0 < c * 32 + 32;
           if (!__any_sync(kFull, need)) continue;
           float v[32];
@@ -538,8 +545,8 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = c * 32 + j;
-            const float xv = __shfl_sync(kFull, xr[c], j);
-            const int32_t idj = __shfl_sync(kFull, ir[c], j);
+            const float xv = __shfl_sync(kFull, xc, j);
+            const int32_t idj = __shfl_sync(kFull, ic, j);
             const uint64_t key = make_key(fmaxf(xv + qn - 2.f * v[j], 0.f), idj);
             if (col >= c0 && col < c1 && key < thr) {
               if (cnt < kTcCap) list[cnt] = key;
