@@ -477,14 +477,14 @@ def main():
                     phases={ph: (v[0] / v[1] if v[1] else 0.0) for ph, v in phases.items()},
                     achieved=achieved, alg=alg, parts=parts)
 
-    def tuned(extra):
+    def tuned(extra, **kw):
         b = U.Params.defaults(**{f: getattr(base, f) for f, _ in U.Params._fields_})
         for kk, v in extra.items():
             setattr(b, kk, v)
         if args.no_tune:
             return b, {}
         return autotune.tune(ix, q, lo, hi, k, t_ids, t_cnt, w.fractions, target=args.target, base=b,
-                             log=log if rank == 0 else None)
+                             log=log if rank == 0 else None, **kw)
 
     # FP32 storage: the headline
     clocks = Clocks(local)
@@ -514,7 +514,14 @@ def main():
     precision = {}
     if not args.no_precision:
         for name, dt in (("bf16", U.BF16), ("fp8e4m3", U.FP8E4M3)):
-            p_, _ = tuned({"dtype": dt, "rerank_mult": 4})
+            p_, rep_ = tuned({"dtype": dt, "rerank_mult": 4})
+            if dt == U.BF16 and not args.no_tune:
+                # tuned again with the tensor-core pre-filter scan from the start (its cheap
+                # scans move the best tau_A up); the faster tuned configuration is reported
+                p_tc, rep_tc = tuned({"dtype": dt, "rerank_mult": 4, "tc_scan": 1},
+                                     tau_a_fracs=(0.01, 0.02, 0.05, 0.08, 0.12, 0.2))
+                if rep_tc.get("ms", 1e9) < rep_.get("ms", 1e9):
+                    p_ = p_tc
             r_ = measure(p_, max(3, args.steps // 2), args.warmup)
             precision[name] = {
                 "value": r_["value"], "ms_per_step": r_["ms"],
