@@ -426,33 +426,46 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       for (int j = 0; j < 32; ++j) gm0[j] = gm1[j] = __int_as_float(0x7f800000);
       for (int row0 = r0; row0 < r1; row0 += kTcRows, ++g) {
         const int ab = (int)(g & 1);
-        float xr[kTcRows / 32];
-#pragma unroll
-        for (int c = 0; c < kTcRows / 32; ++c) {
-          const int64_t row = (int64_t)row0 + c * 32 + lane;
-          xr[c] = row < a.n ? __ldg(a.xn + row) : 0.f;
-        }
+        // norms of the block's rows, two 32-row chunks at a time (lane j holds row
+        // row0 + 32c + j of chunk c); the chunk-pair loop stays rolled, the two chunks
+        // of a pair feed the two halves of the group minima
         const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);
+        float x0n, x1n;
+        {
+          const int64_t row = (int64_t)row0 + lane;
+          x0n = row < a.n ? __ldg(a.xn + row) : 0.f;
+          x1n = row + 32 < a.n ? __ldg(a.xn + row + 32) : 0.f;
+        }
         if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1)))) {
           failed = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * kTcRows);
+#pragma unroll 1
+        for (int cp = 0; cp < kTcRows / 64; ++cp) {
+          const float x0 = x0n, x1 = x1n;
+          if (cp + 1 < kTcRows / 64) {
+            const int64_t row = (int64_t)row0 + (cp + 1) * 64 + lane;
+            x0n = row < a.n ? __ldg(a.xn + row) : 0.f;
+            x1n = row + 32 < a.n ? __ldg(a.xn + row + 32) : 0.f;
+          }
 #pragma unroll
-        for (int c = 0; c < kTcRows / 32; ++c) {
-          const bool need = c1 > c * 32 && c0 < c * 32 + 32;
-          if (!__any_sync(kFull, need)) continue;
-          float v[32];
-          tmem_ld32(taddr + (uint32_t)(c * 32), v);
+          for (int h = 0; h < 2; ++h) {
+            const int c = 2 * cp + h;
+            const bool need = c1 > c * 32 && c0 < c * 32 + 32;
+            if (!__any_sync(kFull, need)) continue;
+            float v[32];
+            tmem_ld32(taddr + (uint32_t)(c * 32), v);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = c * 32 + j;
-            const float xv = __shfl_sync(kFull, xr[c], j);
-            const float dist = fmaxf(xv + qn - 2.f * v[j], 0.f);
-            const bool in = col >= c0 && col < c1;
-            if (c & 1) gm1[j] = in ? fminf(gm1[j], dist) : gm1[j];
-            else gm0[j] = in ? fminf(gm0[j], dist) : gm0[j];
+            for (int j = 0; j < 32; ++j) {
+              const int col = c * 32 + j;
+              const float xv = __shfl_sync(kFull, h ? x1 : x0, j);
+              const float dist = fmaxf(xv + qn - 2.f * v[j], 0.f);
+              const bool in = col >= c0 && col < c1;
+              if (h) gm1[j] = in ? fminf(gm1[j], dist) : gm1[j];
+              else gm0[j] = in ? fminf(gm0[j], dist) : gm0[j];
+            }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
