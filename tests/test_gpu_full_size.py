@@ -65,3 +65,29 @@ def test_full_size_sampled_parity(full):
         assert np.all((A[ids] >= w.lo[i]) & (A[ids] <= w.hi[i])) and len(set(ids.tolist())) == c
     rec = oracle.recall(r["ids"][sample], ex[0], ex[2], w.k)
     assert rec.mean() >= 0.95
+
+
+def test_full_size_tensor_core_scan(full):
+    """BF16 storage with the tensor-core pre-filter scan on the whole 1M-row batch
+    (auto-routed, the bench's BF16 comparison): the pre-filter rows of a stratified
+    sample equal the exact answer (bfloat16 holds the 8-bit integers exactly), the
+    whole batch equals the warp-scan batch, and no row is flagged."""
+    U, w, path = full
+    ix = U.Index(path)
+    base = dict(PARAMS, dtype=U.BF16, rerank_mult=4)
+    tc = ix.search(w.queries, w.lo, w.hi, w.k, strategy="auto", params=U.Params.defaults(tc_scan=1, **base))
+    ws = ix.search(w.queries, w.lo, w.hi, w.k, strategy="auto", params=U.Params.defaults(tc_scan=0, **base))
+    torch.cuda.synchronize()
+    tc = {k: v.cpu().numpy() for k, v in tc.items()}
+    ws = {k: v.cpu().numpy() for k, v in ws.items()}
+    for key in ("ids", "dist", "count", "status"):
+        assert np.array_equal(tc[key], ws[key]), key
+    oi = oracle.OracleIndex(path)
+    rt = oi.route(w.lo, w.hi, PARAMS["tau_a"], PARAMS["tau_b"])
+    pre = np.flatnonzero(rt["strategy"] == 0)
+    rng = np.random.default_rng(1)
+    sample = rng.choice(pre, min(60, len(pre)), replace=False)
+    ex = oracle.exact_knn(w.vectors, w.attrs, w.queries[sample], w.lo[sample], w.hi[sample], w.k)
+    assert np.array_equal(tc["ids"][sample], ex[0]) and np.array_equal(tc["count"][sample], ex[2])
+    fin = np.isfinite(ex[1])
+    assert np.array_equal(tc["dist"][sample].astype(np.float64)[fin], ex[1][fin])
