@@ -70,8 +70,8 @@ def test_full_size_sampled_parity(full):
 def test_full_size_tensor_core_scan(full):
     """BF16 storage with the tensor-core pre-filter scan on the whole 1M-row batch
     (auto-routed, the bench's BF16 comparison): the pre-filter rows of a stratified
-    sample equal the exact answer (bfloat16 holds the 8-bit integers exactly), the
-    whole batch equals the warp-scan batch, and no row is flagged."""
+    sample equal the exact answer (bfloat16 holds the 8-bit integers exactly), and the
+    whole batch (ids, distances, counts, status flags) equals the warp-scan batch."""
     U, w, path = full
     ix = U.Index(path)
     base = dict(PARAMS, dtype=U.BF16, rerank_mult=4)
