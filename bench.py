@@ -171,7 +171,7 @@ def reference_arm(args, rank, world):
     import oracle
     if rank != 0:
         return
-    w = make_workload("c2", seed=args.seed)
+    w = make_workload("c2", seed=args.seed, **({"n": args.n} if args.n else {}))
     path = get_index(w, 0, 1, lambda: None)
     import paper_2412_02448_gb300 as U  # parameters only; no GPU work on this arm
     params = U.Params.defaults(ef=args.ef, ef_post=args.ef_post or args.ef, tau_a=w.n // 100, tau_b=w.n // 2)
@@ -202,7 +202,7 @@ def reference_arm(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1000 * tot / len(steps_t), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "queries_per_step": per_f * len(fr)},
+            "config": {"workload": WORKLOAD, "n": w.n, "queries_per_step": per_f * len(fr)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_f * len(fr)} queries per step, stratified over the fractions"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
