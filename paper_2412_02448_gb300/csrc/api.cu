@@ -1,5 +1,7 @@
 // C ABI entry points: argument checks, parameters, scratch, and the launch
 // sequence route -> pre-filter scan (+ merge) -> hybrid search -> post search.
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstring>
 #include <new>
 #include <string>
@@ -11,6 +13,13 @@ namespace unify {
 
 namespace {
 thread_local std::string g_last_error;
+
+// NVTX range for one phase of a search (visible in a profiler's timeline; the
+// calls do nothing when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 int fail(int code, const std::string& msg) {
   set_error(msg);
@@ -239,7 +248,9 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
   e = cudaMemsetAsync(sc.counters, 0, kNumCounters * sizeof(int32_t), st);
   if (e != cudaSuccess) return cuda_fail(e, "counter reset");
   Outputs o{out_ids, out_dist, out_count, out_status, out_counters};
+  NvtxRange whole("unify:search");
   {
+    NvtxRange r("unify:route");
     PhaseTimer t(idx->tm, 0, st);
     e = launch_route(idx->ix, sc, lo, hi, nq, p.tau_a, p.tau_b, strategy, p.scan_rows, 1, sc.pa, sc.pb, sc.mask,
                      sc.strat, &o, st);
@@ -248,11 +259,13 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
   // the tensor-core scan has no second-attribute predicate: conjunctive queries use the warp scan
   const bool tc = !cj && (strategy == UNIFY_PRE || strategy == UNIFY_AUTO) && tc_scan_available(idx->ix, p);
   if (tc) {
+    NvtxRange r("unify:tensor-core scan");
     PhaseTimer t(idx->tm, 2, st);
     e = launch_tcscan(idx->ix, sc, q, p, o, st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core pre-filter scan");
   }
   {
+    NvtxRange r("unify:search kernel");
     PhaseTimer t(idx->tm, 1, st);
     e = launch_batch(idx->ix, sc, q, p, o, st, tc, cj);
   }

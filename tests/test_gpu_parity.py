@@ -242,6 +242,17 @@ def test_bad_index_files_rejected(U, tmp_path):
         U.Index(bad)
     with pytest.raises(U.UnifyError):
         U.Index(str(tmp_path / "missing.idx"))
+    # wrong magic, unsupported version, truncated file
+    write_index(bad, sec)
+    raw = bytearray(open(bad, "rb").read())
+    for name, data in (("magic", bytes([raw[0] ^ 0xFF]) + bytes(raw[1:])),
+                       ("version", bytes(raw[:8]) + (2).to_bytes(4, "little") + bytes(raw[12:])),
+                       ("truncated", bytes(raw[: len(raw) // 2]))):
+        path = str(tmp_path / f"{name}.idx")
+        with open(path, "wb") as f:
+            f.write(data)
+        with pytest.raises(U.UnifyError):
+            U.Index(path)
 
 
 def test_cuda_graph_plan_replays_search(U, c2_small_index):
