@@ -82,7 +82,8 @@ typedef enum {
 /* Search parameters. unify_default_params() fills the defaults shown. */
 typedef struct {
   int ef;              /* Algorithm 7 layer-0 beam (ann capacity), default 100 */
-  int m;               /* neighbours visited per expanded object (S2), default 16 */
+  int m;               /* hybrid neighbours visited per expanded object, default 16 (S2:
+                          ceil(m / S') per intersected chunk; S1: the m nearest) */
   int ef_post;         /* Algorithm 1 layer-0 beam of Strategy B; <= 0 means ef */
   int rerank_mult;     /* BF16/FP8: re-rank rerank_mult * k candidates in FP32, default 4 */
   unify_dtype_t dtype; /* storage read by traversal and scan, default UNIFY_FP32 */
