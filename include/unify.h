@@ -152,7 +152,9 @@ UNIFY_API int unify_route(unify_index_t* idx, const int64_t* lo, const int64_t* 
  *              for Strategy A), expansions, and the start and end of the query's work
  *              in microseconds since the search kernel's first work unit started
  * The first call with a larger nq grows the index's scratch buffers (a device
- * allocation); make that call before capturing the stream into a CUDA graph. */
+ * allocation), and so does the first call that takes the tensor-core scan (its
+ * buffers, about 16 KB per query of capacity, exist only once a search uses it);
+ * make those calls before capturing the stream into a CUDA graph. */
 UNIFY_API int unify_search(unify_index_t* idx, const float* q, const int64_t* lo, const int64_t* hi, int64_t nq,
                  int k, int ef, unify_strategy_t strategy, const unify_params_t* p, int64_t* out_ids,
                  float* out_dist, int32_t* out_count, uint32_t* out_status, int32_t* out_counters,

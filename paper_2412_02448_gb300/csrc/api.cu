@@ -49,6 +49,11 @@ void free_core(Scratch& sc) {
   release(sc.items);
   release(sc.part);
   release(sc.counters);
+  sc.cap_nq = 0;
+  sc.cap_k = 0;
+}
+
+void free_tc(Scratch& sc) {
   release(sc.tc_bucket);
   release(sc.tc_aq);
   release(sc.tc_aqn);
@@ -60,8 +65,6 @@ void free_core(Scratch& sc) {
   release(sc.tc_pcnt);
   sc.tc_rows = 0;
   sc.tc_dpq = 0;
-  sc.cap_nq = 0;
-  sc.cap_k = 0;
 }
 
 void free_stage(Scratch& sc) {
@@ -83,9 +86,8 @@ cudaError_t alloc(T*& p, size_t elems) {
 }
 
 // Grows the scratch to hold nq queries with k results (device allocation).
-cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k, int d) {
-  const int dpq = ((d + 63) / 64) * 64;  // bfloat16 query rows of the tensor-core scan
-  if (sc.counters && nq <= sc.cap_nq && k <= sc.cap_k && dpq <= sc.tc_dpq) return cudaSuccess;
+cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k) {
+  if (sc.counters && nq <= sc.cap_nq && k <= sc.cap_k) return cudaSuccess;
   int64_t cap = nq > sc.cap_nq ? nq : sc.cap_nq;
   if (cap < 256) cap = 256;
   int kc = k > sc.cap_k ? k : sc.cap_k;
@@ -102,8 +104,29 @@ cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k, int d) {
   if (e == cudaSuccess) e = alloc(sc.items, cap * kMaxScanBlocks);
   if (e == cudaSuccess) e = alloc(sc.part, (size_t)cap * kMaxScanBlocks * kc);
   if (e == cudaSuccess) e = alloc(sc.counters, kNumCounters);
+  if (e != cudaSuccess) {
+    free_core(sc);
+    return e;
+  }
+  sc.cap_nq = cap;
+  sc.cap_k = kc;
+  return cudaSuccess;
+}
+
+// Tensor-core scan buffers for nq queries of d columns, allocated only when a search
+// uses that scan (about 16 KB of candidate lists per query of capacity).
+bool tc_scratch_fits(const Scratch& sc, int64_t nq, int d) {
+  const int dpq = ((d + 63) / 64) * 64;
+  return sc.tc_part && nq <= sc.tc_rows && dpq <= sc.tc_dpq;
+}
+
+cudaError_t ensure_tc_scratch(Scratch& sc, int64_t nq, int d) {
+  if (tc_scratch_fits(sc, nq, d)) return cudaSuccess;
+  const int dpq = ((d + 63) / 64) * 64;  // bfloat16 query rows, K padded to 64
+  int64_t cap = nq > sc.tc_rows ? nq : sc.tc_rows;
   const int64_t rows = ((cap + kTcQueryTile - 1) / kTcQueryTile) * kTcQueryTile;
-  if (e == cudaSuccess) e = alloc(sc.tc_bucket, 1024);
+  free_tc(sc);
+  cudaError_t e = alloc(sc.tc_bucket, 1024);
   if (e == cudaSuccess) e = alloc(sc.tc_aq, rows);
   if (e == cudaSuccess) e = alloc(sc.tc_aqn, rows);
   if (e == cudaSuccess) e = cudaMalloc(&sc.tc_qb, (size_t)rows * dpq * 2);
@@ -113,13 +136,11 @@ cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k, int d) {
   if (e == cudaSuccess) e = alloc(sc.tc_pcnt, (size_t)rows * kTcUnitsPerTile);
   if (e == cudaSuccess) e = alloc(sc.tc_thr, rows);
   if (e != cudaSuccess) {
-    free_core(sc);
+    free_tc(sc);
     return e;
   }
   sc.tc_rows = rows;
   sc.tc_dpq = dpq;
-  sc.cap_nq = cap;
-  sc.cap_k = kc;
   return cudaSuccess;
 }
 
@@ -242,8 +263,16 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
   const int kk = rerank_count(p) > k ? rerank_count(p) : k;  // keys per partial scan list
   if (idx->live_plans > 0 && kk > idx->sc.cap_k)
     return fail(UNIFY_E_LIMIT, "search larger than the scratch held by a live plan; destroy the plans first");
-  cudaError_t e = ensure_scratch(idx->sc, nq, kk, idx->ix.d);
+  cudaError_t e = ensure_scratch(idx->sc, nq, kk);
   if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+  // the tensor-core scan has no second-attribute predicate: conjunctive queries use the warp scan
+  const bool tc = !cj && (strategy == UNIFY_PRE || strategy == UNIFY_AUTO) && tc_scan_available(idx->ix, p);
+  if (tc) {
+    if (idx->live_plans > 0 && !tc_scratch_fits(idx->sc, nq, idx->ix.d))
+      return fail(UNIFY_E_LIMIT, "search larger than the scratch held by a live plan; destroy the plans first");
+    e = ensure_tc_scratch(idx->sc, nq, idx->ix.d);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core scan scratch allocation");
+  }
   Scratch& sc = idx->sc;
   e = cudaMemsetAsync(sc.counters, 0, kNumCounters * sizeof(int32_t), st);
   if (e != cudaSuccess) return cuda_fail(e, "counter reset");
@@ -256,8 +285,6 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
                      sc.strat, &o, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "route kernel");
-  // the tensor-core scan has no second-attribute predicate: conjunctive queries use the warp scan
-  const bool tc = !cj && (strategy == UNIFY_PRE || strategy == UNIFY_AUTO) && tc_scan_available(idx->ix, p);
   if (tc) {
     NvtxRange r("unify:tensor-core scan");
     PhaseTimer t(idx->tm, 2, st);
@@ -283,6 +310,7 @@ int resolve_search_params(const DeviceIndex& ix, const unify_params_t* up, int k
 
 void free_scratch(Scratch& sc) {
   free_core(sc);
+  free_tc(sc);
   free_stage(sc);
 }
 
