@@ -300,6 +300,42 @@ def scan_compare(args):
                       "rows_equal_bf16_warp_vs_tensor_core": float(same.mean()), **res}), flush=True)
 
 
+def build_compare(args):
+    """HSIG construction of the c2 shape (int mixture, d = 128, S = 16, M = 16, efCons =
+    100) at n = --n (default 200,000): the host builder on every host core against the
+    GPU-assisted build (the proposal step of every batch of 64 or more nodes on the
+    GPU). Integer vectors make both sides' float32 distances exact, so the two files
+    must be identical. Prints its own JSON line; not part of the default run."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import hsig_build
+    import paper_2412_02448_gb300 as U
+    from workloads import make_workload
+    w = make_workload("c2", seed=args.seed, n=args.n or 200_000, nq=16)
+    d = cache_dir()
+    p_host = os.path.join(d, f"build_compare_host_{os.getpid()}.idx")
+    p_gpu = os.path.join(d, f"build_compare_gpu_{os.getpid()}.idx")
+    hsig_build.compile()
+    try:
+        t = time.perf_counter()
+        hsig_build.build_index(w.vectors, w.attrs, p_host, w.S, w.M, w.efc, seed=w.seed)
+        host_s = time.perf_counter() - t
+        t = time.perf_counter()
+        U.build_index_gpu(w.vectors, w.attrs, p_gpu, w.S, w.M, w.efc, seed=w.seed)
+        gpu_s = time.perf_counter() - t
+        with open(p_host, "rb") as f1, open(p_gpu, "rb") as f2:
+            equal = f1.read() == f2.read()
+    finally:
+        for p_ in (p_host, p_gpu):
+            if os.path.exists(p_):
+                os.remove(p_)
+    print(json.dumps({"mode": "build_compare", "unit": "s", "higher_is_better": False,
+                      "workload": f"c2 shape: n={w.n} d={w.d} int mixture, S={w.S} M={w.M} efCons={w.efc}",
+                      "host_s": round(host_s, 2), "assisted_s": round(gpu_s, 2),
+                      "speedup": round(host_s / gpu_s, 2), "host_cores": os.cpu_count(),
+                      "files_equal": bool(equal)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,9 +363,14 @@ def main():
     ap.add_argument("--nq", type=int, default=0, help="smaller batch (profiling captures only)")
     ap.add_argument("--scan-compare", action="store_true",
                     help="only compare the pre-filter scans on the c5 shape (its own JSON line)")
+    ap.add_argument("--build-compare", action="store_true",
+                    help="only compare host and GPU-assisted HSIG construction (its own JSON line)")
     args = ap.parse_args()
     if args.scan_compare:
         scan_compare(args)
+        return
+    if args.build_compare:
+        build_compare(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

@@ -58,13 +58,19 @@ def _load():
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                 ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_char_p,
                 ctypes.c_char_p, ctypes.c_int]
+            lib.hsig_build_index_ex.restype = ctypes.c_int
+            lib.hsig_build_index_ex.argtypes = lib.hsig_build_index.argtypes + [ctypes.c_void_p, ctypes.c_void_p]
             _lib = lib
     return _lib
 
 
 def build_index(vectors: np.ndarray, attrs: np.ndarray, path: str, S: int, M: int, efc: int,
-                seed: int = 0, threads: int = 0) -> str:
-    """Build the HSIG for (vectors, attrs) and write it to ``path``."""
+                seed: int = 0, threads: int = 0, propose=None) -> str:
+    """Build the HSIG for (vectors, attrs) and write it to ``path``.
+
+    ``propose``: optional (function address, context address) of a C proposal
+    callback with the signature of ``unify_propose_fn``; it takes over the searches
+    of every batch of at least 64 nodes."""
     x = np.ascontiguousarray(vectors, dtype=np.float32)
     a = np.ascontiguousarray(attrs, dtype=np.int64)
     if x.ndim != 2 or a.shape != (x.shape[0],):
@@ -72,8 +78,12 @@ def build_index(vectors: np.ndarray, attrs: np.ndarray, path: str, S: int, M: in
     lib = _load()
     err = ctypes.create_string_buffer(512)
     tmp = path + ".tmp"
-    rc = lib.hsig_build_index(x.ctypes.data, a.ctypes.data, x.shape[0], x.shape[1], S, M, efc,
-                              seed, threads, tmp.encode(), err, 512)
+    if propose is None:
+        rc = lib.hsig_build_index(x.ctypes.data, a.ctypes.data, x.shape[0], x.shape[1], S, M, efc,
+                                  seed, threads, tmp.encode(), err, 512)
+    else:
+        rc = lib.hsig_build_index_ex(x.ctypes.data, a.ctypes.data, x.shape[0], x.shape[1], S, M, efc,
+                                     seed, threads, tmp.encode(), err, 512, propose[0], propose[1])
     if rc != 0:
         raise RuntimeError(f"hsig_build_index failed ({rc}): {err.value.decode()}")
     os.replace(tmp, path)

@@ -28,6 +28,12 @@
 //
 // Distances are float32 squared L2 with a fixed 8-way accumulation order
 // (compiled with -ffp-contract=off), so the graph is the same on every host.
+//
+// The proposal step of a batch (the searches and pruning of every batch node) can be
+// handed to a callback (hsig_build_index_ex), e.g. the GPU's unify_build_propose. The
+// callback sees the graph as it stood at the start of the batch plus the list of
+// chunks changed since its previous call; batches smaller than kAssistMinBatch stay
+// on the host.
 
 #include <algorithm>
 #include <atomic>
@@ -43,6 +49,8 @@
 #ifdef _OPENMP
 #include <omp.h>
 #endif
+
+#include "../include/unify.h"
 
 namespace {
 
@@ -105,6 +113,17 @@ struct Builder {
   std::vector<int32_t> entry_seg;  // S, -1 when the segment holds no node yet
   std::vector<int32_t> top_seg;    // S, level of entry_seg
   std::vector<int32_t> order;      // attribute order (ties by id)
+
+  // Proposal callback (null: every batch is proposed on the host).
+  unify_propose_fn propose_fn = nullptr;
+  void* propose_ctx = nullptr;
+  int propose_rc = 0;
+  std::vector<int64_t> dirty;        // chunks changed since the last callback
+  std::vector<uint8_t> dirty_flag;   // nrows x S
+  std::vector<int32_t> o_ids;
+  std::vector<float> o_dist;
+  std::vector<uint8_t> o_cnt;
+  static constexpr int64_t kAssistMinBatch = 64;
 
   const float* vec(int64_t v) const { return X + v * (int64_t)d; }
   int64_t row(int32_t v, int l) const { return row0[v] + l; }
@@ -286,7 +305,60 @@ struct Builder {
     }
   }
 
-  void build(int threads) {
+  void mark_dirty(int64_t c) {
+    if (!dirty_flag[c]) {
+      dirty_flag[c] = 1;
+      dirty.push_back(c);
+    }
+  }
+
+  // Proposals of the batch [first, first + count) from the callback.
+  bool propose_by_callback(int64_t first, int64_t count, std::vector<Proposal>& props) {
+    const int64_t last = first + count - 1;
+    const int64_t rf = row0[first];
+    const int64_t rows = row0[last] + level[last] + 1 - rf;
+    o_ids.resize((size_t)rows * S * M);
+    o_dist.resize((size_t)rows * S * M);
+    o_cnt.resize((size_t)rows * S);
+    unify_build_view_t vw;
+    vw.n = n;
+    vw.d = d;
+    vw.S = S;
+    vw.M = M;
+    vw.efc = efc;
+    vw.X = X;
+    vw.level = level.data();
+    vw.row0 = row0.data();
+    vw.nrows = nrows;
+    vw.adj = adj.data();
+    vw.cnt = cnt.data();
+    vw.entry_seg = entry_seg.data();
+    vw.top_seg = top_seg.data();
+    vw.dirty = dirty.data();
+    vw.ndirty = (int64_t)dirty.size();
+    vw.first = first;
+    vw.count = count;
+    propose_rc = propose_fn(propose_ctx, &vw, o_ids.data(), o_dist.data(), o_cnt.data());
+    if (propose_rc != 0) return false;
+    for (int64_t c : dirty) dirty_flag[c] = 0;
+    dirty.clear();
+    for (int64_t t = 0; t < count; ++t) {
+      const int32_t v = (int32_t)(first + t);
+      Proposal& P = props[t];
+      P.fwd.assign((size_t)(level[v] + 1) * S, {});
+      for (int l = 0; l <= level[v]; ++l)
+        for (int j = 0; j < S; ++j) {
+          const int64_t o = (row0[v] + l - rf) * S + j;
+          const int c = o_cnt[o];
+          if (c > M) { propose_rc = -1; return false; }
+          std::vector<Key>& f = P.fwd[(size_t)l * S + j];
+          for (int s = 0; s < c; ++s) f.push_back({o_dist[o * M + s], o_ids[o * M + s]});
+        }
+    }
+    return true;
+  }
+
+  bool build(int threads) {
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);
     int nth = omp_get_max_threads();
@@ -296,6 +368,7 @@ struct Builder {
 #endif
     segment();
     assign_levels();
+    if (propose_fn) dirty_flag.assign((size_t)nrows * S, 0);
     std::vector<Visited> vis(nth);
     std::vector<std::vector<Key>> ann(nth), tmp(nth), kept(nth);
     std::vector<Proposal> props;
@@ -307,16 +380,20 @@ struct Builder {
       int64_t end = std::min<int64_t>(n, done + bs);
       int64_t cntb = end - done;
       props.assign(cntb, {});
+      if (propose_fn && cntb >= kAssistMinBatch) {
+        if (!propose_by_callback(done, cntb, props)) return false;
+      } else {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
-      for (int64_t t = 0; t < cntb; ++t) {
+        for (int64_t t = 0; t < cntb; ++t) {
 #ifdef _OPENMP
-        int th = omp_get_thread_num();
+          int th = omp_get_thread_num();
 #else
-        int th = 0;
+          int th = 0;
 #endif
-        propose((int32_t)(done + t), vis[th], props[t], ann[th], tmp[th]);
+          propose((int32_t)(done + t), vis[th], props[t], ann[th], tmp[th]);
+        }
       }
       // forward edges (batch nodes' own rows) and the reverse-edge list, in id order
       revs.clear();
@@ -329,6 +406,7 @@ struct Builder {
             const std::vector<Key>& f = P.fwd[(size_t)l * S + j];
             if (f.empty()) continue;
             set_chunk(row(v, l), j, f);
+            if (propose_fn) mark_dirty(row(v, l) * S + j);
             for (const Key& o : f) revs.push_back({o.second, l, i, v, o.first});
           }
       }
@@ -344,6 +422,11 @@ struct Builder {
           starts.push_back(e);
       starts.push_back(revs.size());
       const int64_t ngroups = (int64_t)starts.size() - 1;
+      if (propose_fn)
+        for (int64_t g = 0; g < ngroups; ++g) {
+          const Rev& e = revs[starts[g]];
+          mark_dirty(row(e.o, e.l) * S + e.i);
+        }
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
@@ -367,6 +450,7 @@ struct Builder {
       }
       done = end;
     }
+    return true;
   }
 
   // ---- skip list (Section 4.1) and global edge masking (Algorithm 5) ----
@@ -543,9 +627,12 @@ extern "C" {
 
 // Builds the HSIG over X (n x d float32, row-major) with integer attributes A and
 // writes it to out_path. Returns 0 on success, a negative code otherwise (message
-// in errbuf). threads <= 0 uses every available core.
-int hsig_build_index(const float* X, const int64_t* A, int64_t n, int d, int S, int M, int efc,
-                     uint64_t seed, int threads, const char* out_path, char* errbuf, int errlen) {
+// in errbuf). threads <= 0 uses every available core. propose (may be null) takes
+// over the proposal step of every batch of at least kAssistMinBatch nodes; ctx is
+// passed through. -3: the callback returned an error (its code in errbuf).
+int hsig_build_index_ex(const float* X, const int64_t* A, int64_t n, int d, int S, int M, int efc,
+                        uint64_t seed, int threads, const char* out_path, char* errbuf, int errlen,
+                        unify_propose_fn propose, void* ctx) {
   auto fail = [&](int code, const std::string& msg) {
     if (errbuf && errlen > 0) {
       std::strncpy(errbuf, msg.c_str(), errlen - 1);
@@ -558,7 +645,9 @@ int hsig_build_index(const float* X, const int64_t* A, int64_t n, int d, int S, 
   if (d < 1 || S < 1 || S > 32 || M < 1 || M > 255 || efc < 1) return fail(-1, "bad d/S/M/efc (S <= 32, M <= 255)");
   Builder b;
   b.n = n; b.d = d; b.S = S; b.M = M; b.efc = efc; b.seed = seed; b.X = X; b.A = A;
-  b.build(threads);
+  b.propose_fn = propose;
+  b.propose_ctx = ctx;
+  if (!b.build(threads)) return fail(-3, "proposal callback failed with code " + std::to_string(b.propose_rc));
   b.finalize(threads);
 
   std::vector<int32_t> upper_base(n, -1);
@@ -607,6 +696,11 @@ int hsig_build_index(const float* X, const int64_t* A, int64_t n, int d, int S, 
   std::string err;
   if (!write_index(out_path, secs, err)) return fail(-2, err);
   return 0;
+}
+
+int hsig_build_index(const float* X, const int64_t* A, int64_t n, int d, int S, int M, int efc,
+                     uint64_t seed, int threads, const char* out_path, char* errbuf, int errlen) {
+  return hsig_build_index_ex(X, A, n, d, S, M, efc, seed, threads, out_path, errbuf, errlen, nullptr, nullptr);
 }
 
 }  // extern "C"

@@ -245,6 +245,64 @@ UNIFY_API int unify_timing_collect(unify_index_t* idx, double* total_ms, int64_t
 /* Message of the last failed call on this thread ("" when none). */
 UNIFY_API const char* unify_last_error(void);
 
+/* ---- GPU-assisted construction ---------------------------------------------
+ * The host builder inserts nodes in id order in batches (HSIGInsert, Algorithm 6;
+ * BackboneConnectionsBuild, Algorithm 4). Every node of a batch searches the graph as
+ * it stood at the start of the batch. For each segment j it:
+ *   - descends the upper layers with ANNSearch (Algorithm 1, ef 1) over the chunks j;
+ *   - on its own layers runs ANNSearch with efCons over the chunks j;
+ *   - prunes the result to M forward edges with the heuristic of Section 2.2.
+ * That per-batch proposal step is what the GPU takes over. The builder passes
+ * unify_build_propose (with a context from unify_build_assist_create) to its entry
+ * point; the builder applies the proposals, reverse edges and entry points on the
+ * host as before.
+ *
+ * The view describes the builder's state at the start of the batch (host memory,
+ * read-only during the call). */
+typedef struct {
+  int64_t n;
+  int d, S, M, efc;
+  const float* X;            /* n x d float32 vectors, row-major */
+  const int32_t* level;      /* n node levels */
+  const int64_t* row0;       /* n: first row of each node; its rows are row0[v] + l, l <= level[v] */
+  int64_t nrows;
+  const int32_t* adj;        /* nrows x S x M neighbour ids, -1 after the chunk's count */
+  const uint8_t* cnt;        /* nrows x S chunk counts */
+  const int32_t* entry_seg;  /* S entry nodes (-1: segment still empty) */
+  const int32_t* top_seg;    /* S levels of the entry nodes */
+  const int64_t* dirty;      /* chunk indices (row * S + j) changed since the previous call */
+  int64_t ndirty;
+  int64_t first, count;      /* the batch: nodes [first, first + count) */
+} unify_build_view_t;
+
+/* Proposal callback: for every node v of the batch, every layer l <= level[v] and
+ * every segment j, the pruned forward list of chunk (row0[v] + l, j), written at row
+ * row0[v] + l - row0[first]: out_ids / out_dist (rows x S x M, ids and distances to v,
+ * ascending by (distance, id)) and out_cnt (rows x S). Returns 0 on success. */
+typedef int (*unify_propose_fn)(void* ctx, const unify_build_view_t* view, int32_t* out_ids, float* out_dist,
+                                uint8_t* out_cnt);
+
+/* Creates the device state of one GPU-assisted build on `device`; *ctx owns a device
+ * mirror of the vectors and the graph until unify_build_assist_destroy (null is a
+ * no-op). Errors: UNIFY_E_ARG (null ctx, no such device), UNIFY_E_NOMEM, UNIFY_E_CUDA. The paper builds on the CPU; this is the GPU path of the
+ * same batched insertion. */
+UNIFY_API int unify_build_assist_create(int device, void** ctx);
+UNIFY_API void unify_build_assist_destroy(void* ctx);
+
+/* The unify_propose_fn of the GPU. The first call uploads the vectors and the whole
+ * graph; later calls upload only the chunks listed in view->dirty. One warp per
+ * (batch node, segment) runs the descent, ANNSearch with the single sorted candidate
+ * buffer of the search kernel, and the pruning heuristic.
+ * Limits: M <= 32, efc <= 256, d <= 1024, S <= 32 (UNIFY_E_LIMIT otherwise; also
+ * when a search exceeds 2^20 expansions). Other errors: UNIFY_E_ARG (null pointers, a
+ * batch outside [0, n), a dirty chunk outside nrows x S, a view whose n, nrows, d, S
+ * or M differ from the first call's), UNIFY_E_NOMEM, UNIFY_E_CUDA. Distances are
+ * float32; on vectors whose squared distances are integers below 2^24 they are exact,
+ * and the proposals equal the host builder's. Synchronous: the outputs are complete
+ * when it returns. */
+UNIFY_API int unify_build_propose(void* ctx, const unify_build_view_t* view, int32_t* out_ids, float* out_dist,
+                                  uint8_t* out_cnt);
+
 #ifdef __cplusplus
 }
 #endif

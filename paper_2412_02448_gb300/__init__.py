@@ -99,6 +99,10 @@ def lib():
             L.unify_timing_collect.restype = ctypes.c_int
             L.unify_last_error.argtypes = []
             L.unify_last_error.restype = ctypes.c_char_p
+            L.unify_build_assist_create.argtypes = [ctypes.c_int, _P]
+            L.unify_build_assist_create.restype = ctypes.c_int
+            L.unify_build_assist_destroy.argtypes = [_P]
+            L.unify_build_assist_destroy.restype = None
             _lib = L
     return _lib
 
@@ -282,3 +286,24 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def build_index_gpu(vectors: np.ndarray, attrs: np.ndarray, path: str, S: int, M: int, efc: int,
+                    seed: int = 0, threads: int = 0, device: int = 0) -> str:
+    """HSIG construction (Algorithms 4-6) with the proposal step of every batch of
+    64 or more nodes (descent, ANNSearch and pruning per node and segment) on GPU
+    ``device``; the host builder applies edges, reverse edges and entry points and
+    writes the file. Needs M <= 32, efc <= 256, d <= 1024, S <= 32."""
+    import hsig_build
+    L = lib()
+    ctx = _P()
+    _check(L.unify_build_assist_create(device, ctypes.byref(ctx)), "unify_build_assist_create")
+    try:
+        fn = ctypes.cast(L.unify_build_propose, _P).value
+        try:
+            return hsig_build.build_index(vectors, attrs, path, S, M, efc, seed=seed, threads=threads,
+                                          propose=(fn, ctx.value))
+        except RuntimeError as e:
+            raise UnifyError(f"{e}: {L.unify_last_error().decode()}") from None
+    finally:
+        L.unify_build_assist_destroy(ctx)

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libunify.so")
-SOURCES = ["index.cu", "route.cu", "search.cu", "tcscan.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["index.cu", "route.cu", "search.cu", "tcscan.cu", "api.cu", "noalloc.cu", "build_assist.cu"]
 HEADERS = ["common.cuh", "internal.h", "warp_ops.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
