@@ -63,12 +63,19 @@ def cache_dir():
     return d
 
 
-def get_index(w, rank, world, barrier):
+def get_index(w, rank, world, barrier, gpu=False):
+    """The cached index of workload w, built on rank 0 when missing: with the
+    GPU-assisted builder when gpu is set (it writes the host builder's file exactly on
+    integer data; other data falls back to the host builder), else on the host."""
     import hsig_build
     path = hsig_build.cached_index_path(cache_dir(), w.name, w.n, w.seed)
     if rank == 0 and not os.path.exists(path):
         t = time.time()
-        hsig_build.build_index(w.vectors, w.attrs, path, w.S, w.M, w.efc, seed=w.seed)
+        if gpu:
+            import paper_2412_02448_gb300 as U
+            U.build_index(w.vectors, w.attrs, path, w.S, w.M, w.efc, seed=w.seed)
+        else:
+            hsig_build.build_index(w.vectors, w.attrs, path, w.S, w.M, w.efc, seed=w.seed)
         log(f"built index {path} in {time.time() - t:.1f} s")
     barrier()
     return path
@@ -406,7 +413,7 @@ def main():
     if args.nq:
         over["nq"] = args.nq
     w0 = make_workload("c2", seed=args.seed, **over)
-    path = get_index(w0, rank, world, barrier)
+    path = get_index(w0, rank, world, barrier, gpu=True)
     # weak scaling: every rank searches its own batch of the same shape
     w = w0
     w.queries, w.lo, w.hi, w.fractions = replicas.rank_batch(w.queries, w.lo, w.hi, w.fractions, rank, args.seed)

@@ -307,3 +307,29 @@ def build_index_gpu(vectors: np.ndarray, attrs: np.ndarray, path: str, S: int, M
             raise UnifyError(f"{e}: {L.unify_last_error().decode()}") from None
     finally:
         L.unify_build_assist_destroy(ctx)
+
+
+def assisted_build_is_exact(vectors: np.ndarray) -> bool:
+    """True when every coordinate is an integer and d * (max - min)^2 < 2^24: every
+    squared distance and every partial sum of one is then an integer below 2^24,
+    exact in float32 in any summation order, so the GPU-assisted build writes the
+    host builder's file byte for byte."""
+    x = np.asarray(vectors)
+    if x.ndim != 2 or x.size == 0:
+        return False
+    span = float(x.max()) - float(x.min())
+    if x.shape[1] * span * span >= float(1 << 24):
+        return False
+    return all(np.array_equal(c, np.rint(c)) for c in np.array_split(x, max(1, x.shape[0] // 65536)))
+
+
+def build_index(vectors: np.ndarray, attrs: np.ndarray, path: str, S: int, M: int, efc: int,
+                seed: int = 0, threads: int = 0, device: int = 0) -> str:
+    """Writes the HSIG of (vectors, attrs) to ``path``: GPU-assisted when that gives
+    the host builder's file exactly (see assisted_build_is_exact, plus the assist's
+    limits M <= 32, efc <= 256, d <= 1024, S <= 32), otherwise the host builder."""
+    import hsig_build
+    if M <= 32 and efc <= 256 and S <= 32 and np.asarray(vectors).shape[1] <= 1024 and \
+            assisted_build_is_exact(vectors):
+        return build_index_gpu(vectors, attrs, path, S, M, efc, seed=seed, threads=threads, device=device)
+    return hsig_build.build_index(vectors, attrs, path, S, M, efc, seed=seed, threads=threads)

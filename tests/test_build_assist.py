@@ -96,3 +96,17 @@ def test_first_callback_sees_the_whole_graph_and_errors_propagate(tmp_path):
     for j in range(S):
         e = int(s["entry"][j])
         assert 0 <= e < first and s["top"][j] == s["level"][e]
+
+
+def test_assisted_build_is_exact_bound():
+    import paper_2412_02448_gb300 as U
+    lo_hi = np.zeros((2, 258), np.float32)
+    lo_hi[1] = 255.0
+    assert U.assisted_build_is_exact(lo_hi)  # 258 * 255^2 < 2^24
+    wide = np.zeros((2, 259), np.float32)
+    wide[1] = 255.0
+    assert not U.assisted_build_is_exact(wide)  # 259 * 255^2 >= 2^24
+    half = lo_hi.copy()
+    half[0, 7] = 0.5
+    assert not U.assisted_build_is_exact(half)
+    assert not U.assisted_build_is_exact(np.zeros((0, 4), np.float32))
