@@ -52,6 +52,13 @@ def c3_small_index():
 
 
 @pytest.fixture(scope="session")
+def c4_small_index():
+    """The 10M precision shape (unit-normalised d = 96 mixture, ranges 1/10/50 %) at
+    n = 20,000."""
+    return built_index("c4", n=20_000, nq=150)
+
+
+@pytest.fixture(scope="session")
 def c5_small_index():
     """GIST-like shape: d = 960 non-negative values in [0, 1]."""
     return built_index("c5", n=6_000, nq=120, efc=60)

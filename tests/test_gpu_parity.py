@@ -534,3 +534,45 @@ def test_tensor_core_scan_partial_slices_and_empty_ranges(U, c3_small_index, c2_
     for key in ("ids", "dist", "count", "status"):
         assert np.array_equal(tc[key], ref[key]), key
     assert (ref["count"] == 0).sum() >= len(lo) // 7
+
+
+def test_c4_precision_shape_k10_k100(U, c4_small_index):
+    """The precision shape (unit-normalised d = 96 mixture, ranges 1/10/50 %) at
+    n = 20,000, auto-routed, at k = 10 and k = 100: BF16 and FP8 E4M3 storage with the
+    FP32 re-rank of 4k candidates. Every returned distance is the float32 direct
+    distance of its id (within 1e-5 of FP64); per range fraction, recall against the
+    exact answer loses at most 0.03 (BF16) and 0.06 (FP8) against FP32 storage at the
+    same parameters, and the rows routed to the pre-filter scan stay near exact."""
+    w, path = c4_small_index
+    ix = U.Index(path)
+    X = w.vectors.astype(np.float64)
+    ta, tb = w.n // 100, w.n // 2
+    fr = np.unique(w.fractions)
+    pre = oracle.OracleIndex(path).route(w.lo, w.hi, ta, tb)["strategy"] == 0
+    assert 0 < pre.sum() < len(pre)
+    report = {}
+    for k in (10, 100):
+        ex_ids, _, ex_c = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, k)
+        rec = {}
+        for dtype in (U.FP32, U.BF16, U.FP8E4M3):
+            p = U.Params.defaults(dtype=dtype, rerank_mult=4, tau_a=ta, tau_b=tb, m=32, ef_post=max(256, 2 * k),
+                                  cand_cap=CAND, visited_cap=2048)
+            r = _np(ix.search(w.queries, w.lo, w.hi, k, ef=max(128, 2 * k), strategy="auto", params=p))
+            _valid(w, r, w.lo, w.hi)
+            for i in range(len(w.lo)):
+                c = r["count"][i]
+                ids = r["ids"][i, :c]
+                d64 = ((X[ids] - w.queries[i].astype(np.float64)) ** 2).sum(1)
+                assert np.all(np.abs(r["dist"][i, :c] - d64) <= 1e-5 * np.maximum(d64, 1e-30)), (k, dtype)
+            rr = oracle.recall(r["ids"], ex_ids, ex_c, k)
+            rec[dtype] = {float(f): float(rr[w.fractions == f].mean()) for f in fr}
+            rec[dtype]["pre"] = float(rr[pre].mean())
+        report[k] = rec
+        for f in fr:
+            f = float(f)
+            assert rec[U.FP32][f] >= 0.85, (k, f, rec)
+            assert rec[U.BF16][f] >= rec[U.FP32][f] - 0.03, (k, f, rec)
+            assert rec[U.FP8E4M3][f] >= rec[U.FP32][f] - 0.06, (k, f, rec)
+        assert rec[U.BF16]["pre"] >= 0.98 and rec[U.FP8E4M3]["pre"] >= 0.95, (k, rec)
+    print("c4-shape recall by k, dtype, fraction:", json.dumps({str(k): {str(d): v for d, v in r_.items()}
+                                                                 for k, r_ in report.items()}))
