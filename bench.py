@@ -310,9 +310,10 @@ def scan_compare(args):
 def build_compare(args):
     """HSIG construction of the c2 shape (int mixture, d = 128, S = 16, M = 16, efCons =
     100) at n = --n (default 200,000): the host builder on every host core against the
-    GPU-assisted build (the proposal step of every batch of 64 or more nodes on the
-    GPU). Integer vectors make both sides' float32 distances exact, so the two files
-    must be identical. Prints its own JSON line; not part of the default run."""
+    GPU-assisted builds, proposals only (the searches of every batch of 64 or more
+    nodes on the GPU) and proposals plus edge application on the GPU. Integer vectors
+    make every float32 distance exact, so the files must be identical. Prints its own
+    JSON line; not part of the default run."""
     import __graft_entry__
     __graft_entry__.build()
     import hsig_build
@@ -321,26 +322,33 @@ def build_compare(args):
     w = make_workload("c2", seed=args.seed, n=args.n or 200_000, nq=16)
     d = cache_dir()
     p_host = os.path.join(d, f"build_compare_host_{os.getpid()}.idx")
-    p_gpu = os.path.join(d, f"build_compare_gpu_{os.getpid()}.idx")
+    p_gpu = {m: os.path.join(d, f"build_compare_{m}_{os.getpid()}.idx") for m in ("propose", "apply")}
     hsig_build.compile()
+    res = {}
     try:
         t = time.perf_counter()
         hsig_build.build_index(w.vectors, w.attrs, p_host, w.S, w.M, w.efc, seed=w.seed)
-        host_s = time.perf_counter() - t
-        t = time.perf_counter()
-        U.build_index_gpu(w.vectors, w.attrs, p_gpu, w.S, w.M, w.efc, seed=w.seed)
-        gpu_s = time.perf_counter() - t
-        with open(p_host, "rb") as f1, open(p_gpu, "rb") as f2:
-            equal = f1.read() == f2.read()
+        res["host_s"] = time.perf_counter() - t
+        for m, p_ in p_gpu.items():
+            t = time.perf_counter()
+            U.build_index_gpu(w.vectors, w.attrs, p_, w.S, w.M, w.efc, seed=w.seed, device_apply=(m == "apply"))
+            res[f"assisted_{m}_s"] = time.perf_counter() - t
+        with open(p_host, "rb") as f:
+            ref = f.read()
+        equal = {}
+        for m, p_ in p_gpu.items():
+            with open(p_, "rb") as f:
+                equal[m] = f.read() == ref
     finally:
-        for p_ in (p_host, p_gpu):
+        for p_ in [p_host, *p_gpu.values()]:
             if os.path.exists(p_):
                 os.remove(p_)
     print(json.dumps({"mode": "build_compare", "unit": "s", "higher_is_better": False,
                       "workload": f"c2 shape: n={w.n} d={w.d} int mixture, S={w.S} M={w.M} efCons={w.efc}",
-                      "host_s": round(host_s, 2), "assisted_s": round(gpu_s, 2),
-                      "speedup": round(host_s / gpu_s, 2), "host_cores": os.cpu_count(),
-                      "files_equal": bool(equal)}), flush=True)
+                      **{k: round(v, 2) for k, v in res.items()},
+                      "speedup_propose": round(res["host_s"] / res["assisted_propose_s"], 2),
+                      "speedup_apply": round(res["host_s"] / res["assisted_apply_s"], 2),
+                      "host_cores": os.cpu_count(), "files_equal": equal}), flush=True)
 
 
 def main():

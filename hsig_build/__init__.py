@@ -59,18 +59,20 @@ def _load():
                 ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_char_p,
                 ctypes.c_char_p, ctypes.c_int]
             lib.hsig_build_index_ex.restype = ctypes.c_int
-            lib.hsig_build_index_ex.argtypes = lib.hsig_build_index.argtypes + [ctypes.c_void_p, ctypes.c_void_p]
+            lib.hsig_build_index_ex.argtypes = lib.hsig_build_index.argtypes + [ctypes.c_void_p] * 4
             _lib = lib
     return _lib
 
 
 def build_index(vectors: np.ndarray, attrs: np.ndarray, path: str, S: int, M: int, efc: int,
-                seed: int = 0, threads: int = 0, propose=None) -> str:
+                seed: int = 0, threads: int = 0, assist=None) -> str:
     """Build the HSIG for (vectors, attrs) and write it to ``path``.
 
-    ``propose``: optional (function address, context address) of a C proposal
-    callback with the signature of ``unify_propose_fn``; it takes over the searches
-    of every batch of at least 64 nodes."""
+    ``assist``: optional (propose, apply, fetch, context) addresses of C callbacks
+    with the signatures of ``unify_propose_fn``, ``unify_apply_fn`` and
+    ``unify_fetch_fn`` (apply and fetch may both be None). propose takes over the
+    searches of every batch of at least 64 nodes; apply and fetch take over edge
+    application from the first proposal on."""
     x = np.ascontiguousarray(vectors, dtype=np.float32)
     a = np.ascontiguousarray(attrs, dtype=np.int64)
     if x.ndim != 2 or a.shape != (x.shape[0],):
@@ -78,12 +80,12 @@ def build_index(vectors: np.ndarray, attrs: np.ndarray, path: str, S: int, M: in
     lib = _load()
     err = ctypes.create_string_buffer(512)
     tmp = path + ".tmp"
-    if propose is None:
+    if assist is None:
         rc = lib.hsig_build_index(x.ctypes.data, a.ctypes.data, x.shape[0], x.shape[1], S, M, efc,
                                   seed, threads, tmp.encode(), err, 512)
     else:
         rc = lib.hsig_build_index_ex(x.ctypes.data, a.ctypes.data, x.shape[0], x.shape[1], S, M, efc,
-                                     seed, threads, tmp.encode(), err, 512, propose[0], propose[1])
+                                     seed, threads, tmp.encode(), err, 512, *assist)
     if rc != 0:
         raise RuntimeError(f"hsig_build_index failed ({rc}): {err.value.decode()}")
     os.replace(tmp, path)

@@ -33,10 +33,15 @@
 // handed to a callback (hsig_build_index_ex), e.g. the GPU's unify_build_propose. The
 // callback sees the graph as it stood at the start of the batch plus the list of
 // chunks changed since its previous call; batches smaller than kAssistMinBatch stay
-// on the host.
+// on the host. With an apply and a fetch callback as well, the graph moves to the
+// callee at the first proposal: from then on every batch is proposed and applied
+// there (the host still derives the reverse-edge groups and the entry points), and
+// the graph is fetched back before the skip list and Algorithm 5.
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -114,9 +119,16 @@ struct Builder {
   std::vector<int32_t> top_seg;    // S, level of entry_seg
   std::vector<int32_t> order;      // attribute order (ties by id)
 
-  // Proposal callback (null: every batch is proposed on the host).
+  // Proposal callback (null: every batch is proposed on the host); apply and fetch
+  // (both null or both set) move edge application to the callee.
   unify_propose_fn propose_fn = nullptr;
+  unify_apply_fn apply_fn = nullptr;
+  unify_fetch_fn fetch_fn = nullptr;
   void* propose_ctx = nullptr;
+  bool device_owns = false;  // the callee holds the current graph
+  std::vector<int64_t> g_chunk, g_start;
+  std::vector<int32_t> r_v;
+  std::vector<float> r_d;
   int propose_rc = 0;
   std::vector<int64_t> dirty;        // chunks changed since the last callback
   std::vector<uint8_t> dirty_flag;   // nrows x S
@@ -124,6 +136,8 @@ struct Builder {
   std::vector<float> o_dist;
   std::vector<uint8_t> o_cnt;
   static constexpr int64_t kAssistMinBatch = 64;
+  // Seconds spent per phase (reported on stderr when HSIG_BUILD_TIMING is set).
+  double t_propose_host = 0, t_propose_cb = 0, t_apply = 0, t_finalize = 0;
 
   const float* vec(int64_t v) const { return X + v * (int64_t)d; }
   int64_t row(int32_t v, int l) const { return row0[v] + l; }
@@ -312,14 +326,7 @@ struct Builder {
     }
   }
 
-  // Proposals of the batch [first, first + count) from the callback.
-  bool propose_by_callback(int64_t first, int64_t count, std::vector<Proposal>& props) {
-    const int64_t last = first + count - 1;
-    const int64_t rf = row0[first];
-    const int64_t rows = row0[last] + level[last] + 1 - rf;
-    o_ids.resize((size_t)rows * S * M);
-    o_dist.resize((size_t)rows * S * M);
-    o_cnt.resize((size_t)rows * S);
+  unify_build_view_t view(int64_t first, int64_t count) {
     unify_build_view_t vw;
     vw.n = n;
     vw.d = d;
@@ -331,6 +338,7 @@ struct Builder {
     vw.row0 = row0.data();
     vw.nrows = nrows;
     vw.adj = adj.data();
+    vw.adjd = adjd.data();
     vw.cnt = cnt.data();
     vw.entry_seg = entry_seg.data();
     vw.top_seg = top_seg.data();
@@ -338,6 +346,18 @@ struct Builder {
     vw.ndirty = (int64_t)dirty.size();
     vw.first = first;
     vw.count = count;
+    return vw;
+  }
+
+  // Proposals of the batch [first, first + count) from the callback.
+  bool propose_by_callback(int64_t first, int64_t count, std::vector<Proposal>& props) {
+    const int64_t last = first + count - 1;
+    const int64_t rf = row0[first];
+    const int64_t rows = row0[last] + level[last] + 1 - rf;
+    o_ids.resize((size_t)rows * S * M);
+    o_dist.resize((size_t)rows * S * M);
+    o_cnt.resize((size_t)rows * S);
+    unify_build_view_t vw = view(first, count);
     propose_rc = propose_fn(propose_ctx, &vw, o_ids.data(), o_dist.data(), o_cnt.data());
     if (propose_rc != 0) return false;
     for (int64_t c : dirty) dirty_flag[c] = 0;
@@ -380,8 +400,11 @@ struct Builder {
       int64_t end = std::min<int64_t>(n, done + bs);
       int64_t cntb = end - done;
       props.assign(cntb, {});
-      if (propose_fn && cntb >= kAssistMinBatch) {
+      auto t0 = std::chrono::steady_clock::now();
+      const bool by_cb = propose_fn && (cntb >= kAssistMinBatch || device_owns);
+      if (by_cb) {
         if (!propose_by_callback(done, cntb, props)) return false;
+        if (apply_fn) device_owns = true;
       } else {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1)
@@ -395,6 +418,8 @@ struct Builder {
           propose((int32_t)(done + t), vis[th], props[t], ann[th], tmp[th]);
         }
       }
+      auto t1 = std::chrono::steady_clock::now();
+      (by_cb ? t_propose_cb : t_propose_host) += std::chrono::duration<double>(t1 - t0).count();
       // forward edges (batch nodes' own rows) and the reverse-edge list, in id order
       revs.clear();
       for (int64_t t = 0; t < cntb; ++t) {
@@ -405,8 +430,10 @@ struct Builder {
           for (int j = 0; j < S; ++j) {
             const std::vector<Key>& f = P.fwd[(size_t)l * S + j];
             if (f.empty()) continue;
-            set_chunk(row(v, l), j, f);
-            if (propose_fn) mark_dirty(row(v, l) * S + j);
+            if (!device_owns) {
+              set_chunk(row(v, l), j, f);
+              if (propose_fn) mark_dirty(row(v, l) * S + j);
+            }
             for (const Key& o : f) revs.push_back({o.second, l, i, v, o.first});
           }
       }
@@ -422,23 +449,45 @@ struct Builder {
           starts.push_back(e);
       starts.push_back(revs.size());
       const int64_t ngroups = (int64_t)starts.size() - 1;
-      if (propose_fn)
+      if (device_owns) {
+        // the callee stores the forward lists and applies the groups in this order
+        g_chunk.resize(ngroups);
+        g_start.resize(ngroups + 1);
+        r_v.resize(revs.size());
+        r_d.resize(revs.size());
         for (int64_t g = 0; g < ngroups; ++g) {
           const Rev& e = revs[starts[g]];
-          mark_dirty(row(e.o, e.l) * S + e.i);
+          g_chunk[g] = row(e.o, e.l) * S + e.i;
+          g_start[g] = (int64_t)starts[g];
         }
+        g_start[ngroups] = (int64_t)revs.size();
+        for (size_t e = 0; e < revs.size(); ++e) {
+          r_v[e] = revs[e].v;
+          r_d[e] = revs[e].dist;
+        }
+        unify_build_view_t vw = view(done, cntb);
+        propose_rc = apply_fn(propose_ctx, &vw, g_chunk.data(), g_start.data(), ngroups, r_v.data(), r_d.data());
+        if (propose_rc != 0) return false;
+      } else {
+        if (propose_fn)
+          for (int64_t g = 0; g < ngroups; ++g) {
+            const Rev& e = revs[starts[g]];
+            mark_dirty(row(e.o, e.l) * S + e.i);
+          }
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
-      for (int64_t g = 0; g < ngroups; ++g) {
+        for (int64_t g = 0; g < ngroups; ++g) {
 #ifdef _OPENMP
-        int th = omp_get_thread_num();
+          int th = omp_get_thread_num();
 #else
-        int th = 0;
+          int th = 0;
 #endif
-        for (size_t e = starts[g]; e < starts[g + 1]; ++e)
-          add_reverse(revs[e].o, revs[e].l, revs[e].i, {revs[e].dist, revs[e].v}, tmp[th], kept[th]);
+          for (size_t e = starts[g]; e < starts[g + 1]; ++e)
+            add_reverse(revs[e].o, revs[e].l, revs[e].i, {revs[e].dist, revs[e].v}, tmp[th], kept[th]);
+        }
       }
+      t_apply += std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
       // entry points (Algorithm 6, line 11): only the node's own segment
       for (int64_t t = 0; t < cntb; ++t) {
         int32_t v = (int32_t)(done + t);
@@ -449,6 +498,11 @@ struct Builder {
         }
       }
       done = end;
+    }
+    if (device_owns) {
+      unify_build_view_t vw = view(n, 0);
+      propose_rc = fetch_fn(propose_ctx, &vw, adj.data(), adjd.data(), cnt.data());
+      if (propose_rc != 0) return false;
     }
     return true;
   }
@@ -628,11 +682,13 @@ extern "C" {
 // Builds the HSIG over X (n x d float32, row-major) with integer attributes A and
 // writes it to out_path. Returns 0 on success, a negative code otherwise (message
 // in errbuf). threads <= 0 uses every available core. propose (may be null) takes
-// over the proposal step of every batch of at least kAssistMinBatch nodes; ctx is
-// passed through. -3: the callback returned an error (its code in errbuf).
+// over the proposal step of every batch of at least kAssistMinBatch nodes; apply and
+// fetch (both null, or both set together with propose) take over edge application
+// from the first proposal on; ctx is passed through. -3: a callback returned an
+// error (its code in errbuf).
 int hsig_build_index_ex(const float* X, const int64_t* A, int64_t n, int d, int S, int M, int efc,
                         uint64_t seed, int threads, const char* out_path, char* errbuf, int errlen,
-                        unify_propose_fn propose, void* ctx) {
+                        unify_propose_fn propose, unify_apply_fn apply, unify_fetch_fn fetch, void* ctx) {
   auto fail = [&](int code, const std::string& msg) {
     if (errbuf && errlen > 0) {
       std::strncpy(errbuf, msg.c_str(), errlen - 1);
@@ -645,10 +701,19 @@ int hsig_build_index_ex(const float* X, const int64_t* A, int64_t n, int d, int 
   if (d < 1 || S < 1 || S > 32 || M < 1 || M > 255 || efc < 1) return fail(-1, "bad d/S/M/efc (S <= 32, M <= 255)");
   Builder b;
   b.n = n; b.d = d; b.S = S; b.M = M; b.efc = efc; b.seed = seed; b.X = X; b.A = A;
+  if ((apply == nullptr) != (fetch == nullptr) || (apply && !propose))
+    return fail(-1, "apply and fetch go together, and need propose");
   b.propose_fn = propose;
+  b.apply_fn = apply;
+  b.fetch_fn = fetch;
   b.propose_ctx = ctx;
-  if (!b.build(threads)) return fail(-3, "proposal callback failed with code " + std::to_string(b.propose_rc));
+  if (!b.build(threads)) return fail(-3, "build callback failed with code " + std::to_string(b.propose_rc));
+  auto tf = std::chrono::steady_clock::now();
   b.finalize(threads);
+  b.t_finalize = std::chrono::duration<double>(std::chrono::steady_clock::now() - tf).count();
+  if (std::getenv("HSIG_BUILD_TIMING"))
+    std::fprintf(stderr, "hsig_build: propose host %.2f s, propose callback %.2f s, apply edges %.2f s, "
+                 "skip list + Algorithm 5 %.2f s\n", b.t_propose_host, b.t_propose_cb, b.t_apply, b.t_finalize);
 
   std::vector<int32_t> upper_base(n, -1);
   int64_t n_upper = 0;
@@ -700,7 +765,8 @@ int hsig_build_index_ex(const float* X, const int64_t* A, int64_t n, int d, int 
 
 int hsig_build_index(const float* X, const int64_t* A, int64_t n, int d, int S, int M, int efc,
                      uint64_t seed, int threads, const char* out_path, char* errbuf, int errlen) {
-  return hsig_build_index_ex(X, A, n, d, S, M, efc, seed, threads, out_path, errbuf, errlen, nullptr, nullptr);
+  return hsig_build_index_ex(X, A, n, d, S, M, efc, seed, threads, out_path, errbuf, errlen, nullptr, nullptr,
+                             nullptr, nullptr);
 }
 
 }  // extern "C"

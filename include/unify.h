@@ -252,13 +252,23 @@ UNIFY_API const char* unify_last_error(void);
  *   - descends the upper layers with ANNSearch (Algorithm 1, ef 1) over the chunks j;
  *   - on its own layers runs ANNSearch with efCons over the chunks j;
  *   - prunes the result to M forward edges with the heuristic of Section 2.2.
- * That per-batch proposal step is what the GPU takes over. The builder passes
- * unify_build_propose (with a context from unify_build_assist_create) to its entry
- * point; the builder applies the proposals, reverse edges and entry points on the
- * host as before.
+ * Then the batch's forward lists are stored, and every forward edge (v -> o) adds the
+ * reverse edge (o -> v) to chunk (o's row, seg(v)), re-pruned to M on overflow
+ * (Algorithm 4). Reverse edges into one chunk are applied in source-id order.
+ *
+ * Three callbacks let the GPU take these steps over (context from
+ * unify_build_assist_create):
+ *   - propose: the searches and pruning of one batch;
+ *   - apply: storing the batch's forward lists and applying its reverse edges;
+ *   - fetch: copying the finished graph back to the host.
+ * With propose alone, the host applies edges itself and lists the chunks it changed in
+ * view->dirty. With apply as well, the graph lives on the device from the first
+ * proposal on: the host applies nothing, and fetch returns the graph before the host's
+ * final passes (skip list, Algorithm 5).
  *
  * The view describes the builder's state at the start of the batch (host memory,
- * read-only during the call). */
+ * read-only during the call). Once the device holds the graph, adj, adjd and cnt
+ * are stale. */
 typedef struct {
   int64_t n;
   int d, S, M, efc;
@@ -267,6 +277,7 @@ typedef struct {
   const int64_t* row0;       /* n: first row of each node; its rows are row0[v] + l, l <= level[v] */
   int64_t nrows;
   const int32_t* adj;        /* nrows x S x M neighbour ids, -1 after the chunk's count */
+  const float* adjd;         /* nrows x S x M distances to the chunk's owner, 0 after the count */
   const uint8_t* cnt;        /* nrows x S chunk counts */
   const int32_t* entry_seg;  /* S entry nodes (-1: segment still empty) */
   const int32_t* top_seg;    /* S levels of the entry nodes */
@@ -282,10 +293,23 @@ typedef struct {
 typedef int (*unify_propose_fn)(void* ctx, const unify_build_view_t* view, int32_t* out_ids, float* out_dist,
                                 uint8_t* out_cnt);
 
+/* Apply callback, called after propose for the same batch: stores the batch's forward
+ * lists (the proposals, non-empty chunks only) and applies the reverse edges. Group g
+ * targets chunk group_chunk[g] (row * S + j) and holds edges group_start[g] ..
+ * group_start[g + 1] - 1 in source-id order: source rev_v[e] at distance rev_dist[e].
+ * Group targets are distinct and belong to nodes inserted before the batch. */
+typedef int (*unify_apply_fn)(void* ctx, const unify_build_view_t* view, const int64_t* group_chunk,
+                              const int64_t* group_start, int64_t ngroups, const int32_t* rev_v,
+                              const float* rev_dist);
+
+/* Fetch callback: writes the whole graph (nrows x S x M ids and distances, nrows x S
+ * counts) into host arrays laid out as in the view. */
+typedef int (*unify_fetch_fn)(void* ctx, const unify_build_view_t* view, int32_t* adj, float* adjd, uint8_t* cnt);
+
 /* Creates the device state of one GPU-assisted build on `device`; *ctx owns a device
  * mirror of the vectors and the graph until unify_build_assist_destroy (null is a
- * no-op). Errors: UNIFY_E_ARG (null ctx, no such device), UNIFY_E_NOMEM, UNIFY_E_CUDA. The paper builds on the CPU; this is the GPU path of the
- * same batched insertion. */
+ * no-op). Errors: UNIFY_E_ARG (null ctx, no such device), UNIFY_E_NOMEM, UNIFY_E_CUDA.
+ * The paper builds on the CPU; this is the GPU path of the same batched insertion. */
 UNIFY_API int unify_build_assist_create(int device, void** ctx);
 UNIFY_API void unify_build_assist_destroy(void* ctx);
 
@@ -302,6 +326,20 @@ UNIFY_API void unify_build_assist_destroy(void* ctx);
  * when it returns. */
 UNIFY_API int unify_build_propose(void* ctx, const unify_build_view_t* view, int32_t* out_ids, float* out_dist,
                                   uint8_t* out_cnt);
+
+/* The unify_apply_fn of the GPU: forward lists from the device copy of the last
+ * proposals, then one warp per group applying its reverse edges in order (skip an
+ * edge already present; insert in (distance, id) order; on overflow re-prune the M + 1
+ * candidates with the heuristic of Section 2.2, float32 distances between them).
+ * Errors: UNIFY_E_ARG (no preceding propose for view->first, a group chunk outside
+ * nrows x S, group_start not ascending or not starting at 0, a source outside
+ * [0, n)), UNIFY_E_NOMEM, UNIFY_E_CUDA. Synchronous. */
+UNIFY_API int unify_build_apply(void* ctx, const unify_build_view_t* view, const int64_t* group_chunk,
+                                const int64_t* group_start, int64_t ngroups, const int32_t* rev_v,
+                                const float* rev_dist);
+
+/* The unify_fetch_fn of the GPU. UNIFY_E_ARG before the first propose. Synchronous. */
+UNIFY_API int unify_build_fetch(void* ctx, const unify_build_view_t* view, int32_t* adj, float* adjd, uint8_t* cnt);
 
 #ifdef __cplusplus
 }

@@ -289,20 +289,25 @@ class Plan:
 
 
 def build_index_gpu(vectors: np.ndarray, attrs: np.ndarray, path: str, S: int, M: int, efc: int,
-                    seed: int = 0, threads: int = 0, device: int = 0) -> str:
+                    seed: int = 0, threads: int = 0, device: int = 0, device_apply: bool = True) -> str:
     """HSIG construction (Algorithms 4-6) with the proposal step of every batch of
     64 or more nodes (descent, ANNSearch and pruning per node and segment) on GPU
-    ``device``; the host builder applies edges, reverse edges and entry points and
-    writes the file. Needs M <= 32, efc <= 256, d <= 1024, S <= 32."""
+    ``device``. With ``device_apply`` the GPU also stores the forward lists and
+    applies the reverse edges (Algorithm 4) from the first proposal on, and the graph
+    returns to the host once, before the skip list and Algorithm 5; otherwise the host
+    applies every batch's edges. Entry points stay on the host, which writes the
+    file. Needs M <= 32, efc <= 256, d <= 1024, S <= 32."""
     import hsig_build
     L = lib()
     ctx = _P()
     _check(L.unify_build_assist_create(device, ctypes.byref(ctx)), "unify_build_assist_create")
     try:
-        fn = ctypes.cast(L.unify_build_propose, _P).value
+        fns = [ctypes.cast(f, _P).value for f in (L.unify_build_propose, L.unify_build_apply, L.unify_build_fetch)]
+        if not device_apply:
+            fns[1] = fns[2] = None
         try:
             return hsig_build.build_index(vectors, attrs, path, S, M, efc, seed=seed, threads=threads,
-                                          propose=(fn, ctx.value))
+                                          assist=(*fns, ctx.value))
         except RuntimeError as e:
             raise UnifyError(f"{e}: {L.unify_last_error().decode()}") from None
     finally:

@@ -12,8 +12,11 @@
 //     id); drop one that is farther from v than from an edge already kept);
 //   * the nearest result is the entry point of the next layer.
 // Here one warp does this for one (batch node, segment) pair against a device
-// mirror of the graph. The host uploads the chunks it changed between calls and
-// applies the proposals, reverse edges and entry points itself.
+// mirror of the graph. Either the host uploads the chunks it changed between calls and
+// applies the proposals and reverse edges itself, or (apply) the device stores the
+// forward lists and applies the reverse edges of Algorithm 4 in its own copy, one warp
+// per target chunk, and the host fetches the graph once at the end. Entry points stay
+// on the host.
 //
 // ANNSearch uses the single sorted buffer of the post-filter search: cand is a
 // subset of ann (every candidate push is also an ann push), so one array E of
@@ -29,7 +32,9 @@
 // Bounds (checked against the buffers of each launch): warps cover
 // count * S pairs (a warp-uniform early return past the end); neighbour slots are
 // read for lane < cnt <= M <= 32; E holds at most ecap >= efc keys; kept at most
-// M <= 32 keys; output rows are row0[v] + l - row0[first] < rows of the batch.
+// M <= 32 keys; output rows are row0[v] + l - row0[first] < rows of the batch. The
+// reverse-edge warps hold at most M + 1 <= 33 candidate keys; group chunks, group
+// bounds and sources are validated on the host before upload.
 #include <cstring>
 #include <new>
 #include <string>
@@ -247,13 +252,108 @@ __global__ void __launch_bounds__(32 * kBuildWarps) build_kernel(BuildArgs a) {
 
 // Writes uploaded chunk contents into the device graph.
 __global__ void scatter_chunks(const int64_t* __restrict__ idx, const int32_t* __restrict__ ids,
-                               const uint8_t* __restrict__ cnt, int64_t nd, int M, int32_t* adj, uint8_t* cnt_dev) {
+                               const float* __restrict__ dist, const uint8_t* __restrict__ cnt, int64_t nd, int M,
+                               int32_t* adj, float* adjd, uint8_t* cnt_dev) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd * M; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = i / M;
     const int s = (int)(i - e * M);
     adj[idx[e] * M + s] = ids[i];
+    adjd[idx[e] * M + s] = dist[i];
     if (s == 0) cnt_dev[idx[e]] = cnt[e];
   }
+}
+
+// Stores the batch's non-empty forward lists (rows x S chunks from row_first on),
+// padding slots past the count with id -1 and distance 0 as the host does.
+__global__ void store_forward(const int32_t* __restrict__ o_ids, const float* __restrict__ o_dist,
+                              const uint8_t* __restrict__ o_cnt, int64_t nchunks, int M, int64_t chunk0,
+                              int32_t* adj, float* adjd, uint8_t* cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nchunks * M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / M;
+    const int s = (int)(i - e * M);
+    const int c = o_cnt[e];
+    if (c == 0) continue;
+    const int64_t dst = (chunk0 + e) * M + s;
+    adj[dst] = s < c ? o_ids[i] : -1;
+    adjd[dst] = s < c ? o_dist[i] : 0.f;
+    if (s == 0) cnt[chunk0 + e] = (uint8_t)c;
+  }
+}
+
+struct RevArgs {
+  const float* X;
+  int dp4, M;
+  int32_t* adj;
+  float* adjd;
+  uint8_t* cnt;
+  const int64_t* g_chunk;
+  const int64_t* g_start;
+  int64_t ngroups;
+  const int32_t* r_v;
+  const float* r_d;
+};
+
+// Algorithm 4's reverse edges, one warp per target chunk, edges in source-id order:
+// an edge already present changes nothing; otherwise it is inserted in (distance, id)
+// order and, when the chunk then holds M + 1 keys, the chunk is re-pruned with the
+// heuristic of Section 2.2 (candidates ascending; one is dropped when it is farther
+// from the owner than from a neighbour already kept).
+template <int CH, int G>
+__global__ void __launch_bounds__(32 * kBuildWarps) reverse_kernel(RevArgs a) {
+  __shared__ uint64_t sK[kBuildWarps][kBuildMaxM + 1];
+  __shared__ uint64_t sKept[kBuildWarps][kBuildMaxM];
+  __shared__ int sList[kBuildWarps][32];
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  const int64_t g = (int64_t)blockIdx.x * kBuildWarps + warp;
+  if (g >= a.ngroups) return;  // whole warps
+  uint64_t* K = sK[warp];
+  uint64_t* kept = sKept[warp];
+  const int64_t ch = a.g_chunk[g];
+  const int M = a.M;
+  int c = a.cnt[ch];
+  uint64_t key = lane < c ? make_key(a.adjd[ch * M + lane], a.adj[ch * M + lane]) : kKeyMax;
+  K[lane] = warp_sort_asc(key);
+  __syncwarp();
+  const int64_t e1 = a.g_start[g + 1];
+  for (int64_t e = a.g_start[g]; e < e1; ++e) {
+    const int32_t v = a.r_v[e];
+    if (__any_sync(kFull, lane < c && key_id(K[lane]) == v)) continue;
+    const uint64_t kv = make_key(a.r_d[e], v);
+    const int pos = __popc(__ballot_sync(kFull, lane < c && K[lane] < kv));
+    const uint64_t mine = lane < c ? K[lane] : 0;
+    __syncwarp();
+    if (lane < c && lane >= pos) K[lane + 1] = mine;
+    __syncwarp();
+    if (lane == 0) K[pos] = kv;
+    __syncwarp();
+    ++c;
+    if (c <= M) continue;
+    int nk = 0;
+    for (int t = 0; t < c && nk < M; ++t) {
+      const uint64_t r = K[t];
+      float4 xr[CH];
+      load_row<CH>(xr, a.X, a.dp4, key_id(r));
+      const int cid = lane < nk ? key_id(kept[lane]) : -1;
+      const float dk = batch_dist<StoreF32, CH, G>(xr, cid, reinterpret_cast<const unsigned char*>(a.X), a.dp4 * 16,
+                                                   nullptr, a.dp4, sList[warp]);
+      if (!__any_sync(kFull, cid >= 0 && key_dist(r) > dk)) {
+        if (lane == 0) kept[nk] = r;
+        ++nk;
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    if (lane < nk) K[lane] = kept[lane];
+    __syncwarp();
+    c = nk;
+  }
+  if (lane < M) {
+    const bool has = lane < c;
+    a.adj[ch * M + lane] = has ? key_id(K[lane]) : -1;
+    a.adjd[ch * M + lane] = has ? key_dist(K[lane]) : 0.f;
+  }
+  if (lane == 0) a.cnt[ch] = (uint8_t)c;
 }
 
 template <class T>
@@ -278,6 +378,7 @@ struct BuildCtx {
   int32_t* level = nullptr;
   int64_t* row0 = nullptr;
   int32_t* adj = nullptr;
+  float* adjd = nullptr;
   uint8_t* cnt = nullptr;
   int32_t* err = nullptr;
   int32_t* o_ids = nullptr;
@@ -286,19 +387,29 @@ struct BuildCtx {
   int64_t o_cap = 0, o_cap_d = 0, o_cap_c = 0;
   int64_t* u_idx = nullptr;
   int32_t* u_ids = nullptr;
+  float* u_dist = nullptr;
   uint8_t* u_cnt = nullptr;
-  int64_t u_cap = 0, u_cap_i = 0, u_cap_c = 0;
+  int64_t u_cap = 0, u_cap_i = 0, u_cap_d = 0, u_cap_c = 0;
   std::vector<int64_t> h_idx;
   std::vector<int32_t> h_ids;
+  std::vector<float> h_dist;
   std::vector<uint8_t> h_cnt;
+  // the last proposals (device buffers o_*): batch and its rows
+  int64_t prop_first = -1, prop_rows = 0, prop_row_first = 0;
+  // reverse-edge groups of the current batch
+  int64_t* g_chunk = nullptr;
+  int64_t* g_start = nullptr;
+  int32_t* r_v = nullptr;
+  float* r_d = nullptr;
+  int64_t g_cap = 0, g_cap_s = 0, r_cap = 0, r_cap_d = 0;
   cudaStream_t st = nullptr;
 };
 
 namespace {
 
 void build_free(BuildCtx* c) {
-  void* ptrs[] = {c->X, c->level, c->row0, c->adj, c->cnt, c->err, c->o_ids, c->o_dist, c->o_cnt,
-                  c->u_idx, c->u_ids, c->u_cnt};
+  void* ptrs[] = {c->X, c->level, c->row0, c->adj, c->adjd, c->cnt, c->err, c->o_ids, c->o_dist, c->o_cnt,
+                  c->u_idx, c->u_ids, c->u_dist, c->u_cnt, c->g_chunk, c->g_start, c->r_v, c->r_d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st) cudaStreamDestroy(c->st);
@@ -337,6 +448,9 @@ int propose(BuildCtx* c, const unify_build_view_t* v, int32_t* out_ids, float* o
     if (e == cudaSuccess) e = cudaMalloc(&c->adj, (size_t)c->nrows * c->S * c->M * 4);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(c->adj, v->adj, (size_t)c->nrows * c->S * c->M * 4, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMalloc(&c->adjd, (size_t)c->nrows * c->S * c->M * 4);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->adjd, v->adjd, (size_t)c->nrows * c->S * c->M * 4, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = cudaMalloc(&c->cnt, (size_t)c->nrows * c->S);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->cnt, v->cnt, (size_t)c->nrows * c->S, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = cudaMalloc(&c->err, 4);
@@ -348,22 +462,28 @@ int propose(BuildCtx* c, const unify_build_view_t* v, int32_t* out_ids, float* o
     const int64_t nd = v->ndirty;
     c->h_idx.assign(v->dirty, v->dirty + nd);
     c->h_ids.resize((size_t)nd * c->M);
+    c->h_dist.resize((size_t)nd * c->M);
     c->h_cnt.resize((size_t)nd);
     for (int64_t i = 0; i < nd; ++i) {
       const int64_t ch = v->dirty[i];
       if (ch < 0 || ch >= c->nrows * c->S) return bfail(UNIFY_E_ARG, "build assist: dirty chunk out of range");
       std::memcpy(&c->h_ids[(size_t)i * c->M], v->adj + ch * c->M, (size_t)c->M * 4);
+      std::memcpy(&c->h_dist[(size_t)i * c->M], v->adjd + ch * c->M, (size_t)c->M * 4);
       c->h_cnt[i] = v->cnt[ch];
     }
     e = grow(c->u_idx, c->u_cap, nd);
     if (e == cudaSuccess) e = grow(c->u_ids, c->u_cap_i, nd * c->M);
+    if (e == cudaSuccess) e = grow(c->u_dist, c->u_cap_d, nd * c->M);
     if (e == cudaSuccess) e = grow(c->u_cnt, c->u_cap_c, nd);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->u_idx, c->h_idx.data(), nd * 8, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(c->u_ids, c->h_ids.data(), nd * c->M * 4, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->u_dist, c->h_dist.data(), nd * c->M * 4, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->u_cnt, c->h_cnt.data(), nd, cudaMemcpyHostToDevice, c->st);
     if (e != cudaSuccess) return bcuda_fail(e, "build assist: chunk upload");
-    scatter_chunks<<<256, 256, 0, c->st>>>(c->u_idx, c->u_ids, c->u_cnt, nd, c->M, c->adj, c->cnt);
+    scatter_chunks<<<256, 256, 0, c->st>>>(c->u_idx, c->u_ids, c->u_dist, c->u_cnt, nd, c->M, c->adj, c->adjd,
+                                           c->cnt);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bcuda_fail(e, "build assist: chunk scatter");
   }
@@ -411,7 +531,74 @@ int propose(BuildCtx* c, const unify_build_view_t* v, int32_t* out_ids, float* o
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return bcuda_fail(e, "build assist: proposals to the host");
   if (herr) return bfail(UNIFY_E_LIMIT, "build assist: a search hit the expansion bound");
+  c->prop_first = v->first;
+  c->prop_rows = rows;
+  c->prop_row_first = row_first;
   return UNIFY_OK;
+}
+
+template <int CH, int G>
+cudaError_t launch_reverse(const RevArgs& a, cudaStream_t st) {
+  const int64_t blocks = (a.ngroups + kBuildWarps - 1) / kBuildWarps;
+  reverse_kernel<CH, G><<<(unsigned)blocks, 32 * kBuildWarps, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+int apply(BuildCtx* c, const unify_build_view_t* v, const int64_t* g_chunk, const int64_t* g_start, int64_t ngroups,
+          const int32_t* r_v, const float* r_d) {
+  if (c->prop_first < 0 || c->prop_first != v->first)
+    return bfail(UNIFY_E_ARG, "unify_build_apply: no proposals for this batch");
+  if (ngroups < 0 || (ngroups > 0 && (!g_chunk || !g_start)) || !g_start)
+    return bfail(UNIFY_E_ARG, "unify_build_apply: bad groups");
+  if (g_start[0] != 0) return bfail(UNIFY_E_ARG, "unify_build_apply: group_start[0] must be 0");
+  for (int64_t g = 0; g < ngroups; ++g) {
+    if (g_chunk[g] < 0 || g_chunk[g] >= c->nrows * c->S)
+      return bfail(UNIFY_E_ARG, "unify_build_apply: group chunk out of range");
+    if (g_start[g + 1] < g_start[g]) return bfail(UNIFY_E_ARG, "unify_build_apply: group_start not ascending");
+  }
+  const int64_t nrev = g_start[ngroups];
+  if (nrev > 0 && (!r_v || !r_d)) return bfail(UNIFY_E_ARG, "unify_build_apply: null edges");
+  for (int64_t i = 0; i < nrev; ++i)
+    if (r_v[i] < 0 || r_v[i] >= c->n) return bfail(UNIFY_E_ARG, "unify_build_apply: source out of range");
+  // forward lists of the batch from the device copy of its proposals
+  store_forward<<<1024, 256, 0, c->st>>>(c->o_ids, c->o_dist, c->o_cnt, c->prop_rows * c->S, c->M,
+                                         c->prop_row_first * c->S, c->adj, c->adjd, c->cnt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bcuda_fail(e, "unify_build_apply: forward lists");
+  c->prop_first = -1;
+  if (ngroups == 0) {
+    e = cudaStreamSynchronize(c->st);
+    return e == cudaSuccess ? UNIFY_OK : bcuda_fail(e, "unify_build_apply");
+  }
+  e = grow(c->g_chunk, c->g_cap, ngroups);
+  if (e == cudaSuccess) e = grow(c->g_start, c->g_cap_s, ngroups + 1);
+  if (e == cudaSuccess) e = grow(c->r_v, c->r_cap, nrev);
+  if (e == cudaSuccess) e = grow(c->r_d, c->r_cap_d, nrev);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->g_chunk, g_chunk, ngroups * 8, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->g_start, g_start, (ngroups + 1) * 8, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess && nrev > 0) e = cudaMemcpyAsync(c->r_v, r_v, nrev * 4, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess && nrev > 0) e = cudaMemcpyAsync(c->r_d, r_d, nrev * 4, cudaMemcpyHostToDevice, c->st);
+  if (e != cudaSuccess) return bcuda_fail(e, "unify_build_apply: edge upload");
+  RevArgs a;
+  a.X = c->X;
+  a.dp4 = c->dp / 4;
+  a.M = c->M;
+  a.adj = c->adj;
+  a.adjd = c->adjd;
+  a.cnt = c->cnt;
+  a.g_chunk = c->g_chunk;
+  a.g_start = c->g_start;
+  a.ngroups = ngroups;
+  a.r_v = c->r_v;
+  a.r_d = c->r_d;
+  const int chn = (a.dp4 + 31) / 32;
+  if (chn <= 1) e = launch_reverse<1, 16>(a, c->st);
+  else if (chn <= 2) e = launch_reverse<2, 8>(a, c->st);
+  else if (chn <= 4) e = launch_reverse<4, 4>(a, c->st);
+  else e = launch_reverse<8, 2>(a, c->st);
+  if (e != cudaSuccess) return bcuda_fail(e, "unify_build_apply: reverse-edge kernel");
+  e = cudaStreamSynchronize(c->st);
+  return e == cudaSuccess ? UNIFY_OK : bcuda_fail(e, "unify_build_apply");
 }
 
 }  // namespace
@@ -438,6 +625,31 @@ extern "C" void unify_build_assist_destroy(void* ctx) {
   DeviceGuard guard(c->device);
   build_free(c);
   delete c;
+}
+
+extern "C" int unify_build_apply(void* ctx, const unify_build_view_t* view, const int64_t* group_chunk,
+                                 const int64_t* group_start, int64_t ngroups, const int32_t* rev_v,
+                                 const float* rev_dist) {
+  if (!ctx || !view) return bfail(UNIFY_E_ARG, "unify_build_apply: null pointer");
+  BuildCtx* c = static_cast<BuildCtx*>(ctx);
+  if (!c->ready) return bfail(UNIFY_E_ARG, "unify_build_apply: no preceding unify_build_propose");
+  DeviceGuard guard(c->device);
+  return apply(c, view, group_chunk, group_start, ngroups, rev_v, rev_dist);
+}
+
+extern "C" int unify_build_fetch(void* ctx, const unify_build_view_t* view, int32_t* adj, float* adjd, uint8_t* cnt) {
+  if (!ctx || !view || !adj || !adjd || !cnt) return bfail(UNIFY_E_ARG, "unify_build_fetch: null pointer");
+  BuildCtx* c = static_cast<BuildCtx*>(ctx);
+  if (!c->ready) return bfail(UNIFY_E_ARG, "unify_build_fetch: no preceding unify_build_propose");
+  if (view->nrows != c->nrows || view->S != c->S || view->M != c->M)
+    return bfail(UNIFY_E_ARG, "unify_build_fetch: the view changed shape");
+  DeviceGuard guard(c->device);
+  const size_t slots = (size_t)c->nrows * c->S * c->M;
+  cudaError_t e = cudaMemcpyAsync(adj, c->adj, slots * 4, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(adjd, c->adjd, slots * 4, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, c->cnt, (size_t)c->nrows * c->S, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  return e == cudaSuccess ? UNIFY_OK : bcuda_fail(e, "unify_build_fetch");
 }
 
 extern "C" int unify_build_propose(void* ctx, const unify_build_view_t* view, int32_t* out_ids, float* out_dist,

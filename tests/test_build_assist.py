@@ -19,7 +19,7 @@ class View(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int), ("S", ctypes.c_int), ("M", ctypes.c_int),
                 ("efc", ctypes.c_int), ("X", ctypes.c_void_p), ("level", ctypes.c_void_p),
                 ("row0", ctypes.c_void_p), ("nrows", ctypes.c_int64), ("adj", ctypes.c_void_p),
-                ("cnt", ctypes.c_void_p), ("entry_seg", ctypes.c_void_p), ("top_seg", ctypes.c_void_p),
+                ("adjd", ctypes.c_void_p), ("cnt", ctypes.c_void_p), ("entry_seg", ctypes.c_void_p), ("top_seg", ctypes.c_void_p),
                 ("dirty", ctypes.c_void_p), ("ndirty", ctypes.c_int64), ("first", ctypes.c_int64),
                 ("count", ctypes.c_int64)]
 
@@ -33,7 +33,7 @@ def _arr(addr, ctype, count):
 
 
 def test_view_layout_matches_header(tmp_path):
-    fields = ["n", "d", "S", "M", "efc", "X", "level", "row0", "nrows", "adj", "cnt", "entry_seg",
+    fields = ["n", "d", "S", "M", "efc", "X", "level", "row0", "nrows", "adj", "adjd", "cnt", "entry_seg",
               "top_seg", "dirty", "ndirty", "first", "count"]
     prog = tmp_path / "v.c"
     prog.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "unify.h"\nint main(void){'
@@ -79,7 +79,7 @@ def test_first_callback_sees_the_whole_graph_and_errors_propagate(tmp_path):
     fn = PROPOSE(cb)
     with pytest.raises(RuntimeError, match=r"\(-3\).*code 7"):
         hsig_build.build_index(x, a, str(tmp_path / "g.idx"), S, M, efc, seed=5,
-                               propose=(ctypes.cast(fn, ctypes.c_void_p).value, None))
+                               assist=(ctypes.cast(fn, ctypes.c_void_p).value, None, None, None))
     assert len(seen) == 1
     s = seen[0]
     first, count = _first_assisted_batch(n)
@@ -110,3 +110,90 @@ def test_assisted_build_is_exact_bound():
     half[0, 7] = 0.5
     assert not U.assisted_build_is_exact(half)
     assert not U.assisted_build_is_exact(np.zeros((0, 4), np.float32))
+
+
+APPLY = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(View), ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p)
+FETCH = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(View), ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.c_void_p)
+
+
+def test_device_owned_graph_protocol(tmp_path):
+    """With apply and fetch, every batch from the first proposal on (the last, short one
+    included) is proposed and applied by the callee, in strict alternation; apply gets
+    the reverse edges of the proposals grouped by target chunk (ascending) in source-id
+    order; fetch runs once, at the end, and its graph is what the file holds."""
+    rng = np.random.default_rng(4)
+    n, d, S, M, efc = 4300, 4, 2, 4, 8
+    x = rng.integers(0, 8, size=(n, d)).astype(np.float32)
+    a = rng.permutation(n).astype(np.int64)
+    calls, snap = [], {}
+
+    def propose(ctx, view, out_ids, out_dist, out_cnt):
+        v = view.contents
+        level = _arr(v.level, ctypes.c_int32, v.n)
+        row0 = _arr(v.row0, ctypes.c_int64, v.n)
+        if not snap:
+            snap.update(adj=_arr(v.adj, ctypes.c_int32, v.nrows * S * M),
+                        adjd=_arr(v.adjd, ctypes.c_float, v.nrows * S * M),
+                        cnt=_arr(v.cnt, ctypes.c_uint8, v.nrows * S), nrows=v.nrows)
+        rf = row0[v.first]
+        last = v.first + v.count - 1
+        rows = row0[last] + level[last] + 1 - rf
+        cnt = np.zeros(rows * S, np.uint8)
+        ids = np.zeros(rows * S * M, np.int32)
+        dist = np.zeros(rows * S * M, np.float32)
+        # one forward edge per node: layer 0, segment 0, to the node inserted just before the batch
+        for t in range(v.count):
+            e = (row0[v.first + t] - rf) * S
+            cnt[e] = 1
+            ids[e * M] = v.first - 1
+            dist[e * M] = float(t + 1)
+        ctypes.memmove(out_cnt, cnt.ctypes.data, cnt.nbytes)
+        ctypes.memmove(out_ids, ids.ctypes.data, ids.nbytes)
+        ctypes.memmove(out_dist, dist.ctypes.data, dist.nbytes)
+        calls.append(("propose", v.first, v.count))
+        return 0
+
+    def apply(ctx, view, gc, gs, ng, rv, rd):
+        v = view.contents
+        g_chunk = _arr(gc, ctypes.c_int64, ng)
+        g_start = _arr(gs, ctypes.c_int64, ng + 1)
+        srcs = _arr(rv, ctypes.c_int32, g_start[-1])
+        dists = _arr(rd, ctypes.c_float, g_start[-1])
+        calls.append(("apply", v.first, v.count, g_chunk, g_start, srcs, dists))
+        return 0
+
+    def fetch(ctx, view, adj, adjd, cnt):
+        calls.append(("fetch",))
+        ctypes.memmove(adj, snap["adj"].ctypes.data, snap["adj"].nbytes)
+        ctypes.memmove(adjd, snap["adjd"].ctypes.data, snap["adjd"].nbytes)
+        ctypes.memmove(cnt, snap["cnt"].ctypes.data, snap["cnt"].nbytes)
+        return 0
+
+    fns = [PROPOSE(propose), APPLY(apply), FETCH(fetch)]
+    path = hsig_build.build_index(x, a, str(tmp_path / "g.idx"), S, M, efc, seed=2,
+                                  assist=tuple(ctypes.cast(f, ctypes.c_void_p).value for f in fns) + (None,))
+    first, _ = _first_assisted_batch(n)
+    assert calls[-1] == ("fetch",) and sum(c[0] == "fetch" for c in calls) == 1
+    body = calls[:-1]
+    assert [c[0] for c in body] == ["propose", "apply"] * (len(body) // 2)
+    assert body[0][1] == first
+    starts = [c[1] for c in body[0::2]]
+    counts = [c[2] for c in body[0::2]]
+    assert starts == list(np.cumsum([first] + counts[:-1])) and starts[-1] + counts[-1] == n
+    assert counts[-1] < 64  # the short last batch stays with the callee
+    for (_, f, c), (_, f2, c2, g_chunk, g_start, srcs, dists) in zip(body[0::2], body[1::2]):
+        assert (f, c) == (f2, c2)
+        assert g_start[0] == 0 and np.all(np.diff(g_start) > 0) and np.all(np.diff(g_chunk) > 0)
+        # every batch node's single edge comes back, grouped by its segment's chunk of node f - 1
+        assert sorted(srcs.tolist()) == list(range(f, f + c))
+        for g in range(len(g_chunk)):
+            s_ = srcs[g_start[g]:g_start[g + 1]]
+            assert np.all(np.diff(s_) > 0)
+            assert np.array_equal(dists[g_start[g]:g_start[g + 1]], (s_ - f + 1).astype(np.float32))
+    # the file holds the fetched graph (the snapshot taken at the first proposal)
+    g = hsig_build.read_index(path)
+    adj = snap["adj"].reshape(snap["nrows"], S, M)
+    row0 = np.concatenate([[0], np.cumsum(np.asarray(g["level"]) + 1)[:-1]])
+    assert np.array_equal(np.asarray(g["adj0"]), adj[row0])

@@ -44,11 +44,15 @@ def _case(name):
 
 @pytest.mark.parametrize("name", ["c2_int_d128", "int_d200_dup_attrs"])
 def test_assisted_build_equals_host_build(U, tmp_path, name):
+    """Both modes: proposals only (the host applies edges and uploads changed chunks),
+    and proposals plus edge application on the device (the graph fetched at the end)."""
     import hsig_build
     x, a, S, M, efc = _case(name)
     host = hsig_build.build_index(x, a, str(tmp_path / "host.idx"), S, M, efc, seed=3)
-    gpu = U.build_index_gpu(x, a, str(tmp_path / "gpu.idx"), S, M, efc, seed=3)
-    assert _same_file(host, gpu)
+    for device_apply in (False, True):
+        gpu = U.build_index_gpu(x, a, str(tmp_path / f"gpu{int(device_apply)}.idx"), S, M, efc, seed=3,
+                                device_apply=device_apply)
+        assert _same_file(host, gpu), device_apply
 
 
 def test_assisted_build_real_valued(U, tmp_path):
