@@ -94,6 +94,20 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
             log(f"tune {what} ef={p.ef} ef_post={p.ef_post} m={p.m} tau=({p.tau_a},{p.tau_b}): "
                 f"{ms:.3f} ms/batch, recall {gr}")
 
+    def refine(cands, what):
+        """The fastest of cands (tuples led by Params and ms) after re-timing the three
+        fastest with four times the repetitions: single short timings of a ~2 ms batch
+        vary by a few percent, enough to pick a slower configuration."""
+        top = sorted(cands, key=lambda c: c[1])[:3]
+        best_ = None
+        for c in top:
+            ms, _ = _time_search(index, q, lo, hi, k, c[0], 4 * reps, torch)
+            if log:
+                log(f"tune re-time {what}: {c[1]:.3f} -> {ms:.3f} ms/batch")
+            if best_ is None or ms < best_[1]:
+                best_ = (c[0], ms) + tuple(c[2:])
+        return best_
+
     def beams(ref):
         strat = index.route(lo, hi, ref.tau_a, ref.tau_b)["strategy"].cpu().numpy()
         chosen = {"ef": ref.ef, "ef_post": ref.ef_post, "m": ref.m}
@@ -131,18 +145,18 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
 
     cur = beams(base)
     if calibrate_tau:
-        best = None
+        passing = []
         for fa in tau_a_fracs:
             for fb in tau_b_fracs:
                 p = make({"tau_a": int(fa * n), "tau_b": int(fb * n)}, cur)
                 ms, rec = run(p)
                 gr = group_recall(rec, groups)
                 note(p, ms, gr, "tau")
-                if min(gr.values()) >= target and (best is None or ms < best[1]):
-                    best = (p, ms)
-        if best is not None:
-            cur = beams(best[0])
-    best = None
+                if min(gr.values()) >= target:
+                    passing.append((p, ms))
+        if passing:
+            cur = beams(refine(passing, "tau")[0])
+    passing = []
     shapes = [{}, {"warps_per_block": 2}, {"cand_cap": 256}, {"cand_cap": 1024},
                   {"visited_cap": 1024}, {"visited_cap": 4096}, {"scan_rows": 1024}, {"scan_rows": 2048},
                   {"scan_rows": 4096}, {"reg_budget": 80, "visited_cap": 1024},
@@ -163,8 +177,9 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
             continue
         gr = group_recall(rec, groups)
         note(p, ms, gr, f"shape {extra}")
-        if min(gr.values()) >= target and (best is None or ms < best[1]):
-            best = (p, ms, gr)
+        if min(gr.values()) >= target:
+            passing.append((p, ms, gr))
+    best = refine(passing, "shape") if passing else None
     if best is None:
         ms, rec = run(cur)
         best = (cur, ms, group_recall(rec, groups))

@@ -1,0 +1,83 @@
+"""The autotuner's selection logic on the CPU, against a fake index whose recall and
+batch time follow a fixed model (the timing function is replaced; no GPU work):
+beam widths are the smallest meeting the target per strategy, the (tau_A, tau_B)
+pair and the launch shape are the fastest meeting it, and a configuration that only
+looks fastest in a short timing loses once the leaders are re-timed."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2412_02448_gb300 as U  # noqa: E402
+from paper_2412_02448_gb300 import autotune  # noqa: E402
+
+K = 10
+NQ = 60
+Y = np.tile(np.array([50, 5_000, 40_000]), NQ // 3)  # in-range counts of the queries
+GROUPS = np.tile(np.array([0.001, 0.02, 0.4]), NQ // 3)
+N = 100_000
+
+
+class FakeIndex:
+    n = N
+
+    def route(self, lo, hi, tau_a, tau_b):
+        s = np.where(Y <= tau_a, U.PRE, np.where(Y >= tau_b, U.POST, U.HYBRID))
+        return {"strategy": torch.from_numpy(s.astype(np.int32))}
+
+
+def _ids(p):
+    """Exact rows, except hybrid rows below ef 32 and post rows below ef_post 48,
+    which find half of their neighbours."""
+    s = FakeIndex().route(None, None, p.tau_a, p.tau_b)["strategy"].numpy()
+    ids = np.tile(np.arange(K, dtype=np.int64), (NQ, 1))
+    bad = ((s == U.HYBRID) & (p.ef < 32)) | ((s == U.POST) & (p.ef_post < 48))
+    ids[bad, K // 2:] = -1
+    return ids
+
+
+def _true_ms(p):
+    ms = 2.0 + 0.002 * p.ef + 0.001 * p.ef_post + 0.004 * p.m
+    # routing: fastest at tau_A = 2 % and tau_B = 30 % of n
+    ms += abs(p.tau_a - 0.02 * N) / N + abs(p.tau_b - 0.3 * N) / N
+    if p.visited_cap == 1024 and p.reg_budget == 128:
+        ms -= 0.2
+    if p.cand_cap == 256 and p.reg_budget == 128 and p.visited_cap == 2048:
+        ms -= 0.15
+    if p.selection == 1:
+        ms += 1.0
+    return ms
+
+
+def fake_time(index, q, lo, hi, k, params, reps, torch_, strategy="auto"):
+    ms = _true_ms(params)
+    if reps < 10 and params.cand_cap == 256 and params.reg_budget == 128 and params.visited_cap == 2048:
+        ms -= 0.1  # a short timing that flatters this shape
+    return ms, {"ids": torch.from_numpy(_ids(params))}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    """Params.defaults() comes from the compiled library (host code only)."""
+    import os
+    import shutil
+    if not (shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc")):
+        pytest.skip("nvcc not available")
+    U.build()
+
+
+def test_tuner_picks_the_fastest_passing_configuration(monkeypatch):
+    monkeypatch.setattr(autotune, "_time_search", fake_time)
+    truth = np.tile(np.arange(K, dtype=np.int64), (NQ, 1))
+    count = np.full(NQ, K)
+    p, rep = autotune.tune(FakeIndex(), None, None, None, K, truth, count, GROUPS, target=0.95,
+                           efs=(16, 24, 32, 48, 64), ms_=(16, 32), reps=3,
+                           tau_a_fracs=(0.01, 0.02, 0.05), tau_b_fracs=(0.3, 0.5))
+    assert (p.tau_a, p.tau_b) == (2_000, 30_000)
+    assert p.ef == 32 and p.m == 16  # smallest passing hybrid beam, cheapest m
+    assert p.ef_post == 48           # smallest passing post beam
+    assert p.visited_cap == 1024 and p.cand_cap == 512 and p.reg_budget == 128
+    assert p.selection == 2
+    assert min(rep["recall"].values()) >= 0.95
+    shapes = [t for t in rep["trials"] if t["what"].startswith("shape")]
+    assert len(shapes) >= 13
