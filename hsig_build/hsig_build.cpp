@@ -378,6 +378,50 @@ struct Builder {
     return true;
   }
 
+  struct Rev { int32_t o; int32_t l; int32_t i; int32_t v; float dist; };
+  std::vector<uint64_t> rev_key, rev_key_tmp;
+  std::vector<uint32_t> rev_idx, rev_idx_tmp;
+  std::vector<Rev> rev_tmp;
+  std::vector<size_t> radix_count;
+
+  // Stable LSD radix sort of revs by target chunk index, 11 bits per pass; leaves the
+  // sorted keys in rev_key.
+  void sort_by_chunk(std::vector<Rev>& revs) {
+    const size_t N = revs.size();
+    rev_key.resize(N);
+    rev_idx.resize(N);
+    uint64_t kmax = 0;
+    for (size_t e = 0; e < N; ++e) {
+      rev_key[e] = (uint64_t)(row(revs[e].o, revs[e].l) * S + revs[e].i);
+      rev_idx[e] = (uint32_t)e;
+      kmax = std::max(kmax, rev_key[e]);
+    }
+    rev_key_tmp.resize(N);
+    rev_idx_tmp.resize(N);
+    constexpr int kBits = 11;
+    radix_count.assign((size_t)1 << kBits, 0);
+    for (int shift = 0; shift == 0 || (kmax >> shift) != 0; shift += kBits) {
+      std::fill(radix_count.begin(), radix_count.end(), 0);
+      for (size_t e = 0; e < N; ++e) radix_count[(rev_key[e] >> shift) & ((1u << kBits) - 1)]++;
+      size_t sum = 0;
+      for (size_t& c : radix_count) {
+        const size_t t = c;
+        c = sum;
+        sum += t;
+      }
+      for (size_t e = 0; e < N; ++e) {
+        const size_t dst = radix_count[(rev_key[e] >> shift) & ((1u << kBits) - 1)]++;
+        rev_key_tmp[dst] = rev_key[e];
+        rev_idx_tmp[dst] = rev_idx[e];
+      }
+      rev_key.swap(rev_key_tmp);
+      rev_idx.swap(rev_idx_tmp);
+    }
+    rev_tmp.resize(N);
+    for (size_t e = 0; e < N; ++e) rev_tmp[e] = revs[rev_idx[e]];
+    revs.swap(rev_tmp);
+  }
+
   bool build(int threads) {
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);
@@ -392,7 +436,6 @@ struct Builder {
     std::vector<Visited> vis(nth);
     std::vector<std::vector<Key>> ann(nth), tmp(nth), kept(nth);
     std::vector<Proposal> props;
-    struct Rev { int32_t o; int32_t l; int32_t i; int32_t v; float dist; };
     std::vector<Rev> revs;
     int64_t done = 0;
     while (done < n) {
@@ -437,16 +480,13 @@ struct Builder {
             for (const Key& o : f) revs.push_back({o.second, l, i, v, o.first});
           }
       }
-      // reverse edges grouped by target chunk, applied in source-id order
-      std::stable_sort(revs.begin(), revs.end(), [](const Rev& a, const Rev& b) {
-        if (a.o != b.o) return a.o < b.o;
-        if (a.l != b.l) return a.l < b.l;
-        return a.i < b.i;
-      });
+      // reverse edges grouped by target chunk, applied in source-id order: a stable
+      // sort by chunk index (row(o, l) * S + i orders as (o, l, i), since a node's rows
+      // are contiguous and ascend with its id)
+      sort_by_chunk(revs);
       std::vector<size_t> starts;
       for (size_t e = 0; e < revs.size(); ++e)
-        if (e == 0 || revs[e].o != revs[e - 1].o || revs[e].l != revs[e - 1].l || revs[e].i != revs[e - 1].i)
-          starts.push_back(e);
+        if (e == 0 || rev_key[e] != rev_key[e - 1]) starts.push_back(e);
       starts.push_back(revs.size());
       const int64_t ngroups = (int64_t)starts.size() - 1;
       if (device_owns) {
@@ -456,8 +496,7 @@ struct Builder {
         r_v.resize(revs.size());
         r_d.resize(revs.size());
         for (int64_t g = 0; g < ngroups; ++g) {
-          const Rev& e = revs[starts[g]];
-          g_chunk[g] = row(e.o, e.l) * S + e.i;
+          g_chunk[g] = (int64_t)rev_key[starts[g]];
           g_start[g] = (int64_t)starts[g];
         }
         g_start[ngroups] = (int64_t)revs.size();
