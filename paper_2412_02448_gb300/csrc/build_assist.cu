@@ -407,12 +407,17 @@ struct BuildCtx {
 
 namespace {
 
+// Frees every device buffer and the stream, and returns the context to its state
+// after creation (same device).
 void build_free(BuildCtx* c) {
   void* ptrs[] = {c->X, c->level, c->row0, c->adj, c->adjd, c->cnt, c->err, c->o_ids, c->o_dist, c->o_cnt,
                   c->u_idx, c->u_ids, c->u_dist, c->u_cnt, c->g_chunk, c->g_start, c->r_v, c->r_d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st) cudaStreamDestroy(c->st);
+  const int dev = c->device;
+  *c = BuildCtx();
+  c->device = dev;
 }
 
 template <int CH, int G>
@@ -455,7 +460,12 @@ int propose(BuildCtx* c, const unify_build_view_t* v, int32_t* out_ids, float* o
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->cnt, v->cnt, (size_t)c->nrows * c->S, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = cudaMalloc(&c->err, 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, 4, c->st);
-    if (e != cudaSuccess) return bcuda_fail(e, "build assist: device copy of the graph");
+    if (e != cudaSuccess) {
+      // start clean on a later call: nothing of the partial copy stays allocated
+      if (c->st) cudaStreamSynchronize(c->st);
+      build_free(c);
+      return bcuda_fail(e, "build assist: device copy of the graph");
+    }
     c->ready = true;
   } else if (v->ndirty > 0) {
     // the chunks the host changed since the previous batch
