@@ -35,7 +35,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_replicas():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of a possibly CUDA-initialised parent
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     (m0, q0, lo0, f0), (m1, q1, lo1, f1) = out[0], out[1]
