@@ -465,7 +465,11 @@ def main():
     d = w.d
 
     def algorithmic_bytes(params, counters):
-        """Bytes the search kernel must move per launch (kernels)."""
+        """Bytes the search kernel must move per launch, by strategy: a scanned row
+        (its storage bytes plus the 4-byte id) per in-range row for A; per distance
+        evaluation one row, and per expansion the adjacency slots read (S' chunks of
+        ceil(m / S') slots for C; M slots plus the bitmap words for B); plus the FP32
+        re-rank rows of the BF16/FP8 paths."""
         isA, isB, isC = routing["isA"], routing["isB"], routing["isC"]
         row = {U.FP32: 4 * d, U.BF16: 2 * d, U.FP8E4M3: d + 4}[params.dtype]
         per = np.minimum(ix.M, -(-params.m // np.maximum(Sp, 1)))
