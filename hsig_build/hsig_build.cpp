@@ -166,7 +166,7 @@ struct Builder {
     }
   }
 
-  // ---- levels (Algorithm 6, line 2) ----
+  // ---- levels (the level draw of Algorithm 6) ----
   void assign_levels() {
     level.resize(n);
     row0.resize(n);
@@ -298,7 +298,7 @@ struct Builder {
     chunkn(r, j) = (uint8_t)c;
   }
 
-  // Algorithm 4, lines 4-6: add (o -> v) to G[o][i], re-prune on overflow.
+  // Algorithm 4, reverse edges: add (o -> v) to G[o][i], re-prune on overflow.
   void add_reverse(int32_t o, int l, int i, Key kv, std::vector<Key>& cands, std::vector<Key>& kept) {
     int64_t r = row(o, l);
     int c = chunkn(r, i);
@@ -527,7 +527,7 @@ struct Builder {
         }
       }
       t_apply += std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
-      // entry points (Algorithm 6, line 11): only the node's own segment
+      // entry points (Algorithm 6): only the node's own segment
       for (int64_t t = 0; t < cntb; ++t) {
         int32_t v = (int32_t)(done + t);
         int i = seg[v];

@@ -41,7 +41,7 @@
  *   R9 Conjunctive predicate on a second attribute (Section 5.9, "multiple
  *      single-attribute indexes"): the index is built on A1; a query adds
  *      lo2 <= A2 <= hi2. Algorithm 7's layer-0 ann test requires both ranges (the
- *      paper's change of its push-to-ann line); by the same reading Strategy A
+ *      paper's change of its push to ann); by the same reading Strategy A
  *      keeps only rows that satisfy both (rows failing A2 are skipped before any
  *      distance) and Strategy B's final filter tests both. Segments, masks and the
  *      router use A1 alone.

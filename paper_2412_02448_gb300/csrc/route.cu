@@ -1,6 +1,6 @@
 // Range resolution, segment mask and range-aware strategy selection
 // (Section 4.2: Strategy A's skip-list descent lands on the first in-range object;
-// Algorithm 7 line 3: the segments that intersect [l, h]; range-aware selection:
+// Algorithm 7: the segments that intersect [l, h]; range-aware selection:
 // A if Y <= tau_A, B if Y >= tau_B, otherwise C).
 //
 // The skip list's bottom layer is the attribute order, so the descent to the first
