@@ -160,8 +160,8 @@ UNIFY_API int unify_search(unify_index_t* idx, const float* q, const int64_t* lo
                  float* out_dist, int32_t* out_count, uint32_t* out_status, int32_t* out_counters,
                  void* stream);
 
-/* unify_search with a conjunctive predicate on a second attribute (Section 5.9,
- * "multiple single-attribute indexes": the index is built on its own attribute A1,
+/* unify_search with a conjunctive predicate on a second attribute (Section 5.9: one
+ * single-attribute index per attribute; the index is built on its own attribute A1,
  * and Algorithm 7's push-to-ann test requires both ranges). Query i returns the
  * nearest objects with lo[i] <= A1 <= hi[i] AND lo2[i] <= attr2[id] <= hi2[i]:
  * Strategy A scans the A1 range and keeps the rows that pass A2; Strategy C's

@@ -38,8 +38,8 @@
  *      k = ef_post on layer 0), then the range filter, then the first k.
  *   R8 A result holds min(k, found) entries sorted by (distance, id); the rest of
  *      the row is padded with id -1 and distance +inf.
- *   R9 Conjunctive predicate on a second attribute (Section 5.9, "multiple
- *      single-attribute indexes"): the index is built on A1; a query adds
+ *   R9 Conjunctive predicate on a second attribute (Section 5.9, one
+ *      single-attribute index per attribute): the index is built on A1; a query adds
  *      lo2 <= A2 <= hi2. Algorithm 7's layer-0 ann test requires both ranges (the
  *      paper's change of its push to ann); by the same reading Strategy A
  *      keeps only rows that satisfy both (rows failing A2 are skipped before any
