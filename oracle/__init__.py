@@ -50,6 +50,8 @@ def _load():
             lib.orc_index_open.restype = ctypes.c_int
             lib.orc_index_close.argtypes = [P]
             lib.orc_index_close.restype = None
+            lib.orc_index_max_level.argtypes = [P]
+            lib.orc_index_max_level.restype = ctypes.c_int
             lib.orc_exact_knn_batch.argtypes = [P, P, ctypes.c_int64, ctypes.c_int, P, P, P,
                                                 ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P, P]
             lib.orc_exact_knn_batch.restype = ctypes.c_int
@@ -61,6 +63,8 @@ def _load():
             lib.orc_search_batch_sel.restype = ctypes.c_int
             lib.orc_search_batch_ex.argtypes = lib.orc_search_batch_sel.argtypes + [P, P, P]
             lib.orc_search_batch_ex.restype = ctypes.c_int
+            lib.orc_search_batch_tr.argtypes = lib.orc_search_batch_ex.argtypes + [P]
+            lib.orc_search_batch_tr.restype = ctypes.c_int
             lib.orc_exact_knn_batch2.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int, P, P, P, P, P,
                                                  ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P, P]
             lib.orc_exact_knn_batch2.restype = ctypes.c_int
@@ -120,6 +124,7 @@ class OracleIndex:
             raise RuntimeError(f"oracle could not open {path}: code {rc}")
         self._h = h
         self.path = path
+        self.max_level = int(self._lib.orc_index_max_level(h))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -130,11 +135,14 @@ class OracleIndex:
         self.close()
 
     def search(self, queries, lo, hi, k, ef=100, m=16, ef_post=None, strategy="auto",
-               tau_a=0, tau_b=0, threads=None, selection=2, attr2=None, lo2=None, hi2=None):
+               tau_a=0, tau_b=0, threads=None, selection=2, attr2=None, lo2=None, hi2=None, trace=False):
         """O2. Returns dict(ids, dist, count, strategy, n_dist, n_exp). selection: 2 = S2
         (first ceil(m/S') slots per intersected chunk), 1 = S1 (the m neighbours nearest
         to the expanded object over all intersected chunks). attr2/lo2/hi2 add the
-        conjunctive predicate lo2 <= attr2 <= hi2 on a second attribute (R9)."""
+        conjunctive predicate lo2 <= attr2 <= hi2 on a second attribute (R9). With
+        ``trace`` the dict also holds ``eps`` [nq, max_level + 1]: the entry point each
+        layer l of the hierarchical descent started from (column l; -1 where no layer
+        was searched)."""
         Q = _c(queries, np.float32)
         lo, hi = _c(lo, np.int64), _c(hi, np.int64)
         nq = lo.shape[0]
@@ -145,11 +153,14 @@ class OracleIndex:
         A2 = _c(attr2, np.int64) if attr2 is not None else None
         l2 = _c(lo2, np.int64) if attr2 is not None else None
         h2 = _c(hi2, np.int64) if attr2 is not None else None
-        rc = self._lib.orc_search_batch_ex(self._h, _p(Q), _p(lo), _p(hi), nq, k, ef, m, ef_post or ef, st,
+        eps = np.empty((nq, self.max_level + 1), np.int32) if trace else None
+        rc = self._lib.orc_search_batch_tr(self._h, _p(Q), _p(lo), _p(hi), nq, k, ef, m, ef_post or ef, st,
                                            tau_a, tau_b, threads or default_threads(), _p(out["ids"]),
                                            _p(out["dist"]), _p(out["count"]), _p(out["strategy"]),
                                            _p(out["n_dist"]), _p(out["n_exp"]), int(selection),
-                                           _p(A2), _p(l2), _p(h2))
+                                           _p(A2), _p(l2), _p(h2), _p(eps))
+        if trace:
+            out["eps"] = eps
         if rc != 0:
             raise RuntimeError(f"orc_search_batch failed: {rc}")
         return out

@@ -188,6 +188,7 @@ void orc_index_close(orc_index* ix) {
 
 int64_t orc_index_n(const orc_index* ix) { return ix->n; }
 int orc_index_d(const orc_index* ix) { return ix->d; }
+int orc_index_max_level(const orc_index* ix) { return ix->max_level; }
 
 /* ------------------------------------------------------- distances, keys */
 
@@ -367,6 +368,7 @@ typedef struct {
   const int64_t* a2;  /* second attribute by id, or NULL (R9) */
   int64_t lo2, hi2;
   int64_t n_dist, n_exp;
+  int32_t* trace;  /* NULL, or max_level + 1 slots: the entry point each layer starts from */
 } scratch_t;
 
 static int sc_init(scratch_t* s, int64_t n) {
@@ -540,9 +542,11 @@ static int64_t strategy_post(const orc_index* ix, const float* q, int64_t lo, in
   if (pb <= pa) return 0; /* no object in range: the filter would leave nothing */
   int32_t ep = ix->entry_global;
   for (int l = ix->max_level; l >= 1; --l) {
+    if (s->trace) s->trace[l] = ep;
     if (alg1_global(ix, q, ep, l, 1, s)) return -1;
     ep = (int32_t)s->ann.a[0].id;
   }
+  if (s->trace) s->trace[0] = ep;
   if (alg1_global(ix, q, ep, 0, ef_post, s)) return -1;
   int64_t c = s->ann.n;
   key_t_* tmp = (key_t_*)malloc((size_t)(c > 0 ? c : 1) * sizeof(key_t_));
@@ -562,9 +566,11 @@ static int64_t strategy_hybrid(const orc_index* ix, const float* q, int64_t lo, 
   if (mask == 0) return 0;
   int32_t ep = ix->entry_global;
   for (int l = ix->max_level; l >= 1; --l) {
+    if (s->trace) s->trace[l] = ep;
     if (alg7(ix, q, ep, l, 1, m, mask, lo, hi, selection, s)) return -1;
     if (s->ann.n > 0) ep = (int32_t)s->ann.a[0].id;
   }
+  if (s->trace) s->trace[0] = ep;
   if (alg7(ix, q, ep, 0, ef, m, mask, lo, hi, selection, s)) return -1;
   int64_t c = s->ann.n;
   key_t_* tmp = (key_t_*)malloc((size_t)(c > 0 ? c : 1) * sizeof(key_t_));
@@ -592,6 +598,7 @@ typedef struct {
   int32_t* out_strategy;
   int64_t* out_ndist;
   int64_t* out_nexp;
+  int32_t* out_eps;
   int64_t next;
   int failed;
   pthread_mutex_t mu;
@@ -622,6 +629,11 @@ static void* search_worker(void* arg) {
     }
     s.n_dist = 0;
     s.n_exp = 0;
+    s.trace = NULL;
+    if (b->out_eps) {
+      s.trace = b->out_eps + i * (int64_t)(ix->max_level + 1);
+      for (int l = 0; l <= ix->max_level; ++l) s.trace[l] = -1;
+    }
     s.a2 = b->a2;
     if (b->a2) {
       s.lo2 = b->lo2[i];
@@ -650,13 +662,17 @@ static void* search_worker(void* arg) {
 }
 
 /* O2 over a batch of queries. strategy: 0 = A, 1 = C, 2 = B, -1 = range-aware (R3);
- * selection: 2 = S2, 1 = S1 (R6) for Strategy C.
+ * selection: 2 = S2, 1 = S1 (R6) for Strategy C. out_eps (NULL, or nq x (max_level + 1))
+ * receives, for Strategies B and C, the entry point each layer l of Algorithm 2's
+ * descent starts from at slot l (slot max_level is the global entry point, slot 0 the
+ * layer-0 entry); -1 for layers that were not searched.
  * Queries are independent; threads only split the batch. */
-int orc_search_batch_ex(const orc_index* ix, const float* Q, const int64_t* lo, const int64_t* hi,
+int orc_search_batch_tr(const orc_index* ix, const float* Q, const int64_t* lo, const int64_t* hi,
                         int64_t nq, int k, int ef, int m, int ef_post, int strategy, int64_t tau_a,
                         int64_t tau_b, int threads, int64_t* out_ids, double* out_dist,
                         int64_t* out_count, int32_t* out_strategy, int64_t* out_ndist, int64_t* out_nexp,
-                        int selection, const int64_t* attr2, const int64_t* lo2, const int64_t* hi2) {
+                        int selection, const int64_t* attr2, const int64_t* lo2, const int64_t* hi2,
+                        int32_t* out_eps) {
   if (!ix || !Q || !lo || !hi || nq < 0 || k < 1 || ef < 1 || m < 1 || ef_post < 1 || !out_ids ||
       !out_dist || !out_count || strategy < -1 || strategy > 2 || (selection != 1 && selection != 2) ||
       (attr2 && (!lo2 || !hi2)))
@@ -668,7 +684,7 @@ int orc_search_batch_ex(const orc_index* ix, const float* Q, const int64_t* lo, 
   b.ef_post = ef_post; b.strategy = strategy; b.tau_a = tau_a; b.tau_b = tau_b; b.selection = selection;
   b.a2 = attr2; b.lo2 = lo2; b.hi2 = hi2;
   b.out_ids = out_ids; b.out_dist = out_dist; b.out_count = out_count;
-  b.out_strategy = out_strategy; b.out_ndist = out_ndist; b.out_nexp = out_nexp;
+  b.out_strategy = out_strategy; b.out_ndist = out_ndist; b.out_nexp = out_nexp; b.out_eps = out_eps;
   pthread_mutex_init(&b.mu, NULL);
   pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)threads);
   if (!th) return ORC_ENOMEM;
@@ -680,6 +696,17 @@ int orc_search_batch_ex(const orc_index* ix, const float* Q, const int64_t* lo, 
   free(th);
   pthread_mutex_destroy(&b.mu);
   return b.failed ? ORC_ENOMEM : ORC_OK;
+}
+
+/* O2 without the descent trace. */
+int orc_search_batch_ex(const orc_index* ix, const float* Q, const int64_t* lo, const int64_t* hi,
+                        int64_t nq, int k, int ef, int m, int ef_post, int strategy, int64_t tau_a,
+                        int64_t tau_b, int threads, int64_t* out_ids, double* out_dist,
+                        int64_t* out_count, int32_t* out_strategy, int64_t* out_ndist, int64_t* out_nexp,
+                        int selection, const int64_t* attr2, const int64_t* lo2, const int64_t* hi2) {
+  return orc_search_batch_tr(ix, Q, lo, hi, nq, k, ef, m, ef_post, strategy, tau_a, tau_b, threads, out_ids,
+                             out_dist, out_count, out_strategy, out_ndist, out_nexp, selection, attr2, lo2, hi2,
+                             NULL);
 }
 
 /* O2 with one attribute and the given selection. */

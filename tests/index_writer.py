@@ -75,3 +75,45 @@ def tiny_index_sections(g: dict) -> dict:
                 sorted_ids=order, skip_next0=nxt, skip_head=np.array([order[0]], np.int32),
                 skip_nextU=np.full(1, -1, np.int32), adj0=np.asarray(g["adj0"], np.int32).reshape(n, S, M),
                 gmask0=gm, adjU=np.full((1, S, M), -1, np.int32), gmaskU=np.zeros((1, W), np.uint32))
+
+
+def layered_index_sections(g: dict) -> dict:
+    """Sections for a multi-layer index described by a golden JSON dict: per-node
+    levels, upper-layer rows given as {v, l, adj, bits}, the global entry point and
+    per-segment entry points. Upper rows are laid out by id, (v, l) at
+    upper_base[v] + l - 1; the level-l skip list links the nodes of level >= l in
+    (attribute, id) order."""
+    sec = tiny_index_sections(g)
+    n, S, M = g["n"], g["S"], g["M"]
+    W = (S * M + 31) // 32
+    level = np.asarray(g["level"], np.int32)
+    L = int(level.max())
+    upper_base = np.full(n, -1, np.int32)
+    rows = 0
+    for v in range(n):
+        if level[v] > 0:
+            upper_base[v] = rows
+            rows += int(level[v])
+    adjU = np.full((max(rows, 1), S, M), -1, np.int32)
+    gmU = np.zeros((max(rows, 1), W), np.uint32)
+    for r in g["upper"]:
+        row = upper_base[r["v"]] + r["l"] - 1
+        adjU[row] = np.asarray(r["adj"], np.int32)
+        for b in r["bits"]:
+            gmU[row, b // 32] |= np.uint32(1 << (b % 32))
+    order = sec["sorted_ids"]
+    head = np.full(L + 1, -1, np.int32)
+    head[0] = order[0]
+    nextU = np.full(max(rows, 1), -1, np.int32)
+    for lv in range(1, L + 1):
+        chain = [int(v) for v in order if level[v] >= lv]
+        head[lv] = chain[0]
+        for a, b in zip(chain[:-1], chain[1:]):
+            nextU[upper_base[a] + lv - 1] = b
+    meta = sec["meta"].copy()
+    meta[4] = L
+    meta[5] = g["entry_global"]
+    meta[6] = rows
+    sec.update(meta=meta, level=level, upper_base=upper_base, skip_head=head, skip_nextU=nextU,
+               adjU=adjU, gmaskU=gmU, entry_seg=np.asarray(g["entry_seg"], np.int32))
+    return sec

@@ -493,3 +493,181 @@ def test_conjunctive_full_second_range_is_single_attribute(c1_index):
                       attr2=a2, lo2=lo2, hi2=hi2)
         for key in ("ids", "dist", "count", "n_dist", "n_exp", "strategy"):
             assert np.array_equal(a[key], b[key]), (st, key)
+
+
+# ---------------------------------------------------------------- hierarchical descent (Algorithm 2)
+
+@pytest.fixture(scope="module")
+def layered(tmp_path_factory):
+    from index_writer import layered_index_sections
+    with open(os.path.join(GOLDEN, "layered_line_graph.json")) as f:
+        g = json.load(f)
+    path = str(tmp_path_factory.mktemp("layered") / "layered.idx")
+    write_index(path, layered_index_sections(g))
+    return g, path
+
+
+def test_golden_layered_graph_search(layered):
+    """Hand-traced searches on a three-layer index: Strategy C's upper layers take
+    'lies in an intersected segment' as ann test and keep their entry point while ann
+    stays empty; Strategy B's upper layers follow bitmap-marked slots only; both
+    descend from the global entry point (Algorithm 2). Ids, distances, expansion and
+    distance counts and the entry point of every layer are the traced ones."""
+    g, path = layered
+    oi = oracle.OracleIndex(path)
+    assert oi.max_level == 2
+    for case in g["cases"]:
+        r = oi.search(np.array([case["q"]], np.float32), [case["lo"]], [case["hi"]], case["k"],
+                      ef=case["ef"], m=case["m"], ef_post=case["ef"], strategy=case["strategy"], trace=True)
+        assert list(r["ids"][0]) == case["expect_ids"], case["name"]
+        for got, exp in zip(r["dist"][0], case["expect_dist"]):
+            if exp is None:
+                assert np.isinf(got), case["name"]
+            else:
+                assert got == exp, case["name"]  # exact: q = 9.5 and integer coordinates
+        assert r["n_exp"][0] == case["expect_n_exp"], case["name"]
+        assert r["n_dist"][0] == case["expect_n_dist"], case["name"]
+        assert list(r["eps"][0]) == case["expect_eps"], case["name"]
+
+
+def test_golden_layered_graph_route(layered):
+    """Range bounds, masks and the skip-list descent through levels 2, 1 and 0 of the
+    same index, against the traced values."""
+    g, path = layered
+    oi = oracle.OracleIndex(path)
+    rc = g["route_cases"]
+    r = oi.route(np.array([c["lo"] for c in rc]), np.array([c["hi"] for c in rc]))
+    for i, c in enumerate(rc):
+        assert int(r["mask"][i]) == c["mask"], c
+        assert int(r["first"][i]) == c["first"], c
+        assert (int(r["pa"][i]), int(r["pb"][i])) == (c["pa"], c["pb"]), c
+
+
+def _upper_row(ix, v, l):
+    return int(ix["upper_base"][v]) + l - 1
+
+
+def _greedy_post_layer(ix, X, q, ep, l):
+    """Algorithm 1 at ann size 1 is the greedy walk: move to the nearest of the current
+    node and its bitmap-marked neighbours on layer l until the current node is the
+    nearest (keys (squared distance, id), FP64)."""
+    S, M = ix["S"], ix["M"]
+    key = lambda v: (float(((X[v] - q) ** 2).sum()), int(v))
+    cur = ep
+    while True:
+        row = _upper_row(ix, cur, l)
+        adj = ix["adjU"][row].reshape(S * M)
+        bits = np.unpackbits(ix["gmaskU"][row].view(np.uint8), bitorder="little")[:S * M].astype(bool)
+        nb = [int(v) for v in adj[bits & (adj >= 0)]]
+        best = min([key(cur)] + [key(v) for v in nb])
+        if best[1] == cur:
+            return cur
+        cur = best[1]
+
+
+def _frontier_hybrid_layer(ix, X, q, ep, l, mask, m, seg_of):
+    """Algorithm 7 at ann size 1 on layer l, written as a best-first search with a
+    threshold: the threshold is the best key seen among objects of intersected
+    segments (none at first); an unseen selected neighbour joins the frontier when no
+    threshold exists yet or its key is below it; the search stops when the frontier's
+    nearest object is above the threshold. Selection S2: the first ceil(m / S') slots
+    of each intersected chunk. Returns the object holding the threshold, or ep."""
+    import heapq
+    S, M = ix["S"], ix["M"]
+    segs = [j for j in range(S) if (mask >> j) & 1]
+    per = min(M, -(-m // len(segs)))
+    key = lambda v: (float(((X[v] - q) ** 2).sum()), int(v))
+    passes = lambda v: (mask >> int(seg_of[v])) & 1
+    best = key(ep) if passes(ep) else None
+    frontier, seen = [key(ep)], {ep}
+    while frontier:
+        o = heapq.heappop(frontier)
+        if best is not None and best < o:
+            break
+        adj = ix["adjU"][_upper_row(ix, o[1], l)]
+        for j in segs:
+            for v in adj[j, :per]:
+                v = int(v)
+                if v < 0:
+                    break
+                if v in seen:
+                    continue
+                seen.add(v)
+                kv = key(v)
+                if best is None or kv < best:
+                    heapq.heappush(frontier, kv)
+                    if passes(v):
+                        best = kv
+    return ep if best is None else best[1]
+
+
+def test_upper_layer_descent_matches_independent_restatement(c1_index):
+    """The entry point of every layer of the oracle's hierarchical descent (Algorithm 2)
+    equals an independent restatement: Strategy B as the greedy walk over bitmap
+    slots, Strategy C as a threshold best-first search whose threshold comes from
+    objects of intersected segments. Both start at the global entry point. The c1
+    ranges cover parts of segments, so the segment test and the exact range test pick
+    different entry points for many queries (checked, so the pin is not vacuous)."""
+    import hsig_build
+    w, path = c1_index
+    ix = hsig_build.read_index(path)
+    L = ix["max_level"]
+    assert L >= 2
+    S = ix["S"]
+    seg_of = np.searchsorted(ix["seg_bounds"][1:S], w.attrs, side="right")
+    X = w.vectors.astype(np.float64)
+    oi = oracle.OracleIndex(path)
+    m = 16
+    sel = np.arange(0, len(w.lo), 2)
+    Q, lo, hi = w.queries[sel], w.lo[sel], w.hi[sel]
+    rc = oi.search(Q, lo, hi, w.k, ef=40, m=m, strategy="hybrid", trace=True)
+    rb = oi.search(Q, lo, hi, w.k, ef=40, ef_post=40, strategy="post", trace=True)
+    masks = oi.route(lo, hi)["mask"]
+    inrange = lambda v, i: lo[i] <= w.attrs[v] <= hi[i]
+    differs = 0
+    for i in range(len(sel)):
+        q = Q[i].astype(np.float64)
+        ep_b = ep_c = ix["entry_global"]
+        for l in range(L, 0, -1):
+            assert rb["eps"][i, l] == ep_b, (i, l)
+            assert rc["eps"][i, l] == ep_c, (i, l)
+            ep_b = _greedy_post_layer(ix, X, q, ep_b, l)
+            nxt = _frontier_hybrid_layer(ix, X, q, ep_c, l, int(masks[i]), m, seg_of)
+            differs += int(nxt != ep_c and not inrange(nxt, i))
+            ep_c = nxt
+        assert rb["eps"][i, 0] == ep_b, i
+        assert rc["eps"][i, 0] == ep_c, i
+    # upper-layer entry points outside [lo, hi] but inside an intersected segment occur
+    assert differs >= 10
+
+
+def test_single_segment_full_range_post_equals_hybrid(c1_index, tmp_path):
+    """With one segment, every chunk slot marked as a global edge and a range holding
+    every object, Strategy C (S2 with m = M: every slot; the ann test always passes on
+    every layer) and Strategy B (every slot is bitmap-marked; the filter keeps all)
+    run the same Algorithm 2 over the same multi-layer graph. Ids, distances, counts,
+    distance and expansion counts and the entry point of every layer must agree."""
+    import hsig_build
+    w, _ = c1_index
+    path = str(tmp_path / "s1.idx")
+    hsig_build.build_index(w.vectors, w.attrs, path, 1, 16, 60, seed=3)
+    ix = hsig_build.read_index(path)
+    assert ix["S"] == 1 and ix["max_level"] >= 2
+    sec = {k: np.array(ix[k]) for k in ix if isinstance(ix[k], np.ndarray)}
+    M, W = ix["M"], ix["W"]
+    for a, g in (("adj0", "gmask0"), ("adjU", "gmaskU")):
+        filled = (sec[a].reshape(sec[a].shape[0], M) >= 0)
+        bits = np.zeros((filled.shape[0], W * 32), bool)
+        bits[:, :M] = filled
+        sec[g] = np.packbits(bits, axis=1, bitorder="little").view(np.uint32).reshape(-1, W)
+    full = str(tmp_path / "s1_full_bitmap.idx")
+    write_index(full, sec)
+    oi = oracle.OracleIndex(full)
+    lo = np.full(len(w.lo), w.attrs.min())
+    hi = np.full(len(w.lo), w.attrs.max())
+    for ef in (1, 10, 64):
+        c = oi.search(w.queries, lo, hi, w.k, ef=ef, m=M, strategy="hybrid", trace=True)
+        b = oi.search(w.queries, lo, hi, w.k, ef=ef, ef_post=ef, strategy="post", trace=True)
+        for key in ("ids", "dist", "count", "n_dist", "n_exp", "eps"):
+            assert np.array_equal(c[key], b[key]), (ef, key)
+    assert np.all(c["eps"][:, ix["max_level"]] == ix["entry_global"])
