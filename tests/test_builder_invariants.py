@@ -89,3 +89,35 @@ def test_builder_is_deterministic(tmp_path):
     hsig_build.build_index(w.vectors, w.attrs, p2, w.S, w.M, 40, seed=3, threads=4)
     with open(p1, "rb") as f1, open(p2, "rb") as f2:
         assert f1.read() == f2.read()
+
+
+def test_inclusiveness_of_contiguous_segment_combinations(tmp_path):
+    """Section 5.4's inclusiveness metric on the c1 shape (eight equal segments):
+    for 1, 2, 4, 6 and 8 contiguous segments, an HNSW is built on those segments'
+    objects alone (the builder with one segment), and the share of its layer-0 edges
+    that the HSIG also holds, within the same segments, is averaged over several
+    placements of the combination. The paper reports above 80 % for every size."""
+    from workloads import make_workload
+    w = make_workload("c1", seed=7)
+    path = str(tmp_path / "hsig.idx")
+    hsig_build.build_index(w.vectors, w.attrs, path, w.S, w.M, w.efc, seed=7)
+    ix = hsig_build.read_index(path)
+    n, S, M = ix["n"], ix["S"], ix["M"]
+    seg = np.searchsorted(ix["seg_bounds"][1:S], w.attrs, side="right")
+    adj = np.asarray(ix["adj0"]).reshape(n, S * M)
+    hsig_edges = {(v, int(u)) for v in range(n) for u in adj[v] if u >= 0}
+    report = {}
+    for c, starts in ((1, (0, 3, 7)), (2, (0, 3, 6)), (4, (0, 4)), (6, (0, 2)), (8, (0,))):
+        vals = []
+        for s0 in starts:
+            members = np.flatnonzero((seg >= s0) & (seg < s0 + c))
+            sub = str(tmp_path / f"hnsw_{c}_{s0}.idx")
+            hsig_build.build_index(w.vectors[members], w.attrs[members], sub, 1, M, w.efc, seed=7)
+            h = hsig_build.read_index(sub)
+            hadj = np.asarray(h["adj0"]).reshape(len(members), M)
+            vv, ss = np.nonzero(hadj >= 0)
+            edges = list(zip(members[vv].tolist(), members[hadj[vv, ss]].tolist()))
+            vals.append(sum(e in hsig_edges for e in edges) / len(edges))
+        report[c] = float(np.mean(vals))
+    print("inclusiveness by contiguous segments:", report)
+    assert all(v > 0.8 for v in report.values()), report
