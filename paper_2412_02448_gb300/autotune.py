@@ -52,8 +52,10 @@ def _time_search(index, q, lo, hi, k, params, reps, torch, strategy="auto"):
 def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=None,
          efs=(16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512), ms_=(16, 24, 32, 48, 64), reps=3, log=None,
          calibrate_tau=True, tau_a_fracs=(0.01, 0.015, 0.02, 0.03, 0.05, 0.08),
-         tau_b_fracs=(0.3, 0.4, 0.5, 0.6, 0.75)):
+         tau_b_fracs=(0.3, 0.4, 0.5, 0.6, 0.75), eval_rows=None):
     """Returns (Params, report). q/lo/hi are device tensors; truth_* and groups numpy.
+    With ``eval_rows`` (indices into the batch) the truth arrays hold the exact answers
+    of those rows only, and recall is measured on them; the whole batch is timed.
 
     1. Beam widths under the router of ``base``: the smallest ef_post meeting the
        target on the B-routed queries of every group; for every selection width m
@@ -72,6 +74,9 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
     base = base or U.Params.defaults()
     report = {"trials": []}
     n = index.n
+    ev = np.arange(len(groups)) if eval_rows is None else np.asarray(eval_rows)
+    groups = np.asarray(groups)
+    g_ev = groups[ev]
 
     def make(extra, ref=None):
         ref = ref if ref is not None else base
@@ -84,7 +89,7 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
 
     def run(p):
         ms, out = _time_search(index, q, lo, hi, k, p, reps, torch)
-        ids = out["ids"].cpu().numpy()
+        ids = out["ids"].cpu().numpy()[ev]
         return ms, recall_rows(ids, truth_ids, truth_count, k)
 
     def note(p, ms, gr, what):
@@ -109,7 +114,7 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
         return best_
 
     def beams(ref):
-        strat = index.route(lo, hi, ref.tau_a, ref.tau_b)["strategy"].cpu().numpy()
+        strat = index.route(lo, hi, ref.tau_a, ref.tau_b)["strategy"].cpu().numpy()[ev]
         chosen = {"ef": ref.ef, "ef_post": ref.ef_post, "m": ref.m}
         selB, selC = strat == U.POST, strat == U.HYBRID
         if selB.any():
@@ -119,7 +124,7 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
                     continue
                 p = make(dict(chosen, ef_post=ef), ref)
                 ms, rec = run(p)
-                gr = group_recall(rec, groups, selB)
+                gr = group_recall(rec, g_ev, selB)
                 note(p, ms, gr, "ef_post")
                 if min(gr.values()) >= target:
                     chosen["ef_post"] = ef
@@ -132,7 +137,7 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
                         continue
                     p = make(dict(chosen, m=m, ef=ef), ref)
                     ms, rec = run(p)
-                    gr = group_recall(rec, groups, selC)
+                    gr = group_recall(rec, g_ev, selC)
                     note(p, ms, gr, "hybrid")
                     if min(gr.values()) >= target:
                         if best_c is None or ms < best_c[2]:
@@ -150,7 +155,7 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
             for fb in tau_b_fracs:
                 p = make({"tau_a": int(fa * n), "tau_b": int(fb * n)}, cur)
                 ms, rec = run(p)
-                gr = group_recall(rec, groups)
+                gr = group_recall(rec, g_ev)
                 note(p, ms, gr, "tau")
                 if min(gr.values()) >= target:
                     passing.append((p, ms))
@@ -175,15 +180,136 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
             ms, rec = run(p)
         except U.UnifyError:
             continue
-        gr = group_recall(rec, groups)
+        gr = group_recall(rec, g_ev)
         note(p, ms, gr, f"shape {extra}")
         if min(gr.values()) >= target:
             passing.append((p, ms, gr))
     best = refine(passing, "shape") if passing else None
     if best is None:
         ms, rec = run(cur)
-        best = (cur, ms, group_recall(rec, groups))
+        best = (cur, ms, group_recall(rec, g_ev))
     report["chosen"] = {f: getattr(best[0], f) for f, _ in U.Params._fields_}
     report["ms"] = best[1]
     report["recall"] = best[2]
     return best[0], report
+
+
+def turning_points(table, n):
+    """The two turning points of Section 4.2's range-aware selection from per-bin
+    costs. ``table`` lists bins in ascending Y, each a dict with ``y_lo``, ``y_hi``
+    (inclusive bounds of the in-range counts it holds) and the cost of each strategy
+    at its smallest beam meeting the recall target, ``ms_pre``, ``ms_hybrid`` and
+    ``ms_post`` (inf when no beam met it).
+
+    tau_A: the last Y of the run of bins, from the smallest ranges up, where
+    pre-filtering costs no more than hybrid filtering (0 when the first bin already
+    prefers hybrid). tau_B: the first Y of the run of bins, from the largest ranges
+    down, where post-filtering costs no more than hybrid filtering (n + 1 when the
+    last bin prefers hybrid). Pre-filtering keeps priority where both runs meet
+    (the router tests A first), so tau_B > tau_A."""
+    tau_a, tau_b = 0, n + 1
+    for row in table:
+        if row["ms_pre"] <= row["ms_hybrid"]:
+            tau_a = int(row["y_hi"])
+        else:
+            break
+    for row in reversed(table):
+        if row["ms_post"] <= row["ms_hybrid"]:
+            tau_b = int(row["y_lo"])
+        else:
+            break
+    return tau_a, max(tau_b, tau_a + 1)
+
+
+def calibrate_tau(index, vectors, attr_domain, k, target=0.95, base=None, n_sample=2048, bins=12,
+                  efs=(10, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512), reps=3, seed=0, log=None):
+    """tau_A and tau_B by the preprocessing of Section 4.2: base objects drawn as
+    queries, each given a random range; every query run with Strategies A, B and C;
+    for each strategy and range size the cost at the smallest beam that meets the
+    recall target; the turning points where pre- and post-filtering overtake hybrid
+    filtering are tau_A and tau_B.
+
+    ``vectors`` is the base set (n x d, host), ``attr_domain`` the (lo, hi) span of
+    the attribute values. Ranges have log-uniform widths between one value and the
+    whole domain at uniform offsets. Queries are grouped into ``bins`` log-spaced
+    bins of their exact in-range count Y; each bin's queries run as one batch per
+    strategy and beam, timed with CUDA events. Recall (Eq. 1) is measured against
+    Strategy A (exact). Returns (tau_a, tau_b, table)."""
+    import torch
+
+    import paper_2412_02448_gb300 as U
+
+    base = base or U.Params.defaults()
+    rng = np.random.default_rng([seed, 77])
+    n = index.n
+    ids = rng.choice(n, size=min(n_sample, n), replace=False)
+    a_lo, a_hi = int(attr_domain[0]), int(attr_domain[1])
+    span = a_hi - a_lo + 1
+    width = np.maximum(1, np.rint(span * 10.0 ** rng.uniform(-np.log10(span), 0.0, size=len(ids)))).astype(np.int64)
+    width = np.minimum(width, span)
+    lo = a_lo + (rng.random(len(ids)) * (span - width + 1)).astype(np.int64)
+    lo = np.minimum(lo, a_hi - width + 1)
+    hi = lo + width - 1
+    dev = index.device
+    q_all = torch.from_numpy(np.ascontiguousarray(vectors[np.sort(ids)], dtype=np.float32)).to(dev)
+    lo_all = torch.from_numpy(lo).to(dev)
+    hi_all = torch.from_numpy(hi).to(dev)
+    rt = index.route(lo_all, hi_all, base.tau_a, base.tau_b)
+    Y = (rt["pb"] - rt["pa"]).cpu().numpy().astype(np.int64)
+    edges = np.unique(np.rint(np.geomspace(1, n + 1, bins + 1)).astype(np.int64))
+    table = []
+
+    def params(**kw):
+        p = U.Params.defaults(**{f: getattr(base, f) for f, _ in U.Params._fields_})
+        for kk, v in kw.items():
+            setattr(p, kk, v)
+        if max(p.ef, p.ef_post) > p.cand_cap // 2:
+            p.cand_cap = min(4096, 2 * max(p.ef, p.ef_post))
+        return p
+
+    for b in range(len(edges) - 1):
+        sel = np.flatnonzero((Y >= edges[b]) & (Y < edges[b + 1]))
+        if len(sel) == 0:
+            continue
+        st = torch.from_numpy(sel).to(dev)
+        q, lo_b, hi_b = q_all[st], lo_all[st], hi_all[st]
+        ms_pre, exact = _time_search(index, q, lo_b, hi_b, k, params(), reps, torch, strategy="pre")
+        t_ids, t_cnt = exact["ids"].cpu().numpy(), exact["count"].cpu().numpy()
+        row = {"y_lo": int(edges[b]), "y_hi": int(edges[b + 1] - 1), "queries": int(len(sel)),
+               "ms_pre": ms_pre}
+        for name, strat, key in (("hybrid", "hybrid", "ef"), ("post", "post", "ef_post")):
+            row["ms_" + name], row["ef_" + name] = float("inf"), None
+            for ef in efs:
+                if ef < k:
+                    continue
+                ms, out = _time_search(index, q, lo_b, hi_b, k, params(**{key: ef}), reps, torch, strategy=strat)
+                rec = recall_rows(out["ids"].cpu().numpy(), t_ids, t_cnt, k).mean()
+                if rec >= target:
+                    row["ms_" + name], row["ef_" + name] = ms, ef
+                    break
+        table.append(row)
+        if log:
+            log(f"calibrate tau: Y in [{row['y_lo']}, {row['y_hi']}] ({row['queries']} queries): pre "
+                f"{row['ms_pre']:.3f} ms, hybrid {row['ms_hybrid']:.3f} ms (ef {row['ef_hybrid']}), post "
+                f"{row['ms_post']:.3f} ms (ef_post {row['ef_post']})")
+    tau_a, tau_b = turning_points(table, n)
+    return tau_a, tau_b, table
+
+
+def calibrated_params(base, tau_a, tau_b, table):
+    """Params routed by (tau_a, tau_b) with the beams the calibration found: ef is the
+    largest hybrid beam any bin between the thresholds needed, ef_post the largest
+    post-filter beam of the bins at or above tau_B (base's beams where none was
+    recorded)."""
+    import paper_2412_02448_gb300 as U
+    p = U.Params.defaults(**{f: getattr(base, f) for f, _ in U.Params._fields_})
+    p.tau_a, p.tau_b = int(tau_a), int(tau_b)
+    efc = [r["ef_hybrid"] for r in table if r["y_hi"] > tau_a and r["y_lo"] < tau_b and r["ef_hybrid"]]
+    efp = [r["ef_post"] for r in table if r["y_hi"] >= tau_b and r["ef_post"]]
+    if efc:
+        p.ef = int(max(efc))
+    if efp:
+        p.ef_post = int(max(efp))
+    if max(p.ef, p.ef_post) > p.cand_cap // 2:
+        p.cand_cap = min(4096, 2 * max(p.ef, p.ef_post))
+    return p

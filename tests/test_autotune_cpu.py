@@ -81,3 +81,31 @@ def test_tuner_picks_the_fastest_passing_configuration(monkeypatch):
     assert min(rep["recall"].values()) >= 0.95
     shapes = [t for t in rep["trials"] if t["what"].startswith("shape")]
     assert len(shapes) >= 13
+
+
+def _table(costs):
+    """Bins [10^i, 10^(i+1) - 1] with (pre, hybrid, post) costs."""
+    return [{"y_lo": 10 ** i, "y_hi": 10 ** (i + 1) - 1, "ms_pre": a, "ms_hybrid": c, "ms_post": b}
+            for i, (a, c, b) in enumerate(costs)]
+
+
+def test_turning_points_from_cost_table():
+    """Section 4.2: tau_A ends the run of small-range bins where pre-filtering costs no
+    more than hybrid filtering; tau_B starts the run of large-range bins where
+    post-filtering costs no more than hybrid filtering."""
+    inf = float("inf")
+    n = 10 ** 6
+    t = _table([(0.1, 0.5, inf), (0.2, 0.5, inf), (0.9, 0.5, 2.0), (5.0, 0.6, 0.9), (40.0, 0.8, 0.7),
+                (90.0, 1.0, 0.6)])
+    assert autotune.turning_points(t, n) == (99, 10 ** 4)
+    # hybrid never loses: tau_A = 0 and tau_B = n + 1 (neither A nor B is routed)
+    t = _table([(0.9, 0.5, inf), (5.0, 0.6, 0.9), (40.0, 0.8, 0.9)])
+    assert autotune.turning_points(t, n) == (0, n + 1)
+    # a dip of pre-filtering after hybrid has won does not move tau_A; a bin where B
+    # loses breaks its run from the top
+    t = _table([(0.1, 0.5, inf), (0.9, 0.5, inf), (0.4, 0.5, 3.0), (5.0, 0.6, 0.5), (40.0, 0.8, 0.9),
+                (90.0, 1.0, 0.6)])
+    assert autotune.turning_points(t, n) == (9, 10 ** 5)
+    # pre-filtering wins everywhere: tau_B stays above tau_A
+    t = _table([(0.1, 0.5, 0.2), (0.2, 0.5, 0.1)])
+    assert autotune.turning_points(t, n) == (99, 100)

@@ -22,6 +22,7 @@ import numpy as np
 __all__ = [
     "Workload", "CONFIGS", "make_workload", "gaussian_iid", "int_mixture",
     "unit_mixture", "nonneg_mixture", "make_ranges", "log_uniform_fractions", "second_attribute",
+    "query_batch",
 ]
 
 
@@ -40,6 +41,7 @@ class Workload:
     efc: int
     seed: int
     params: dict = field(default_factory=dict)
+    centroids: np.ndarray | None = None  # mixture centroids the queries are drawn around
 
     @property
     def n(self) -> int:
@@ -157,18 +159,15 @@ def make_workload(name: str, seed: int = 1234, **overrides) -> Workload:
     rng_r = np.random.default_rng([seed, 3])
 
     kind = cfg["kind"]
+    c = None
     if kind == "gauss":
         x = gaussian_iid(rng_base, n, d)
-        q = gaussian_iid(rng_q, nq, d)
     elif kind == "int_mixture":
         x, c = int_mixture(rng_base, n, d, cfg.get("centroids", 1000), cfg.get("sigma", 20.0))
-        q, _ = int_mixture(rng_q, nq, d, centroids=c, sigma=cfg.get("sigma", 20.0))
     elif kind == "unit_mixture":
         x, c = unit_mixture(rng_base, n, d, cfg.get("centroids", 500))
-        q, _ = unit_mixture(rng_q, nq, d, centroids=c)
     elif kind == "nonneg_mixture":
         x, c = nonneg_mixture(rng_base, n, d, cfg.get("centroids", 1000))
-        q, _ = nonneg_mixture(rng_q, nq, d, centroids=c)
     else:
         raise ValueError(kind)
 
@@ -179,15 +178,41 @@ def make_workload(name: str, seed: int = 1234, **overrides) -> Workload:
         domain = int(cfg.get("domain", n))
         attrs = rng_attr.integers(0, domain, size=n, dtype=np.int64)
 
+    params = {k_: v for k_, v in cfg.items() if k_ not in ("n", "d", "nq")}
+    params["domain"] = domain
+    q, lo, hi, fr = _draw_queries(cfg, c, d, nq, domain, rng_q, rng_r)
+    return Workload(name=name, vectors=np.ascontiguousarray(x, dtype=np.float32),
+                    attrs=attrs, queries=q, lo=lo, hi=hi, fractions=fr, k=int(cfg["k"]), S=int(cfg["S"]),
+                    M=int(cfg["M"]), efc=int(cfg["efc"]), seed=seed, params=params, centroids=c)
+
+
+def _draw_queries(cfg, centroids, d, nq, domain, rng_q, rng_r):
+    """Query vectors (around the base set's centroids, or N(0, 1) for the i.i.d.
+    shape) and their ranges, by the workload's recipe."""
+    kind = cfg["kind"]
+    if kind == "gauss":
+        q = gaussian_iid(rng_q, nq, d)
+    elif kind == "int_mixture":
+        q, _ = int_mixture(rng_q, nq, d, centroids=centroids, sigma=cfg.get("sigma", 20.0))
+    elif kind == "unit_mixture":
+        q, _ = unit_mixture(rng_q, nq, d, centroids=centroids)
+    else:
+        q, _ = nonneg_mixture(rng_q, nq, d, centroids=centroids)
     if cfg["frac"] == "logu":
         fr = log_uniform_fractions(rng_r, nq)
     else:
         fl = np.asarray(cfg["frac"], dtype=np.float64)
         fr = fl[np.arange(nq) % len(fl)]
     lo, hi = make_ranges(rng_r, fr, domain)
-    params = {k_: v for k_, v in cfg.items() if k_ not in ("n", "d", "nq")}
-    params["domain"] = domain
-    return Workload(name=name, vectors=np.ascontiguousarray(x, dtype=np.float32),
-                    attrs=attrs, queries=np.ascontiguousarray(q, dtype=np.float32),
-                    lo=lo, hi=hi, fractions=fr, k=int(cfg["k"]), S=int(cfg["S"]),
-                    M=int(cfg["M"]), efc=int(cfg["efc"]), seed=seed, params=params)
+    return np.ascontiguousarray(q, dtype=np.float32), lo, hi, fr
+
+
+def query_batch(w: Workload, query_seed: int, nq: int | None = None):
+    """Another batch of queries for the base set of ``w``, drawn by the same recipe
+    from an independent stream (``query_seed``): a held-out batch for tuning.
+    Returns (queries, lo, hi, fractions)."""
+    cfg = dict(CONFIGS[w.name])
+    cfg.update({k_: v for k_, v in w.params.items() if k_ in cfg})
+    nq = int(nq if nq is not None else len(w.lo))
+    return _draw_queries(cfg, w.centroids, w.d, nq, int(w.params["domain"]),
+                         np.random.default_rng([query_seed, 2]), np.random.default_rng([query_seed, 3]))
