@@ -200,16 +200,16 @@ def test_device_owned_graph_protocol(tmp_path):
 
 
 def test_build_index_dispatch(monkeypatch, tmp_path):
-    """build_index takes the GPU-assisted builder only when it writes the host file
-    exactly and the assist's limits hold; otherwise the host builder."""
+    """build_index takes the GPU-assisted builder whenever the assist's limits hold
+    (integer or real-valued data), otherwise the host builder."""
     import paper_2412_02448_gb300 as U
     called = []
     monkeypatch.setattr(U, "build_index_gpu", lambda *a, **k: called.append("gpu") or a[2])
     monkeypatch.setattr(hsig_build, "build_index", lambda *a, **k: called.append("host") or a[2])
     ints = np.arange(40, dtype=np.float32).reshape(10, 4)
     attrs = np.arange(10, dtype=np.int64)
-    cases = [(ints, 16, 100, "gpu"), (ints + 0.25, 16, 100, "host"), (ints, 40, 100, "host"),
-             (ints, 16, 300, "host")]
+    cases = [(ints, 16, 100, "gpu"), (ints + 0.25, 16, 100, "gpu"), (ints, 40, 100, "host"),
+             (ints, 16, 300, "host"), (np.zeros((10, 1100), np.float32), 16, 100, "host")]
     for x, M, efc, want in cases:
         called.clear()
         U.build_index(x, attrs, str(tmp_path / "i.idx"), 2, M, efc)

@@ -21,7 +21,30 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 EXACT_BITS = 3  # UNIFY_Q_LIMIT | UNIFY_Q_TRUNCATED
-CAND = 2048     # candidate-buffer entries used by the exactness checks
+CAND = 4096     # candidate-buffer entries used by the exactness checks (the maximum)
+
+
+def _exact_rows(r, o, cap=CAND, floor=0.98, what=""):
+    """Rows to compare bit for bit, after checking that every flag is legitimate.
+
+    The candidate buffer holds visited objects only, so a row can overflow it
+    (UNIFY_Q_TRUNCATED) only when its exact traversal visits more objects than the
+    buffer holds: the oracle's distance count, summed over all layers, is an upper
+    bound. The expansion bound (100,000 per layer, UNIFY_Q_LIMIT) is out of reach at
+    these sizes. Flagged rows are reported with their recall against the oracle's
+    traversal; at least ``floor`` of the rows must be unflagged."""
+    st = r["status"]
+    assert not np.any(st & 1), what  # UNIFY_Q_LIMIT
+    trunc = (st & 2) != 0
+    assert np.all(o["n_dist"][trunc] > cap), (what, np.flatnonzero(trunc & (o["n_dist"] <= cap)))
+    ok = ~trunc
+    if trunc.any():
+        k = r["ids"].shape[1]
+        rec = oracle.recall(r["ids"][trunc], o["ids"][trunc], o["count"][trunc], k)
+        print(f"{what}: {trunc.mean():.3f} of rows truncated; their recall against the oracle's rows "
+              f"{rec.mean():.3f} (min {rec.min():.3f})")
+    assert ok.mean() >= floor, (what, ok.mean())
+    return ok
 
 
 def _valid(w, r, lo, hi):
@@ -123,9 +146,10 @@ def test_graph_strategies_match_oracle(U, c2_small_index, strategy, ef):
     r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=ef, strategy=strategy, counters=True,
                       params=U.Params.defaults(cand_cap=CAND)))
     o = oi.search(w.queries, w.lo, w.hi, w.k, ef=ef, m=16, strategy=strategy)
-    ok = (r["status"] & EXACT_BITS) == 0
     _valid(w, r, w.lo, w.hi)
-    assert ok.mean() > 0.8
+    ok = _exact_rows(r, o, what=f"{strategy} ef={ef}")
+    # every row's exact traversal fits the buffer here, so every row is compared
+    assert np.all(o["n_dist"] <= CAND) and ok.all()
     assert np.array_equal(r["ids"][ok], o["ids"][ok])
     assert np.array_equal(r["count"][ok], o["count"][ok])
     assert np.array_equal(r["counters"][ok, 1], o["n_exp"][ok])
@@ -141,9 +165,9 @@ def test_hybrid_selection_width(U, c2_small_index, m):
     r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=50, strategy="hybrid",
                       params=U.Params.defaults(m=m, cand_cap=CAND), counters=True))
     o = oi.search(w.queries, w.lo, w.hi, w.k, ef=50, m=m, strategy="hybrid")
-    ok = (r["status"] & EXACT_BITS) == 0
     _valid(w, r, w.lo, w.hi)
-    assert ok.mean() > 0.8
+    ok = _exact_rows(r, o, what=f"hybrid m={m}")
+    assert np.all(o["n_dist"] <= CAND) and ok.all()
     assert np.array_equal(r["ids"][ok], o["ids"][ok])
     assert np.array_equal(r["counters"][ok, 1], o["n_exp"][ok])
 
@@ -158,20 +182,33 @@ def test_auto_routing_matches_oracle(U, c2_small_index):
     _valid(w, r, w.lo, w.hi)
     o = oi.search(w.queries, w.lo, w.hi, w.k, ef=80, m=16, strategy="auto", tau_a=ta, tau_b=tb)
     assert set(np.unique(o["strategy"]).tolist()) == {0, 1, 2}
-    ok = (r["status"] & EXACT_BITS) == 0
+    ok = _exact_rows(r, o, what="auto")
+    assert ok.all()
     assert np.array_equal(r["ids"][ok], o["ids"][ok])
+    assert np.array_equal(r["count"], o["count"])
     ex = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, w.k)
     rec = oracle.recall(r["ids"], ex[0], ex[2], w.k)
     assert rec.mean() > 0.9
 
 
-def test_golden_tiny_line_graph_gpu(U, tmp_path):
-    from index_writer import tiny_index_sections, write_index
-    with open(os.path.join(GOLDEN, "tiny_line_graph.json")) as f:
+@pytest.mark.parametrize("name", ["tiny_line_graph", "layered_line_graph"])
+def test_golden_graphs_gpu(U, tmp_path, name):
+    """The hand-traced cases of the one-layer and the three-layer golden indexes
+    through the C ABI: ids, distances and expansion counts as traced (the upper
+    layers' entry points show in the expansion counts); the GPU counts at least the
+    traced distance evaluations (a forgotten visited id is evaluated again). Range
+    bounds and masks of the layered index's route cases as traced."""
+    from index_writer import layered_index_sections, tiny_index_sections, write_index
+    with open(os.path.join(GOLDEN, name + ".json")) as f:
         g = json.load(f)
-    path = str(tmp_path / "tiny.idx")
-    write_index(path, tiny_index_sections(g))
+    path = str(tmp_path / (name + ".idx"))
+    write_index(path, (layered_index_sections if "upper" in g else tiny_index_sections)(g))
     ix = U.Index(path)
+    if "route_cases" in g:
+        rc = g["route_cases"]
+        rt = _np(ix.route(np.array([c["lo"] for c in rc]), np.array([c["hi"] for c in rc])))
+        for i, c in enumerate(rc):
+            assert (int(rt["pa"][i]), int(rt["pb"][i]), int(rt["mask"][i])) == (c["pa"], c["pb"], c["mask"]), c
     for case in g["cases"]:
         p = U.Params.defaults(m=case["m"], ef_post=case["ef"])
         r = _np(ix.search(np.array([case["q"]], np.float32), [case["lo"]], [case["hi"]], case["k"],
@@ -184,7 +221,10 @@ def test_golden_tiny_line_graph_gpu(U, tmp_path):
                 assert got == pytest.approx(exp, rel=1e-5, abs=1e-6)
         if case["strategy"] != "pre":
             assert r["counters"][0, 1] == case["expect_n_exp"], case["name"]
-        assert r["counters"][0, 0] >= case["expect_n_dist"] or case["strategy"] == "pre"
+            # the oracle evaluates each layer's entry point again; the GPU carries its
+            # key down from the layer above (one evaluation fewer per layer below the top)
+            reused = max(g.get("level", [0]))
+            assert r["counters"][0, 0] >= case["expect_n_dist"] - reused, case["name"]
 
 
 def test_edge_cases(U, c2_small_index):
@@ -438,9 +478,9 @@ def test_hybrid_s1_matches_oracle(U, c2_small_index, m):
     p = U.Params.defaults(m=m, cand_cap=CAND, selection=1)
     r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=50, strategy="hybrid", params=p, counters=True))
     o = oi.search(w.queries, w.lo, w.hi, w.k, ef=50, m=m, strategy="hybrid", selection=1)
-    ok = (r["status"] & EXACT_BITS) == 0
     _valid(w, r, w.lo, w.hi)
-    assert ok.mean() > 0.8
+    ok = _exact_rows(r, o, what=f"S1 m={m}")
+    assert np.all(o["n_dist"] <= CAND) and ok.all()
     assert np.array_equal(r["ids"][ok], o["ids"][ok])
     assert np.array_equal(r["count"][ok], o["count"][ok])
     assert np.array_equal(r["counters"][ok, 1], o["n_exp"][ok])
@@ -480,8 +520,8 @@ def test_conjunctive_second_attribute_matches_oracle(U, c2_small_index):
                           attr2=a2, lo2=lo2, hi2=hi2))
         o = oi.search(w.queries, w.lo, w.hi, w.k, ef=64, m=16, strategy=strategy, tau_a=ta, tau_b=tb,
                       attr2=a2, lo2=lo2, hi2=hi2)
-        ok = (r["status"] & EXACT_BITS) == 0
-        assert ok.mean() > 0.8, strategy
+        ok = _exact_rows(r, o, what=f"conjunctive {strategy}")
+        assert np.all(o["n_dist"] <= CAND) and ok.all(), strategy
         for i in np.flatnonzero(ok)[:50]:
             c = int(r["count"][i])
             ids = r["ids"][i, :c]
@@ -541,8 +581,9 @@ def test_c4_precision_shape_k10_k100(U, c4_small_index):
     n = 20,000, auto-routed, at k = 10 and k = 100: BF16 and FP8 E4M3 storage with the
     FP32 re-rank of 4k candidates. Every returned distance is the float32 direct
     distance of its id (within 1e-5 of FP64); per range fraction, recall against the
-    exact answer loses at most 0.03 (BF16) and 0.06 (FP8) against FP32 storage at the
-    same parameters, and the rows routed to the pre-filter scan stay near exact."""
+    exact answer is at least 0.95 with FP32 storage and loses at most 0.03 (BF16) and
+    0.06 (FP8) against it at the same parameters, and the rows routed to the
+    pre-filter scan stay near exact."""
     w, path = c4_small_index
     ix = U.Index(path)
     X = w.vectors.astype(np.float64)
@@ -570,7 +611,7 @@ def test_c4_precision_shape_k10_k100(U, c4_small_index):
         report[k] = rec
         for f in fr:
             f = float(f)
-            assert rec[U.FP32][f] >= 0.85, (k, f, rec)
+            assert rec[U.FP32][f] >= 0.95, (k, f, rec)  # the recall@k target of every range fraction
             assert rec[U.BF16][f] >= rec[U.FP32][f] - 0.03, (k, f, rec)
             assert rec[U.FP8E4M3][f] >= rec[U.FP32][f] - 0.06, (k, f, rec)
         assert rec[U.BF16]["pre"] >= 0.98 and rec[U.FP8E4M3]["pre"] >= 0.95, (k, rec)
