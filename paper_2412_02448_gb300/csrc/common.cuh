@@ -168,12 +168,14 @@ __device__ __forceinline__ float warp_transpose_reduce(float (&v)[V]) {
 // are the same and only the load width differs (16, 8 or 4 bytes per chunk).
 struct StoreF32 {
   static constexpr int kChunkBytes = 16;
+  static constexpr bool kScaled = false;
   __device__ static __forceinline__ float4 load(const unsigned char* row, int c, float) {
     return __ldg(reinterpret_cast<const float4*>(row) + c);
   }
 };
 struct StoreBF16 {  // bfloat16, converted from float32 with round-to-nearest-even
   static constexpr int kChunkBytes = 8;
+  static constexpr bool kScaled = false;
   __device__ static __forceinline__ float4 load(const unsigned char* row, int c, float) {
     const uint2 u = __ldg(reinterpret_cast<const uint2*>(row) + c);
     // a bfloat16 is the upper half of a float32
@@ -181,17 +183,40 @@ struct StoreBF16 {  // bfloat16, converted from float32 with round-to-nearest-ev
                        __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
   }
 };
-struct StoreFP8 {  // E4M3 codes of x / s with s = max|x| / 448 per vector
+// E4M3 codes of x / s with s = max|x| / 448 per vector. load() returns the decoded
+// codes without the scale: the distance loops apply s inside their first FMA
+// (q - s x as one fused operation, see diff4), so the scale costs no multiply.
+struct StoreFP8 {
   static constexpr int kChunkBytes = 4;
-  __device__ static __forceinline__ float4 load(const unsigned char* row, int c, float scale) {
+  static constexpr bool kScaled = true;
+  __device__ static __forceinline__ float4 load(const unsigned char* row, int c, float) {
     const uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(row) + c);
     const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xffffu), __NV_E4M3);
     const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3);
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
-    return make_float4(a.x * scale, a.y * scale, b.x * scale, b.y * scale);
+    return make_float4(a.x, a.y, b.x, b.y);
   }
 };
+
+// q - x for a chunk loaded by T::load: for scaled formats x holds codes and the
+// difference is q - scale * code, fused.
+template <class T>
+__device__ __forceinline__ float4 diff4(const float4& q, const float4& x, float scale) {
+  if constexpr (T::kScaled) {
+    return make_float4(fmaf(-scale, x.x, q.x), fmaf(-scale, x.y, q.y), fmaf(-scale, x.z, q.z),
+                       fmaf(-scale, x.w, q.w));
+  } else {
+    return make_float4(q.x - x.x, q.y - x.y, q.z - x.z, q.w - x.w);
+  }
+}
+
+// The value of a chunk loaded by T::load (the scale applied for scaled formats).
+template <class T>
+__device__ __forceinline__ float4 value4(const float4& x, float scale) {
+  if constexpr (T::kScaled) return make_float4(scale * x.x, scale * x.y, scale * x.z, scale * x.w);
+  else return x;
+}
 
 // Squared-L2 partial of one lane over its chunks of a row in storage format T.
 template <class T, int CH>
@@ -203,12 +228,11 @@ __device__ __forceinline__ float l2_partial_t(const float4 (&q)[CH], const unsig
   for (int t = 0; t < CH; ++t) {
     int c = lane + 32 * t;
     if (c < nchunks) {
-      float4 x = T::load(row, c, scale);
-      float a = q[t].x - x.x, b = q[t].y - x.y, e = q[t].z - x.z, f = q[t].w - x.w;
-      s = fmaf(a, a, s);
-      s = fmaf(b, b, s);
-      s = fmaf(e, e, s);
-      s = fmaf(f, f, s);
+      const float4 e = diff4<T>(q[t], T::load(row, c, scale), scale);
+      s = fmaf(e.x, e.x, s);
+      s = fmaf(e.y, e.y, s);
+      s = fmaf(e.z, e.z, s);
+      s = fmaf(e.w, e.w, s);
     }
   }
   return s;

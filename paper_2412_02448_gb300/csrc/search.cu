@@ -219,7 +219,7 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
 #pragma unroll
         for (int t = 0; t < CH; ++t) {
           const int c = lane + 32 * t;
-          xo[t] = c < a.dp4 ? T::load(orow, c, sc) : make_float4(0.f, 0.f, 0.f, 0.f);
+          xo[t] = c < a.dp4 ? value4<T>(T::load(orow, c, sc), sc) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
       uint64_t* selk = reinterpret_cast<uint64_t*>(w.slots);
@@ -517,15 +517,16 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
 #pragma unroll
     for (int h = 0; h < 32; h += RB) {
       float4 x[RB][CH];
+      float sc[RB];
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
         const int row = min(base + h + r, r1 - 1);
         const unsigned char* src = a.vts + (int64_t)row * a.row_bytes;
-        const float sc = a.scale_sorted ? __ldg(a.scale_sorted + row) : 1.f;
+        sc[r] = a.scale_sorted ? __ldg(a.scale_sorted + row) : 1.f;
 #pragma unroll
         for (int t = 0; t < CH; ++t) {
           const int c = lane + 32 * t;
-          x[r][t] = c < a.dp4 ? T::load(src, c, sc) : make_float4(0.f, 0.f, 0.f, 0.f);
+          x[r][t] = c < a.dp4 ? T::load(src, c, sc[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
 #pragma unroll
@@ -533,12 +534,11 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
         float s = 0.f;
 #pragma unroll
         for (int t = 0; t < CH; ++t) {
-          const float e0 = q[t].x - x[r][t].x, e1 = q[t].y - x[r][t].y;
-          const float e2 = q[t].z - x[r][t].z, e3 = q[t].w - x[r][t].w;
-          s = fmaf(e0, e0, s);
-          s = fmaf(e1, e1, s);
-          s = fmaf(e2, e2, s);
-          s = fmaf(e3, e3, s);
+          const float4 e = diff4<T>(q[t], x[r][t], sc[r]);
+          s = fmaf(e.x, e.x, s);
+          s = fmaf(e.y, e.y, s);
+          s = fmaf(e.z, e.z, s);
+          s = fmaf(e.w, e.w, s);
         }
         part[h + r] = s;
       }

@@ -42,14 +42,15 @@ __device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, cons
       ids[u] = clist[c < nv ? c : nv - 1];
     }
     float4 x[G][CH];
+    float sc[G];
 #pragma unroll
     for (int u = 0; u < G; ++u) {
       const unsigned char* row = rows + (int64_t)ids[u] * row_bytes;
-      const float sc = scale ? __ldg(scale + ids[u]) : 1.f;
+      sc[u] = scale ? __ldg(scale + ids[u]) : 1.f;
 #pragma unroll
       for (int t = 0; t < CH; ++t) {
         const int c = lane + 32 * t;
-        x[u][t] = c < dp4 ? T::load(row, c, sc) : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[u][t] = c < dp4 ? T::load(row, c, sc[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     float part[G];
@@ -58,12 +59,12 @@ __device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, cons
       float s = 0.f;
 #pragma unroll
       for (int t = 0; t < CH; ++t) {
-        const float e0 = q[t].x - x[u][t].x, e1 = q[t].y - x[u][t].y;
-        const float e2 = q[t].z - x[u][t].z, e3 = q[t].w - x[u][t].w;
-        s = fmaf(e0, e0, s);
-        s = fmaf(e1, e1, s);
-        s = fmaf(e2, e2, s);
-        s = fmaf(e3, e3, s);
+        // chunks past the row are zero in q and x alike, so their difference is zero
+        const float4 e = diff4<T>(q[t], x[u][t], sc[u]);
+        s = fmaf(e.x, e.x, s);
+        s = fmaf(e.y, e.y, s);
+        s = fmaf(e.z, e.z, s);
+        s = fmaf(e.w, e.w, s);
       }
       part[u] = (g * G + u < nv) ? s : 0.f;
     }
