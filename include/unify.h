@@ -74,7 +74,8 @@ typedef enum {
 #define UNIFY_E_LIMIT (-6)   /* a size exceeds a compiled limit (message says which) */
 
 /* Per-query status bits written to out_status. */
-#define UNIFY_Q_LIMIT 1u      /* the expansion bound (max_expansions) stopped a layer */
+#define UNIFY_Q_LIMIT 1u      /* the expansion bound (max_expansions) stopped a layer, or a
+                                 wait of the tensor-core scan ran out (empty row) */
 #define UNIFY_Q_TRUNCATED 2u  /* the candidate buffer overflowed and dropped its worst
                                  entries; the result is valid but may differ from the
                                  unbounded algorithm */
@@ -102,7 +103,11 @@ typedef struct {
                           tensor cores (tcgen05 MMA over TMA-staged row tiles shared by 128
                           queries, top rerank_mult * k by bf16 distance, FP32 re-rank) when
                           d is a multiple of 8, d <= 1024 and rerank_mult * k <= 64;
-                          0 (default): warp scan */
+                          0 (default): warp scan. 2: test of the scan's failure path only:
+                          the scan's collecting pass waits on a barrier that nothing arrives
+                          at, every wait between its roles is limited to 50 ms, the waits run
+                          out, and the pre-filter rows come back empty with UNIFY_Q_LIMIT
+                          (the call itself succeeds; the next search is unaffected) */
   int selection;       /* hybrid neighbour selection (Section 4.2; Section 5.6 compares the two):
                           2 (default) = S2, the first ceil(m / S') slots of every intersected
                           chunk; 1 = S1, the m neighbours nearest to the expanded object among

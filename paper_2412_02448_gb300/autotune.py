@@ -99,19 +99,21 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
             log(f"tune {what} ef={p.ef} ef_post={p.ef_post} m={p.m} tau=({p.tau_a},{p.tau_b}): "
                 f"{ms:.3f} ms/batch, recall {gr}")
 
-    def refine(cands, what):
+    def refine(cands, what, tie=0.01):
         """The fastest of cands (tuples led by Params and ms) after re-timing the three
         fastest with four times the repetitions: single short timings of a ~2 ms batch
-        vary by a few percent, enough to pick a slower configuration."""
+        vary by a few percent, enough to pick a slower configuration. Candidates within
+        ``tie`` (relative) of the fastest count as equal, and the one listed first in
+        ``cands`` wins, so that repeated runs settle on the same configuration."""
         top = sorted(cands, key=lambda c: c[1])[:3]
-        best_ = None
+        timed = []
         for c in top:
             ms, _ = _time_search(index, q, lo, hi, k, c[0], 4 * reps, torch)
             if log:
                 log(f"tune re-time {what}: {c[1]:.3f} -> {ms:.3f} ms/batch")
-            if best_ is None or ms < best_[1]:
-                best_ = (c[0], ms) + tuple(c[2:])
-        return best_
+            timed.append((cands.index(c), (c[0], ms) + tuple(c[2:])))
+        fastest = min(t[1][1] for t in timed)
+        return min((t for t in timed if t[1][1] <= fastest * (1 + tie)), key=lambda t: t[0])[1]
 
     def beams(ref):
         strat = index.route(lo, hi, ref.tau_a, ref.tau_b)["strategy"].cpu().numpy()[ev]

@@ -189,6 +189,7 @@ int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Para
   if (p.ef < 1 || p.ef > 2048 || p.ef_post < 1 || p.ef_post > 2048) return fail(UNIFY_E_ARG, "ef and ef_post must be in [1, 2048]");
   if (p.m < 1 || p.m > 1024) return fail(UNIFY_E_ARG, "m must be in [1, 1024]");
   if (p.selection != 1 && p.selection != 2) return fail(UNIFY_E_ARG, "selection must be 1 (S1) or 2 (S2)");
+  if (p.tc_scan < 0 || p.tc_scan > 2) return fail(UNIFY_E_ARG, "tc_scan must be 0, 1 or 2");
   if (p.selection == 1 && p.m > 64) return fail(UNIFY_E_ARG, "selection S1 takes m <= 64");
   if (p.cand_cap < 32 || p.cand_cap > kMaxCand) return fail(UNIFY_E_ARG, "cand_cap must be in [32, 4096]");
   if (d.visited_cap < 64 || d.visited_cap > 65536 || (d.visited_cap & (d.visited_cap - 1)))

@@ -72,12 +72,14 @@ constexpr int kStageA = kTcQ * kTcKc * 2;     // 16 KB of queries
 constexpr int kStageB = kTcRows * kTcKc * 2;  // 32 KB of rows
 constexpr long long kWaitLimit = 1ll << 22;   // polls
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s of elapsed time
+constexpr uint64_t kTestWaitNs = 50000000ull;  // 50 ms: the limit of the timeout test
 
 struct TcSmem {
   // 1024-byte aligned stages first
   uint8_t a[kTcStages][kStageA];
   uint8_t b[kTcStages][kStageB];
   uint64_t full[kTcStages], empty[kTcStages], accf[2], acce[2], drain;
+  uint64_t never;  // no thread arrives on it (the timeout test waits on it)
   uint64_t ufull[kUnitRing], uempty[kUnitRing];
   int uring[kUnitRing];  // claimed unit (-1: no more units)
   uint32_t tmem;
@@ -118,8 +120,8 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Waits for the completion of the phase with the given parity; false on timeout.
 // A few immediate polls, then polls with a growing sleep in between, bounded
-// both by the number of polls and by kWaitNs of elapsed time.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// both by the number of polls and by limit_ns of elapsed time.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   const uint32_t addr = smem_u32(bar);
 #pragma unroll 1
   for (int i = 0; i < 16; ++i)
@@ -131,7 +133,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (mbar_try(addr, parity)) return true;
     __nanosleep(ns);
     if (ns < 512) ns <<= 1;
-    if ((i & 63) == 63 && global_ns() - t0 > kWaitNs) return false;
+    if ((i & 63) == 63 && global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -233,6 +235,8 @@ struct TcArgs {
   unsigned long long* qthr;  // per query (bucketed order): smallest key known to have R keys at or below it
   int32_t* counters;
   int k, R;
+  uint64_t wait_ns;  // elapsed-time limit of every wait on another role
+  int stall;         // timeout test: the collecting epilogue waits on a barrier nobody arrives at
   Outputs o;
 };
 
@@ -282,6 +286,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       mbar_init(&s.acce[i], 4 * 32);
     }
     mbar_init(&s.drain, 1);
+    mbar_init(&s.never, 1);
     for (int i = 0; i < kUnitRing; ++i) {
       mbar_init(&s.ufull[i], 1);
       mbar_init(&s.uempty[i], 1 + 4 * 32);  // the MMA issuer and the 128 epilogue threads
@@ -308,7 +313,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         // claim the next unit and hand it to the other roles
         const int us = (int)(useq % kUnitRing);
         const long long uu = useq / kUnitRing;
-        if (uu > 0 && !mbar_wait(&s.uempty[us], (uint32_t)((uu - 1) & 1))) {
+        if (uu > 0 && !mbar_wait(&s.uempty[us], (uint32_t)((uu - 1) & 1), a.wait_ns)) {
           ok = false;
           break;
         }
@@ -324,7 +329,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
           for (int kc = 0; kc < a.KC; ++kc, ++it) {
             const int st = (int)(it % kTcStages);
             const long long u = it / kTcStages;
-            if (u > 0 && !mbar_wait(&s.empty[st], (uint32_t)((u - 1) & 1))) {
+            if (u > 0 && !mbar_wait(&s.empty[st], (uint32_t)((u - 1) & 1), a.wait_ns)) {
               ok = false;
               break;
             }
@@ -338,7 +343,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       for (int st = 0; st < kTcStages; ++st) {
         if (it <= st) continue;
         const long long last_use = (it - 1 - st) / kTcStages;
-        if (!mbar_wait(&s.full[st], (uint32_t)(last_use & 1))) ok = false;
+        if (!mbar_wait(&s.full[st], (uint32_t)(last_use & 1), kWaitNs)) ok = false;
       }
       if (!ok) atomicExch(err, 1);
     }
@@ -351,7 +356,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       long long it = 0, g = 0;
       for (long long useq = 0; ok; ++useq) {
         const int us = (int)(useq % kUnitRing);
-        if (!mbar_wait(&s.ufull[us], (uint32_t)((useq / kUnitRing) & 1))) {
+        if (!mbar_wait(&s.ufull[us], (uint32_t)((useq / kUnitRing) & 1), a.wait_ns)) {
           ok = false;
           break;
         }
@@ -364,7 +369,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         for (int row0 = r0; row0 < r1 && ok; row0 += kTcRows, ++g) {
           const int ab = (int)(g & 1);
           const long long ua = g >> 1;
-          if (ua > 0 && !mbar_wait(&s.acce[ab], (uint32_t)((ua - 1) & 1))) {
+          if (ua > 0 && !mbar_wait(&s.acce[ab], (uint32_t)((ua - 1) & 1), a.wait_ns)) {
             ok = false;
             break;
           }
@@ -372,7 +377,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
           const uint32_t d_tmem = tmem + (uint32_t)(ab * kTcRows);
           for (int kc = 0; kc < a.KC; ++kc, ++it) {
             const int st = (int)(it % kTcStages);
-            if (!mbar_wait(&s.full[st], (uint32_t)((it / kTcStages) & 1))) {
+            if (!mbar_wait(&s.full[st], (uint32_t)((it / kTcStages) & 1), a.wait_ns)) {
               ok = false;
               break;
             }
@@ -390,7 +395,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       }
       // every product issued has completed before tensor memory is released
       umma_commit(&s.drain);
-      if (!mbar_wait(&s.drain, 0)) ok = false;
+      if (!mbar_wait(&s.drain, 0, kWaitNs)) ok = false;
       if (!ok) atomicExch(err, 1);
     }
     __syncwarp();
@@ -401,7 +406,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
     long long g = 0;
     for (long long useq = 0; !failed; ++useq) {
       const int us = (int)(useq % kUnitRing);
-      if (!__all_sync(kFull, mbar_wait(&s.ufull[us], (uint32_t)((useq / kUnitRing) & 1)))) {
+      if (!__all_sync(kFull, mbar_wait(&s.ufull[us], (uint32_t)((useq / kUnitRing) & 1), a.wait_ns))) {
         failed = true;
         break;
       }
@@ -436,7 +441,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
           x0n = row < a.n ? __ldg(a.xn + row) : 0.f;
           x1n = row + 32 < a.n ? __ldg(a.xn + row + 32) : 0.f;
         }
-        if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1)))) {
+        if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1), a.wait_ns))) {
           failed = true;
           break;
         }
@@ -497,9 +502,12 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
     const int tq = threadIdx.x;
     bool failed = false;
     long long g = 0;
+    // timeout test: this wait runs out after wait_ns; the producer's and the MMA
+    // issuer's waits on the epilogue then run out in turn, and both drain
+    if (a.stall && !__all_sync(kFull, mbar_wait(&s.never, 0, a.wait_ns))) failed = true;
     for (long long useq = 0; !failed; ++useq) {
       const int us = (int)(useq % kUnitRing);
-      if (!__all_sync(kFull, mbar_wait(&s.ufull[us], (uint32_t)((useq / kUnitRing) & 1)))) {
+      if (!__all_sync(kFull, mbar_wait(&s.ufull[us], (uint32_t)((useq / kUnitRing) & 1), a.wait_ns))) {
         failed = true;
         break;
       }
@@ -536,7 +544,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
           xnext = row < a.n ? __ldg(a.xn + row) : 0.f;
           inext = row < a.n ? __ldg(a.sorted_ids + row) : 0;
         }
-        if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1)))) {
+        if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1), a.wait_ns))) {
           failed = true;
           break;
         }
@@ -876,6 +884,8 @@ cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float*
   a.counters = sc.counters;
   a.k = p.k;
   a.R = rerank_count(p);
+  a.stall = p.tc_scan == 2 ? 1 : 0;
+  a.wait_ns = p.tc_scan == 2 ? kTestWaitNs : kWaitNs;
   a.o = o;
   tc_tile_prep<<<ix.num_sms, 256, 0, st>>>(a);
   tc_unit_plan<<<1, 1024, 0, st>>>(a);

@@ -1,8 +1,9 @@
 """The autotuner's selection logic on the CPU, against a fake index whose recall and
 batch time follow a fixed model (the timing function is replaced; no GPU work):
 beam widths are the smallest meeting the target per strategy, the (tau_A, tau_B)
-pair and the launch shape are the fastest meeting it, and a configuration that only
-looks fastest in a short timing loses once the leaders are re-timed."""
+pair and the launch shape are the fastest meeting it, a configuration that only
+looks fastest in a short timing loses once the leaders are re-timed, and leaders
+within 1 % of each other resolve to the one listed first."""
 import numpy as np
 import pytest
 
@@ -38,8 +39,9 @@ def _ids(p):
 
 def _true_ms(p):
     ms = 2.0 + 0.002 * p.ef + 0.001 * p.ef_post + 0.004 * p.m
-    # routing: fastest at tau_A = 2 % and tau_B = 30 % of n
-    ms += abs(p.tau_a - 0.02 * N) / N + abs(p.tau_b - 0.3 * N) / N
+    # routing: fastest at tau_A = 2 % and tau_B = 30 % of n (the neighbouring pairs are
+    # a few percent slower, above the tuner's 1 % tie margin)
+    ms += 10 * (abs(p.tau_a - 0.02 * N) + abs(p.tau_b - 0.3 * N)) / N
     if p.visited_cap == 1024 and p.reg_budget == 128:
         ms -= 0.2
     if p.cand_cap == 256 and p.reg_budget == 128 and p.visited_cap == 2048:
@@ -109,3 +111,28 @@ def test_turning_points_from_cost_table():
     # pre-filtering wins everywhere: tau_B stays above tau_A
     t = _table([(0.1, 0.5, 0.2), (0.2, 0.5, 0.1)])
     assert autotune.turning_points(t, n) == (99, 100)
+
+
+def test_tuner_breaks_near_ties_by_listing_order(monkeypatch):
+    """Shapes within 1 % of the fastest count as equal; the earliest listed wins, so
+    repeated runs do not flip between near-equal configurations."""
+    def near_tie(index, q, lo, hi, k, params, reps, torch_, strategy="auto"):
+        ms = 3.0
+        if params.cand_cap == 1024:
+            ms = 2.0      # listed before visited_cap 1024 among the shapes
+        if params.visited_cap == 1024 and params.reg_budget == 128:
+            ms = 1.99     # 0.5 % faster: a tie
+        if params.scan_rows == 2048:
+            ms = 1.95     # 2.5 % faster: a real win
+        return ms, {"ids": torch.from_numpy(np.tile(np.arange(K, dtype=np.int64), (NQ, 1)))}
+    monkeypatch.setattr(autotune, "_time_search", near_tie)
+    truth = np.tile(np.arange(K, dtype=np.int64), (NQ, 1))
+    p, _ = autotune.tune(FakeIndex(), None, None, None, K, truth, np.full(NQ, K), GROUPS, target=0.95,
+                         efs=(16,), ms_=(16,), reps=3, calibrate_tau=False)
+    assert p.scan_rows == 2048
+    monkeypatch.setattr(autotune, "_time_search",
+                        lambda *a, **k: (near_tie(*a, **k)[0] + (1.0 if a[5].scan_rows == 2048 else 0.0),
+                                         near_tie(*a, **k)[1]))
+    p, _ = autotune.tune(FakeIndex(), None, None, None, K, truth, np.full(NQ, K), GROUPS, target=0.95,
+                         efs=(16,), ms_=(16,), reps=3, calibrate_tau=False)
+    assert p.cand_cap == 1024 and p.visited_cap == 2048

@@ -441,6 +441,36 @@ def test_tensor_core_scan_matches_warp_scan(U, c2_small_index):
         assert np.array_equal(r0[key], r1[key]), key
 
 
+def test_tensor_core_scan_wait_timeout_recovers(U, c2_small_index):
+    """The tensor-core scan's failure path, without a GPU fault: with tc_scan = 2 the
+    collecting pass waits on a barrier that nothing arrives at, under a 50 ms limit.
+    The wait runs out, the other roles' waits run out in turn and drain, and the call
+    returns normally with every pre-filter row empty and flagged UNIFY_Q_LIMIT, while
+    the graph-routed rows of the same batch are searched as usual. The next search on
+    the same index returns the warp scan's rows again."""
+    w, path = c2_small_index
+    ix = U.Index(path)
+    ta, tb = w.n // 100, w.n // 2
+    ref = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy="auto",
+                        params=U.Params.defaults(dtype=U.BF16, rerank_mult=4, tau_a=ta, tau_b=tb, cand_cap=CAND)))
+    pre = oracle.OracleIndex(path).route(w.lo, w.hi, ta, tb)["strategy"] == 0
+    assert 0 < pre.sum() < len(pre)
+    bad = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy="auto",
+                        params=U.Params.defaults(dtype=U.BF16, rerank_mult=4, tau_a=ta, tau_b=tb, cand_cap=CAND,
+                                                 tc_scan=2)))
+    assert np.all((bad["status"][pre] & U.Q_LIMIT) != 0)
+    assert np.all(bad["count"][pre] == 0) and np.all(bad["ids"][pre] == -1)
+    for key in ("ids", "dist", "count", "status"):
+        assert np.array_equal(bad[key][~pre], ref[key][~pre]), key
+    again = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy="auto",
+                          params=U.Params.defaults(dtype=U.BF16, rerank_mult=4, tau_a=ta, tau_b=tb, cand_cap=CAND,
+                                                   tc_scan=1)))
+    for key in ("ids", "dist", "count", "status"):
+        assert np.array_equal(again[key], ref[key]), key
+    with pytest.raises(U.UnifyError):
+        ix.search(w.queries[:4], w.lo[:4], w.hi[:4], w.k, params=U.Params.defaults(tc_scan=3))
+
+
 def test_tensor_core_scan_wide_rows(U, c5_small_index):
     """d = 960 (15 K-slices per block) on real data: the bf16 candidates are chosen
     by the expanded distance form, so rows may differ from the exact scan only by
