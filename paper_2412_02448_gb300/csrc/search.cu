@@ -379,7 +379,7 @@ __device__ int rerank_write(const BatchArgs& a, const WarpMem& w, const float4 (
   return nt;
 }
 
-template <class T, int CH, int G>
+template <class T, int CH, int G, int GF>
 __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool hybrid) {
   const int lane = lane_id();
   int t_start = 0;
@@ -449,7 +449,7 @@ __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool h
         src = w.E;
       }
       if (nc > a.rerank) nc = a.rerank;
-      cnt = rerank_write<CH, G>(a, w, q, src, nc, qi, hybrid ? w.E : w.ann);
+      cnt = rerank_write<CH, GF>(a, w, q, src, nc, qi, hybrid ? w.E : w.ann);
     } else if (hybrid) {
       cnt = nA < a.k ? nA : a.k;
       write_row(w.ann, cnt, a.k, qi, a.o);
@@ -494,7 +494,7 @@ __device__ void graph_query(const BatchArgs& a, const WarpMem& w, int qi, bool h
   __syncwarp();
 }
 
-template <class T, int CH, int G>
+template <class T, int CH, int G, int GF>
 __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
   const int lane = lane_id();
   uint64_t* topk = w.ann;  // ann_cap >= kk
@@ -510,13 +510,16 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
   const int64_t l2 = a.cj.attr2 ? a.cj.lo2[qi] : 0, h2 = a.cj.attr2 ? a.cj.hi2[qi] : 0;
   float4 q[CH];
   load_query<CH>(q, a.q + (int64_t)qi * a.d, a.d);
-  constexpr int RB = (16 / CH) > 2 ? (16 / CH) : 2;  // rows per load batch
+  // rows per load batch: all 32 rows of a step where raw narrow chunks are held and
+  // rows have at most 128 elements (bfloat16: 64 registers), otherwise 16 / CH (64
+  // registers of float32 chunks)
+  constexpr int RB = (CH == 1 && T::kRawRegs < 4 && T::kHoldRaw) ? 32 : ((16 / CH) > 2 ? (16 / CH) : 2);
   int nt = 0;
   for (int base = r0; base < r1; base += 32) {
     float part[32];
 #pragma unroll
     for (int h = 0; h < 32; h += RB) {
-      float4 x[RB][CH];
+      Held<T> x[RB][CH];
       float sc[RB];
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
@@ -526,7 +529,7 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
 #pragma unroll
         for (int t = 0; t < CH; ++t) {
           const int c = lane + 32 * t;
-          x[r][t] = c < a.dp4 ? T::load(src, c, sc[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
+          x[r][t] = hold<T>(c < a.dp4 ? T::load_raw(src, c) : T::zero_raw());
         }
       }
 #pragma unroll
@@ -534,7 +537,7 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
         float s = 0.f;
 #pragma unroll
         for (int t = 0; t < CH; ++t) {
-          const float4 e = diff4<T>(q[t], x[r][t], sc[r]);
+          const float4 e = diff4<T>(q[t], unhold<T>(x[r][t]), sc[r]);
           s = fmaf(e.x, e.x, s);
           s = fmaf(e.y, e.y, s);
           s = fmaf(e.z, e.z, s);
@@ -579,7 +582,7 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
   }
   int cnt;
   if (a.rerank > 0) {
-    cnt = rerank_write<CH, G>(a, w, q, topk, nt, qi, w.E);
+    cnt = rerank_write<CH, GF>(a, w, q, topk, nt, qi, w.E);
   } else {
     cnt = min(nt, a.k);
     write_row(topk, cnt, a.k, qi, a.o);
@@ -594,7 +597,7 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
 
 // MINB: minimum resident CTAs of 128 threads per SM the register allocation must
 // allow (4 -> 128 registers, 6 -> 80, 8 -> 64).
-template <class T, int CH, int G, int MINB>
+template <class T, int CH, int G, int GF, int MINB>
 __global__ void __launch_bounds__(128, MINB) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -605,45 +608,46 @@ __global__ void __launch_bounds__(128, MINB) batch_kernel(BatchArgs a) {
     if (lane == 0) idx = atomicAdd(&a.counters[CNT_TAKE], 1);
     idx = __shfl_sync(kFull, idx, 0);
     if (idx < nC) {
-      graph_query<T, CH, G>(a, w, a.queues[a.cap_nq + idx], true);
+      graph_query<T, CH, G, GF>(a, w, a.queues[a.cap_nq + idx], true);
     } else if (idx < nC + nB) {
-      graph_query<T, CH, G>(a, w, a.queues[2 * a.cap_nq + (idx - nC)], false);
+      graph_query<T, CH, G, GF>(a, w, a.queues[2 * a.cap_nq + (idx - nC)], false);
     } else if (idx < nC + nB + nI) {
-      scan_item<T, CH, G>(a, w, idx - nC - nB);
+      scan_item<T, CH, G, GF>(a, w, idx - nC - nB);
     } else {
       break;
     }
   }
 }
 
-template <class T, int CH, int G, int MINB>
+template <class T, int CH, int G, int GF, int MINB>
 static cudaError_t launch_t(const BatchArgs& a, int wpb, int num_sms, cudaStream_t st) {
   const int threads = 32 * wpb;
   const size_t smem = (size_t)wpb * a.warp_bytes;
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, CH, G, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, CH, G, GF, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<T, CH, G, MINB>, threads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<T, CH, G, GF, MINB>, threads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  batch_kernel<T, CH, G, MINB><<<num_sms * per_sm, threads, smem, st>>>(a);
+  batch_kernel<T, CH, G, GF, MINB><<<num_sms * per_sm, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <class T>
 static cudaError_t launch_dt(const BatchArgs& a, int wpb, int regs, int num_sms, cudaStream_t st) {
-  // G candidates per distance group: G * CH = 16 row chunks (64 registers) in flight,
-  // 8 chunks under the 64-register budget
+  // G rows per distance group: G * CH = 16 row chunks in flight (8 under the
+  // 64-register budget); a group of 32 raw bfloat16 or FP8 rows measured no faster on
+  // GB300. GF rows per group of the float32 re-rank, which runs after the traversal.
   const int ch = (a.dp4 + 31) / 32;
   if (ch <= 1) {
-    if (regs == 80) return launch_t<T, 1, 16, 6>(a, wpb, num_sms, st);
-    if (regs == 64) return launch_t<T, 1, 8, 8>(a, wpb, num_sms, st);
-    return launch_t<T, 1, 16, 4>(a, wpb, num_sms, st);
+    if (regs == 80) return launch_t<T, 1, 16, 16, 6>(a, wpb, num_sms, st);
+    if (regs == 64) return launch_t<T, 1, 8, 8, 8>(a, wpb, num_sms, st);
+    return launch_t<T, 1, 16, 16, 4>(a, wpb, num_sms, st);
   }
-  if (ch <= 2) return launch_t<T, 2, 8, 4>(a, wpb, num_sms, st);
-  if (ch <= 4) return launch_t<T, 4, 4, 4>(a, wpb, num_sms, st);
-  return launch_t<T, 8, 2, 4>(a, wpb, num_sms, st);
+  if (ch <= 2) return launch_t<T, 2, 8, 8, 4>(a, wpb, num_sms, st);
+  if (ch <= 4) return launch_t<T, 4, 4, 4, 4>(a, wpb, num_sms, st);
+  return launch_t<T, 8, 2, 2, 4>(a, wpb, num_sms, st);
 }
 
 int rerank_count(const Params& p) { return p.dtype == UNIFY_FP32 ? 0 : p.rerank_mult * p.k; }

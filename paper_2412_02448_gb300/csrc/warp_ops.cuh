@@ -41,7 +41,7 @@ __device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, cons
       const int c = g * G + u;
       ids[u] = clist[c < nv ? c : nv - 1];
     }
-    float4 x[G][CH];
+    Held<T> x[G][CH];
     float sc[G];
 #pragma unroll
     for (int u = 0; u < G; ++u) {
@@ -50,7 +50,7 @@ __device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, cons
 #pragma unroll
       for (int t = 0; t < CH; ++t) {
         const int c = lane + 32 * t;
-        x[u][t] = c < dp4 ? T::load(row, c, sc[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[u][t] = hold<T>(c < dp4 ? T::load_raw(row, c) : T::zero_raw());
       }
     }
     float part[G];
@@ -60,7 +60,7 @@ __device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, cons
 #pragma unroll
       for (int t = 0; t < CH; ++t) {
         // chunks past the row are zero in q and x alike, so their difference is zero
-        const float4 e = diff4<T>(q[t], x[u][t], sc[u]);
+        const float4 e = diff4<T>(q[t], unhold<T>(x[u][t]), sc[u]);
         s = fmaf(e.x, e.x, s);
         s = fmaf(e.y, e.y, s);
         s = fmaf(e.z, e.z, s);
