@@ -462,7 +462,7 @@ def run(args):
         nflag, flag_by = flagged(status)
         return dict(ms=ms_max, value=replicas.aggregate_qps(nq, world, ms_max), out=out, wall=wall,
                     timeline=timeline, routed=(int(isA.sum()), int(isC.sum()), int(isB.sum())), recall=gr,
-                    flagged=nflag, flagged_by=flag_by,
+                    flagged=nflag, flagged_by=flag_by, tc_used=phases["tcscan"][1] > 0,
                     phases={ph: (v[0] / v[1] if v[1] else 0.0) for ph, v in phases.items()},
                     achieved=achieved, alg=alg, parts=parts)
 
@@ -491,31 +491,43 @@ def run(args):
                 "phase_ms_per_step": {ph: round(v, 4) for ph, v in r_["phases"].items() if not ph.startswith("unused")},
                 "params": params_dict(p_)}
 
+    def tuned_both_scans(extra, k):
+        """Tuned once with each pre-filter scan (the tensor-core run also tries larger
+        tau_A, since its cheap shared scans move the best threshold up); the faster
+        tuned configuration."""
+        p_, rep_ = tuned(extra, k)
+        if not args.no_tune:
+            p_tc, rep_tc = tuned(dict(extra, tc_scan=1), k, tau_a_fracs=(0.01, 0.02, 0.05, 0.08, 0.12, 0.2))
+            if rep_tc.get("ms", 1e9) < rep_.get("ms", 1e9):
+                p_, rep_ = p_tc, rep_tc
+        return p_, rep_
+
+    def other_scan(p_, k):
+        """The same parameters with the other pre-filter scan (tensor cores or warps)."""
+        p0 = U.Params.defaults(**{f: getattr(p_, f) for f, _ in U.Params._fields_})
+        p0.tc_scan = 1 - p_.tc_scan
+        r0 = measure(p0, max(3, args.steps // 2), args.warmup, k)
+        return ("tensor_core_scan" if p0.tc_scan else "warp_scan"), {
+            "value": r0["value"], "ms_per_step": r0["ms"], "recall_by_fraction": fmt_recall(r0["recall"]),
+            "phase_ms_per_step": {ph: round(v, 4) for ph, v in r0["phases"].items() if not ph.startswith("unused")}}
+
     def precision_line(dt, k):
         """BF16 or FP8 storage with the FP32 re-rank of 4k candidates, tuned on the
-        held-out batch; BF16 is tuned with each pre-filter scan and the faster kept,
-        the other scan measured beside it at the same parameters."""
-        p_, rep_ = tuned({"dtype": dt, "rerank_mult": 4}, k)
-        if dt == U.BF16 and not args.no_tune:
-            p_tc, rep_tc = tuned({"dtype": dt, "rerank_mult": 4, "tc_scan": 1}, k,
-                                 tau_a_fracs=(0.01, 0.02, 0.05, 0.08, 0.12, 0.2))
-            if rep_tc.get("ms", 1e9) < rep_.get("ms", 1e9):
-                p_ = p_tc
+        held-out batch with each pre-filter scan, the faster kept and the other scan
+        measured beside it at the same parameters."""
+        p_, _ = tuned_both_scans({"dtype": dt, "rerank_mult": 4}, k)
         r_ = measure(p_, max(3, args.steps // 2), args.warmup, k)
         line_ = summary(r_, p_)
-        if dt == U.BF16:
-            p0 = U.Params.defaults(**{f: getattr(p_, f) for f, _ in U.Params._fields_})
-            p0.tc_scan = 1 - p_.tc_scan
-            r0 = measure(p0, max(3, args.steps // 2), args.warmup, k)
-            line_["tensor_core_scan" if p0.tc_scan else "warp_scan"] = {
-                "value": r0["value"], "ms_per_step": r0["ms"], "recall_by_fraction": fmt_recall(r0["recall"]),
-                "phase_ms_per_step": {ph: round(v, 4) for ph, v in r0["phases"].items() if not ph.startswith("unused")}}
+        name_, other_ = other_scan(p_, k)
+        line_[name_] = other_
         return line_
 
-    # FP32 storage at k = 10: the headline
+    # FP32 storage at k = 10: the headline (its pre-filter queries on the warp scan or on
+    # the tensor cores with tf32 operands and the FP32 re-rank of 4k candidates,
+    # whichever tunes faster)
     clocks = Clocks(local)
+    params, report = tuned_both_scans({"rerank_mult": 4}, 10)
     clocks.start()
-    params, report = tuned({})
     m32 = measure(params, args.steps, args.warmup)
     clk = clocks.stop()
     value, ms_max, out = m32["value"], m32["ms"], m32["out"]
@@ -530,6 +542,10 @@ def run(args):
     if traffic is None:
         roofline["traffic_capture"] = ({"bytes": capture["bytes"], "params": capture["params"],
                                         "note": "captured with other parameters"} if capture else None)
+    headline_other = None
+    if not args.no_extra:
+        nm_, headline_other = other_scan(params, 10)
+        headline_other = {"scan": nm_, **headline_other}
 
     # hybrid selection S1 (the m neighbours nearest to the expanded object) with the
     # same parameters, beside the tuned selection (the comparison of Section 5.6)
@@ -549,7 +565,7 @@ def run(args):
         precision["bf16"] = precision_line(U.BF16, 10)
         precision["fp8e4m3"] = precision_line(U.FP8E4M3, 10)
         if 100 in ks:
-            p100, _ = tuned({}, 100)
+            p100, _ = tuned_both_scans({"rerank_mult": 4}, 100)
             precision["k100"] = {"fp32": summary(measure(p100, max(3, args.steps // 2), args.warmup, 100), p100),
                                  "bf16": precision_line(U.BF16, 100),
                                  "fp8e4m3": precision_line(U.FP8E4M3, 100)}
@@ -645,7 +661,10 @@ def run(args):
             "cuda_graph": {"ms_per_step": graph_ms, "value": world * nq / (graph_ms / 1000.0),
                            "same_ids_as_direct": graph_ok},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 2 * args.steps,
+            # per step: route and search kernels, plus the tensor-core scan's eight
+            # (bucket count, bucket scan, scatter, tile prep, unit plan, two passes, finish)
+            "gpu_launches": (2 + (8 if m32["tc_used"] else 0)) * args.steps,
+            "other_scan": headline_other,
             "clocks": clk,
             "cpu_baseline": cpu,
         }
@@ -686,7 +705,9 @@ def scan_compare(args):
     stream = torch.cuda.current_stream(dev)
     variants = {"fp32_warp": U.Params.defaults(),
                 "bf16_warp": U.Params.defaults(dtype=U.BF16, rerank_mult=4),
-                "bf16_tensor_core": U.Params.defaults(dtype=U.BF16, rerank_mult=4, tc_scan=1)}
+                "bf16_tensor_core": U.Params.defaults(dtype=U.BF16, rerank_mult=4, tc_scan=1),
+                "fp32_tensor_core": U.Params.defaults(rerank_mult=4, tc_scan=1),
+                "fp8_tensor_core": U.Params.defaults(dtype=U.FP8E4M3, rerank_mult=4, tc_scan=1)}
     steps = max(3, min(args.steps, 20))
     res, rows = {}, {}
     for name, p in variants.items():
@@ -712,7 +733,7 @@ def scan_compare(args):
                      "phase_ms_per_step": {kk: round(v[0] / max(1, v[1]), 4) for kk, v in ph.items()
                                            if not kk.startswith("unused")}}
     ref = rows["fp32_warp"]
-    for name in ("bf16_warp", "bf16_tensor_core"):
+    for name in ("bf16_warp", "bf16_tensor_core", "fp32_tensor_core", "fp8_tensor_core"):
         rec = autotune.recall_rows(rows[name]["ids"], ref["ids"], ref["count"], k)
         res[name]["recall_vs_fp32_scan"] = autotune.group_recall(rec, w.fractions)
         res[name]["recall_vs_fp32_scan"] = {f"{100 * f_:g}%": round(v_, 4) for f_, v_ in
@@ -728,12 +749,15 @@ def scan_compare(args):
             pk = json.load(f)
     except OSError:
         pass
-    tc_ms = res["bf16_tensor_core"]["phase_ms_per_step"].get("tcscan", 0.0)
-    if tc_ms > 0:
-        tf = flops / (tc_ms / 1000.0) / 1e12
-        res["bf16_tensor_core"]["useful_tflops"] = tf
-        if pk.get("bf16_tflops"):
-            res["bf16_tensor_core"]["tensor_frac_of_measured_bf16"] = tf / pk["bf16_tflops"]
+    # the operand formats' dense peaks from the measured bf16 one by the nominal ratios
+    # (tf32 1/2, E4M3 2x of bf16)
+    for name, ratio in (("bf16_tensor_core", 1.0), ("fp32_tensor_core", 0.5), ("fp8_tensor_core", 2.0)):
+        tc_ms = res[name]["phase_ms_per_step"].get("tcscan", 0.0)
+        if tc_ms > 0:
+            tf = flops / (tc_ms / 1000.0) / 1e12
+            res[name]["useful_tflops"] = tf
+            if pk.get("bf16_tflops"):
+                res[name]["tensor_frac_of_measured_peak"] = tf / (ratio * pk["bf16_tflops"])
     for name, row_bytes in (("fp32_warp", 4 * w.d + 4), ("bf16_warp", 2 * w.d + 4)):
         gbs = float(row_bytes * Y.sum()) / (res[name]["ms_per_step"] / 1000.0) / 1e9
         res[name]["row_bytes_gbs"] = gbs

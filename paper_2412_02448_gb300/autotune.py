@@ -65,8 +65,8 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
        queries run under the strategies): the (tau_A, tau_B) pair with the fastest
        batch whose recall meets the target in every group; then step 1 again under
        the new router.
-    3. CTA shape, buffer sizes, scan work-item size, register budget and (BF16
-       storage) the tensor-core pre-filter scan."""
+    3. CTA shape, buffer sizes, scan work-item size, register budget and the
+       tensor-core pre-filter scan."""
     import torch
 
     import paper_2412_02448_gb300 as U
@@ -173,9 +173,9 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
     if cur.m <= 64:
         # hybrid selection S1 instead of S2 (Section 5.6 compares the two)
         shapes.append({"selection": 1})
-    if cur.dtype == U.BF16:
-        # pre-filter queries on the tensor cores instead of the warp scan
-        shapes.append({"tc_scan": 1 - cur.tc_scan})
+    # pre-filter queries on the tensor cores instead of the warp scan (or back): bfloat16,
+    # tf32 or E4M3 operands by the storage format
+    shapes.append({"tc_scan": 1 - cur.tc_scan})
     for extra in shapes:
         p = make(extra, cur)
         try:

@@ -57,6 +57,7 @@ void free_tc(Scratch& sc) {
   release(sc.tc_bucket);
   release(sc.tc_aq);
   release(sc.tc_aqn);
+  release(sc.tc_aqs);
   if (sc.tc_qb) cudaFree(sc.tc_qb);
   sc.tc_qb = nullptr;
   release(sc.tc_tile);
@@ -64,7 +65,7 @@ void free_tc(Scratch& sc) {
   release(sc.tc_thr);
   release(sc.tc_pcnt);
   sc.tc_rows = 0;
-  sc.tc_dpq = 0;
+  sc.tc_qrow_bytes = 0;
 }
 
 void free_stage(Scratch& sc) {
@@ -116,20 +117,20 @@ cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k) {
 // Tensor-core scan buffers for nq queries of d columns, allocated only when a search
 // uses that scan (about 16 KB of candidate lists per query of capacity).
 bool tc_scratch_fits(const Scratch& sc, int64_t nq, int d) {
-  const int dpq = ((d + 63) / 64) * 64;
-  return sc.tc_part && nq <= sc.tc_rows && dpq <= sc.tc_dpq;
+  return sc.tc_part && nq <= sc.tc_rows && tc_query_row_bytes(d) <= sc.tc_qrow_bytes;
 }
 
 cudaError_t ensure_tc_scratch(Scratch& sc, int64_t nq, int d) {
   if (tc_scratch_fits(sc, nq, d)) return cudaSuccess;
-  const int dpq = ((d + 63) / 64) * 64;  // bfloat16 query rows, K padded to 64
+  const size_t qrow = tc_query_row_bytes(d);  // query rows of any of the scan's formats, K padded
   int64_t cap = nq > sc.tc_rows ? nq : sc.tc_rows;
   const int64_t rows = ((cap + kTcQueryTile - 1) / kTcQueryTile) * kTcQueryTile;
   free_tc(sc);
   cudaError_t e = alloc(sc.tc_bucket, 1024);
   if (e == cudaSuccess) e = alloc(sc.tc_aq, rows);
   if (e == cudaSuccess) e = alloc(sc.tc_aqn, rows);
-  if (e == cudaSuccess) e = cudaMalloc(&sc.tc_qb, (size_t)rows * dpq * 2);
+  if (e == cudaSuccess) e = alloc(sc.tc_aqs, rows);
+  if (e == cudaSuccess) e = cudaMalloc(&sc.tc_qb, (size_t)rows * qrow);
   if (e == cudaSuccess) e = alloc(sc.tc_tile, 4 * (rows / kTcQueryTile) + 1);
   // at most kTcUnitsPerTile units per tile, one list of kTcCandCap keys per query and unit
   if (e == cudaSuccess) e = alloc(sc.tc_part, (size_t)rows * kTcUnitsPerTile * kTcCandCap);
@@ -140,7 +141,7 @@ cudaError_t ensure_tc_scratch(Scratch& sc, int64_t nq, int d) {
     return e;
   }
   sc.tc_rows = rows;
-  sc.tc_dpq = dpq;
+  sc.tc_qrow_bytes = qrow;
   return cudaSuccess;
 }
 
@@ -190,6 +191,8 @@ int resolve(const DeviceIndex& ix, const unify_params_t* up, int k, int ef, Para
   if (p.m < 1 || p.m > 1024) return fail(UNIFY_E_ARG, "m must be in [1, 1024]");
   if (p.selection != 1 && p.selection != 2) return fail(UNIFY_E_ARG, "selection must be 1 (S1) or 2 (S2)");
   if (p.tc_scan < 0 || p.tc_scan > 2) return fail(UNIFY_E_ARG, "tc_scan must be 0, 1 or 2");
+  if (p.tc_scan && (p.rerank_mult < 1 || (long)p.rerank_mult * k > kMaxCand))
+    return fail(UNIFY_E_ARG, "rerank_mult must be >= 1 with rerank_mult * k <= 4096");
   if (p.selection == 1 && p.m > 64) return fail(UNIFY_E_ARG, "selection S1 takes m <= 64");
   if (p.cand_cap < 32 || p.cand_cap > kMaxCand) return fail(UNIFY_E_ARG, "cand_cap must be in [32, 4096]");
   if (d.visited_cap < 64 || d.visited_cap > 65536 || (d.visited_cap & (d.visited_cap - 1)))

@@ -96,10 +96,18 @@ __global__ void derive_kernel(const float* __restrict__ vec, const int32_t* __re
 
 // Reduced-precision copies, one warp per attribute-order position p (object v):
 // bfloat16 by round-to-nearest-even; FP8 E4M3 codes of x / s (saturating,
-// round-to-nearest-even) with s = max|x| / 448 (s = 1 for an all-zero vector).
+// round-to-nearest-even) with s = max|x| / 448 (s = 1 for an all-zero vector). Also
+// the squared norms, in attribute order, of the bfloat16 rows, the float32 rows and
+// the decoded FP8 rows (s * code), which the tensor-core scan of each format uses.
+__device__ __forceinline__ float fp8_value(uint32_t code) {
+  const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)(code & 0xffu), __NV_E4M3);
+  return __half2float(*reinterpret_cast<const __half*>(&h));
+}
+
 __global__ void lowp_kernel(const float* __restrict__ vec, const int32_t* __restrict__ sorted_ids, int64_t n,
                             int dp, uint2* bf_id, uint2* bf_sorted, uint32_t* f8_id, uint32_t* f8_sorted,
-                            float* sc_id, float* sc_sorted, float* xn_sorted) {
+                            float* sc_id, float* sc_sorted, float* xn_sorted, float* xn32_sorted,
+                            float* xn8_sorted) {
   const int lane = threadIdx.x & 31;
   const int dp4 = dp / 4;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -113,7 +121,7 @@ __global__ void lowp_kernel(const float* __restrict__ vec, const int32_t* __rest
     }
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     const float s = mx > 0.f ? mx / 448.f : 1.f;
-    float nn = 0.f;  // squared norm of the bfloat16 row
+    float nn = 0.f, n32 = 0.f, n8 = 0.f;  // squared norms: bfloat16, float32, decoded FP8 rows
     for (int c = lane; c < dp4; c += 32) {
       const float4 x = row[c];
       uint2 b;
@@ -131,16 +139,30 @@ __global__ void lowp_kernel(const float* __restrict__ vec, const int32_t* __rest
       nn = fmaf(b1, b1, nn);
       nn = fmaf(b2, b2, nn);
       nn = fmaf(b3, b3, nn);
+      n32 = fmaf(x.x, x.x, n32);
+      n32 = fmaf(x.y, x.y, n32);
+      n32 = fmaf(x.z, x.z, n32);
+      n32 = fmaf(x.w, x.w, n32);
+      for (int t = 0; t < 4; ++t) {
+        const float e = s * fp8_value(f >> (8 * t));
+        n8 = fmaf(e, e, n8);
+      }
       bf_id[(int64_t)v * dp4 + c] = b;
       bf_sorted[p * dp4 + c] = b;
       f8_id[(int64_t)v * dp4 + c] = f;
       f8_sorted[p * dp4 + c] = f;
     }
-    for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
+    for (int off = 16; off > 0; off >>= 1) {
+      nn += __shfl_xor_sync(0xffffffffu, nn, off);
+      n32 += __shfl_xor_sync(0xffffffffu, n32, off);
+      n8 += __shfl_xor_sync(0xffffffffu, n8, off);
+    }
     if (lane == 0) {
       sc_id[v] = s;
       sc_sorted[p] = s;
       xn_sorted[p] = nn;
+      xn32_sorted[p] = n32;
+      xn8_sorted[p] = n8;
     }
   }
 }
@@ -148,11 +170,12 @@ __global__ void lowp_kernel(const float* __restrict__ vec, const int32_t* __rest
 void free_device(DeviceIndex& ix) {
   void* ptrs[] = {ix.vec, ix.vec_sorted, ix.sorted_ids, ix.sorted_attr, ix.pos, ix.upper_base, ix.adj0,
                   ix.gmask0, ix.adjU, ix.gmaskU, ix.seg_bounds, ix.seg_start, ix.vt_bf16, ix.vts_bf16,
-                  ix.vt_fp8, ix.vts_fp8, ix.scale_fp8, ix.scale_fp8_sorted, ix.xn_bf16_sorted};
+                  ix.vt_fp8, ix.vts_fp8, ix.scale_fp8, ix.scale_fp8_sorted, ix.xn_bf16_sorted,
+                  ix.xn_f32_sorted, ix.xn_fp8_sorted};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ix.vt_bf16 = ix.vts_bf16 = ix.vt_fp8 = ix.vts_fp8 = nullptr;
-  ix.scale_fp8 = ix.scale_fp8_sorted = ix.xn_bf16_sorted = nullptr;
+  ix.scale_fp8 = ix.scale_fp8_sorted = ix.xn_bf16_sorted = ix.xn_f32_sorted = ix.xn_fp8_sorted = nullptr;
   ix.vec = ix.vec_sorted = nullptr;
   ix.sorted_ids = ix.pos = ix.upper_base = ix.adj0 = ix.adjU = ix.seg_start = nullptr;
   ix.sorted_attr = ix.seg_bounds = nullptr;
@@ -337,6 +360,8 @@ extern "C" int unify_load_index(const char* path, int device, unify_index_t** ou
   if (e == cudaSuccess) e = cudaMalloc(&ix.scale_fp8, n * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&ix.scale_fp8_sorted, n * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&ix.xn_bf16_sorted, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&ix.xn_f32_sorted, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&ix.xn_fp8_sorted, n * sizeof(float));
   if (e == cudaSuccess) {
     derive_kernel<<<1024, 256>>>(ix.vec, ix.sorted_ids, d_attr, ix.n, ix.dp, ix.vec_sorted, ix.sorted_attr, ix.pos);
     e = cudaGetLastError();
@@ -345,7 +370,7 @@ extern "C" int unify_load_index(const char* path, int device, unify_index_t** ou
     lowp_kernel<<<1024, 256>>>(ix.vec, ix.sorted_ids, ix.n, ix.dp, reinterpret_cast<uint2*>(ix.vt_bf16),
                                reinterpret_cast<uint2*>(ix.vts_bf16), reinterpret_cast<uint32_t*>(ix.vt_fp8),
                                reinterpret_cast<uint32_t*>(ix.vts_fp8), ix.scale_fp8, ix.scale_fp8_sorted,
-                               ix.xn_bf16_sorted);
+                               ix.xn_bf16_sorted, ix.xn_f32_sorted, ix.xn_fp8_sorted);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -47,6 +47,8 @@ struct DeviceIndex {
   float* scale_fp8 = nullptr;         // per-vector scale max|x| / 448 (by id)
   float* scale_fp8_sorted = nullptr;  // the same in attribute order
   float* xn_bf16_sorted = nullptr;    // squared norms of the bfloat16 rows, attribute order
+  float* xn_f32_sorted = nullptr;     // squared norms of the float32 rows, attribute order
+  float* xn_fp8_sorted = nullptr;     // squared norms of the decoded FP8 rows, attribute order
   int num_sms = 0;
 };
 
@@ -68,14 +70,15 @@ struct Scratch {
   // tensor-core pre-filter scan
   int32_t* tc_bucket = nullptr;  // 1024 bucket counters / cursors
   int32_t* tc_aq = nullptr;      // pre-filter query ids in bucketed order
-  float* tc_aqn = nullptr;       // squared norms of their bfloat16 vectors
-  void* tc_qb = nullptr;         // their bfloat16 vectors, tc_rows x tc_dpq
+  float* tc_aqn = nullptr;       // squared norms of their vectors in the scan's format
+  float* tc_aqs = nullptr;       // their FP8 scales
+  void* tc_qb = nullptr;         // their vectors in the scan's format, tc_rows x tc_qrow_bytes
   int32_t* tc_tile = nullptr;    // per tile: first row, row blocks, units, unit offsets (4 x tiles + 1)
   uint64_t* tc_part = nullptr;   // per work unit: kTcQueryTile lists of up to kTcCandCap candidate keys
   int32_t* tc_pcnt = nullptr;    // per work unit and query: candidates found
   unsigned long long* tc_thr = nullptr;  // per pre-filter query: threshold key shared by its units
   int64_t tc_rows = 0;
-  int tc_dpq = 0;
+  size_t tc_qrow_bytes = 0;
   // host-buffer staging
   int64_t stage_nq = 0;
   int stage_k = 0, stage_d = 0;
@@ -136,6 +139,7 @@ cudaError_t launch_route(const DeviceIndex& ix, const Scratch& sc, const int64_t
 cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
                          const Outputs& o, cudaStream_t st, bool skip_scan = false, const Conj* cj = nullptr);
 bool tc_scan_available(const DeviceIndex& ix, const Params& p);
+size_t tc_query_row_bytes(int d);  // bytes of one query row of the tensor-core scan, any format
 cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
                           const Outputs& o, cudaStream_t st);
 int batch_smem_per_warp(const Params& p);

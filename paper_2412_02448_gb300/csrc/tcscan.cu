@@ -52,6 +52,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 #include "warp_ops.cuh"
@@ -62,14 +64,48 @@ namespace {
 
 constexpr int kTcQ = kTcQueryTile;  // queries per tile (MMA M = tensor-memory lanes)
 constexpr int kTcRows = 256;        // rows per block (MMA N = tensor-memory columns per accumulator)
-constexpr int kTcKc = 64;           // K elements per stage (one 128-byte swizzle row)
+constexpr int kTcKb = 128;          // bytes of K per stage (one 128-byte swizzle row)
 constexpr int kTcStages = 4;
 constexpr int kTcCap = kTcCandCap;  // candidate slots per query and work unit
 constexpr int kUnitRing = 4;        // claimed work units handed from the producer to the other roles
 constexpr int kTcRMax = 64;         // candidates kept per query for the re-rank
 constexpr int kBuckets = 1024;
-constexpr int kStageA = kTcQ * kTcKc * 2;     // 16 KB of queries
-constexpr int kStageB = kTcRows * kTcKc * 2;  // 32 KB of rows
+constexpr int kStageA = kTcQ * kTcKb;     // 16 KB of queries
+constexpr int kStageB = kTcRows * kTcKb;  // 32 KB of rows
+
+// Operand formats of the scan. Every MMA instruction takes 32 bytes of K, so a stage
+// holds four of them whatever the element width:
+//   bfloat16  (BF16 storage): kind::f16, K = 16 elements, 64 per stage;
+//   tf32      (FP32 storage): kind::tf32, the float32 rows and queries as stored, of
+//                             which the tensor cores use the top 19 bits; K = 8, 32
+//                             per stage;
+//   E4M3      (FP8 storage):  kind::f8f6f4, the stored codes of the rows and E4M3 codes
+//                             of the queries (per-query scale max|q| / 448); the dot
+//                             product of the codes is scaled by s_q * s_x in the
+//                             epilogue; K = 32, 128 per stage.
+enum TcFmt { kFmtBF16 = 0, kFmtTF32 = 1, kFmtFP8 = 2 };
+
+template <int F>
+struct TcTraits;
+template <>
+struct TcTraits<kFmtBF16> {
+  static constexpr int kElemBytes = 2;
+  static constexpr bool kScaled = false;
+  // instruction descriptor type fields (A and B): bfloat16
+  static constexpr uint32_t kAB = (1u << 7) | (1u << 10);
+};
+template <>
+struct TcTraits<kFmtTF32> {
+  static constexpr int kElemBytes = 4;
+  static constexpr bool kScaled = false;
+  static constexpr uint32_t kAB = (2u << 7) | (2u << 10);  // tf32
+};
+template <>
+struct TcTraits<kFmtFP8> {
+  static constexpr int kElemBytes = 1;
+  static constexpr bool kScaled = true;
+  static constexpr uint32_t kAB = (0u << 7) | (0u << 10);  // E4M3
+};
 constexpr long long kWaitLimit = 1ll << 22;   // polls
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s of elapsed time
 constexpr uint64_t kTestWaitNs = 50000000ull;  // 50 ms: the limit of the timeout test
@@ -158,18 +194,34 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: bf16 A and B, f32 accumulator, K-major A and
-// B, M = 128, N = 256.
-__device__ __forceinline__ uint32_t idesc_bf16() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcRows >> 3) << 17) | ((uint32_t)(kTcQ >> 4) << 24);
+// Instruction descriptor: f32 accumulator, the format's A and B types (the same for
+// both), K-major A and B, M = 128, N = 256.
+template <int F>
+__device__ __forceinline__ uint32_t idesc_of() {
+  return (1u << 4) | TcTraits<F>::kAB | ((uint32_t)(kTcRows >> 3) << 17) | ((uint32_t)(kTcQ >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+template <int F>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (F == kFmtBF16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else if constexpr (F == kFmtTF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -216,16 +268,19 @@ __device__ __forceinline__ void sort64(float (&v)[64]) {
 
 struct TcArgs {
   const int32_t* sorted_ids;
-  const float* xn;     // ||bf16(x)||^2 in attribute order
+  const float* xn;     // squared norms of the rows as the scan's format holds them, attribute order
+  const float* xs;     // FP8: per-row scales in attribute order (else null)
   const float* vec;    // float32 rows by id (re-rank)
-  const unsigned char* vt_bf16;  // bfloat16 rows by id (scan of an overflowed query)
+  const unsigned char* vt;  // rows by id in the storage format (scan of an overflowed query)
+  const float* vscale;      // FP8: per-row scales by id (else null)
   const float* q;      // float32 queries (re-rank)
   int dp4, d, KC, num_sms;
   int64_t n;
   const int32_t* pa;
   const int32_t* pb;
   const int32_t* aq;    // pre-filter query ids in bucketed order
-  const float* aqn;     // ||bf16(q)||^2 in the same order
+  const float* aqn;     // squared norms of their vectors as the scan's format holds them, same order
+  const float* aqs;     // FP8: their scales (else null)
   int32_t* tile_lo;     // first row of each tile's union range
   int32_t* tile_nb;     // 256-row blocks of the union range
   int32_t* tile_units;  // work units the range is split into
@@ -265,9 +320,11 @@ __device__ __forceinline__ void tile_unit_rows(const TcArgs& a, int t, int u, in
 // those 64 minima is at least the query's 64th-smallest distance in the unit, so
 // key(T, INT_MAX) is above every key of the query's top R (R <= 64): it is published
 // into the shared threshold with atomicMin before the scan pass starts.
-template <bool kBound>
+template <int F, bool kBound>
 __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__ CUtensorMap tmX,
                                                           const __grid_constant__ CUtensorMap tmQ, TcArgs a) {
+  constexpr bool kSc = TcTraits<F>::kScaled;
+  constexpr int kKc = kTcKb / TcTraits<F>::kElemBytes;  // K elements per stage
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023));
   const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -334,8 +391,8 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
               break;
             }
             mbar_expect_tx(&s.full[st], kStageA + kStageB);
-            tma_load_2d(s.a[st], &tmQ, kc * kTcKc, t * kTcQ, &s.full[st]);
-            tma_load_2d(s.b[st], &tmX, kc * kTcKc, row0, &s.full[st]);
+            tma_load_2d(s.a[st], &tmQ, kc * kKc, t * kTcQ, &s.full[st]);
+            tma_load_2d(s.b[st], &tmX, kc * kKc, row0, &s.full[st]);
           }
       }
       // no copy may still be landing in shared memory when the CTA leaves: wait
@@ -352,7 +409,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
     // ---- MMA issuer (lane 0 issues; the warp stays converged)
     if (lane == 0) {
       bool ok = true;
-      const uint32_t idesc = idesc_bf16();
+      const uint32_t idesc = idesc_of<F>();
       long long it = 0, g = 0;
       for (long long useq = 0; ok; ++useq) {
         const int us = (int)(useq % kUnitRing);
@@ -385,8 +442,8 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
             const uint64_t da = sw128_desc(smem_u32(s.a[st]));
             const uint64_t db = sw128_desc(smem_u32(s.b[st]));
 #pragma unroll
-            for (int kk = 0; kk < kTcKc / 16; ++kk)
-              umma_bf16(d_tmem, da + 2 * kk, db + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < kTcKb / 32; ++kk)  // 32 bytes of K per instruction
+              umma<F>(d_tmem, da + 2 * kk, db + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
             umma_commit(&s.empty[st]);
           }
           if (!ok) break;
@@ -419,12 +476,13 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       const int qpos = t * kTcQ + tq;
       const bool qv = qpos < nA;
       int pa = 0, pb = 0;
-      float qn = 0.f;
+      float qn = 0.f, qs = 1.f;
       if (qv) {
         const int qi = a.aq[qpos];
         pa = a.pa[qi];
         pb = a.pb[qi];
         qn = a.aqn[qpos];
+        if constexpr (kSc) qs = a.aqs[qpos];
       }
       float gm0[32], gm1[32];
 #pragma unroll
@@ -435,11 +493,15 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         // row0 + 32c + j of chunk c); the chunk-pair loop stays rolled, the two chunks
         // of a pair feed the two halves of the group minima
         const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);
-        float x0n, x1n;
+        float x0n, x1n, s0n = 1.f, s1n = 1.f;
         {
           const int64_t row = (int64_t)row0 + lane;
           x0n = row < a.n ? __ldg(a.xn + row) : 0.f;
           x1n = row + 32 < a.n ? __ldg(a.xn + row + 32) : 0.f;
+          if constexpr (kSc) {
+            s0n = row < a.n ? __ldg(a.xs + row) : 0.f;
+            s1n = row + 32 < a.n ? __ldg(a.xs + row + 32) : 0.f;
+          }
         }
         if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1), a.wait_ns))) {
           failed = true;
@@ -449,11 +511,15 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * kTcRows);
 #pragma unroll 1
         for (int cp = 0; cp < kTcRows / 64; ++cp) {
-          const float x0 = x0n, x1 = x1n;
+          const float x0 = x0n, x1 = x1n, s0 = s0n, s1 = s1n;
           if (cp + 1 < kTcRows / 64) {
             const int64_t row = (int64_t)row0 + (cp + 1) * 64 + lane;
             x0n = row < a.n ? __ldg(a.xn + row) : 0.f;
             x1n = row + 32 < a.n ? __ldg(a.xn + row + 32) : 0.f;
+            if constexpr (kSc) {
+              s0n = row < a.n ? __ldg(a.xs + row) : 0.f;
+              s1n = row + 32 < a.n ? __ldg(a.xs + row + 32) : 0.f;
+            }
           }
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -466,7 +532,9 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
             for (int j = 0; j < 32; ++j) {
               const int col = c * 32 + j;
               const float xv = __shfl_sync(kFull, h ? x1 : x0, j);
-              const float dist = fmaxf(xv + qn - 2.f * v[j], 0.f);
+              float w = 2.f;  // weight of the dot product
+              if constexpr (kSc) w = 2.f * qs * __shfl_sync(kFull, h ? s1 : s0, j);
+              const float dist = fmaxf(xv + qn - w * v[j], 0.f);
               const bool in = col >= c0 && col < c1;
               if (h) gm1[j] = in ? fminf(gm1[j], dist) : gm1[j];
               else gm0[j] = in ? fminf(gm0[j], dist) : gm0[j];
@@ -520,13 +588,14 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       const int qpos = t * kTcQ + tq;
       const bool qv = qpos < nA;
       int pa = 0, pb = 0;
-      float qn = 0.f;
+      float qn = 0.f, qs = 1.f;
       uint64_t thr = kKeyMax;
       if (qv) {
         const int qi = a.aq[qpos];
         pa = a.pa[qi];
         pb = a.pb[qi];
         qn = a.aqn[qpos];
+        if constexpr (kSc) qs = a.aqs[qpos];
         thr = *reinterpret_cast<volatile unsigned long long*>(a.qthr + qpos);
       }
       uint64_t* list = a.part + ((int64_t)x * kTcQ + tq) * kTcCap;
@@ -537,12 +606,13 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         // holds row row0 + 32c + j of chunk c; the next chunk's loads are issued before
         // the current chunk is processed (the chunk loop stays rolled: a compact body)
         const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);  // this query's columns
-        float xnext;
+        float xnext, snext = 1.f;
         int32_t inext;
         {
           const int64_t row = (int64_t)row0 + lane;
           xnext = row < a.n ? __ldg(a.xn + row) : 0.f;
           inext = row < a.n ? __ldg(a.sorted_ids + row) : 0;
+          if constexpr (kSc) snext = row < a.n ? __ldg(a.xs + row) : 0.f;
         }
         if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1), a.wait_ns))) {
           failed = true;
@@ -552,12 +622,13 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * kTcRows);
 #pragma unroll 1
         for (int c = 0; c < kTcRows / 32; ++c) {
-          const float xc = xnext;
+          const float xc = xnext, sc = snext;
           const int32_t ic = inext;
           if (c + 1 < kTcRows / 32) {
             const int64_t row = (int64_t)row0 + (c + 1) * 32 + lane;
             xnext = row < a.n ? __ldg(a.xn + row) : 0.f;
             inext = row < a.n ? __ldg(a.sorted_ids + row) : 0;
+            if constexpr (kSc) snext = row < a.n ? __ldg(a.xs + row) : 0.f;
           }
           const bool need = c1 > c * 32 && c0 < c * 32 + 32;
           if (!__any_sync(kFull, need)) continue;
@@ -568,7 +639,9 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
             const int col = c * 32 + j;
             const float xv = __shfl_sync(kFull, xc, j);
             const int32_t idj = __shfl_sync(kFull, ic, j);
-            const uint64_t key = make_key(fmaxf(xv + qn - 2.f * v[j], 0.f), idj);
+            float w = 2.f;  // weight of the dot product
+            if constexpr (kSc) w = 2.f * qs * __shfl_sync(kFull, sc, j);
+            const uint64_t key = make_key(fmaxf(xv + qn - w * v[j], 0.f), idj);
             if (col >= c0 && col < c1 && key < thr) {
               if (cnt < kTcCap) list[cnt] = key;
               ++cnt;
@@ -675,10 +748,10 @@ __global__ void tc_unit_plan(TcArgs a) {
 // tile that overlap its range into the R smallest keys, re-ranks them with exact
 // float32 distances and writes the result row. A list that overflowed (more than
 // kTcCap candidates below the bound) sends the query through an exact warp scan of
-// its range instead: bfloat16 rows against the float32 query, direct differences,
-// the same selection as the warp scan of the search kernel. After a timed-out wait
-// the rows are empty and flagged.
-template <int CH, int G>
+// its range instead: the stored rows (format T) against the float32 query, direct
+// differences, the same selection as the warp scan of the search kernel. After a
+// timed-out wait the rows are empty and flagged.
+template <class T, int CH, int G>
 __global__ void __launch_bounds__(128) tc_finish(TcArgs a) {
   __shared__ uint64_t top[4][kTcRMax];
   __shared__ uint64_t out[4][kTcRMax];
@@ -721,7 +794,7 @@ __global__ void __launch_bounds__(128) tc_finish(TcArgs a) {
     } else {
       for (int base = pa; base < pb; base += 32) {
         int cid = base + lane < pb ? __ldg(a.sorted_ids + base + lane) : -1;
-        const float dist = batch_dist<StoreBF16, CH, G>(qv, cid, a.vt_bf16, a.dp4 * 8, nullptr, a.dp4, clist[warp]);
+        const float dist = batch_dist<T, CH, G>(qv, cid, a.vt, a.dp4 * T::kChunkBytes, a.vscale, a.dp4, clist[warp]);
         nt = topk_offer(top[warp], nt, a.R, cid >= 0 ? make_key(dist, cid) : kKeyMax, R[warp]);
       }
     }
@@ -772,12 +845,15 @@ __global__ void tc_bucket_scan(int32_t* bucket) {
   bucket[t] = sm[t] - bucket[t];  // exclusive start, used as a fill cursor
 }
 
-// Places every pre-filter query in its bucket, writes its bfloat16 vector
-// (zero-padded to dpq) and the squared norm of those bfloat16 values, and resets
-// its shared threshold.
+// Places every pre-filter query in its bucket, writes its vector in the scan's
+// format (zero-padded to dpq elements: bfloat16 by round-to-nearest-even; float32 as
+// given for tf32; E4M3 codes of q / s_q with s_q = max|q| / 448, saturating) and the
+// squared norm of those values (for E4M3, of the decoded s_q * code), and resets its
+// shared threshold.
+template <int F>
 __global__ void tc_scatter(const int32_t* __restrict__ queues, const int32_t* __restrict__ pa,
                            const float* __restrict__ q, int d, int dpq, int32_t* counters, int32_t* bucket,
-                           int64_t n, int32_t* aq, float* aqn, __nv_bfloat16* qb, unsigned long long* qthr) {
+                           int64_t n, int32_t* aq, float* aqn, float* aqs, void* qb, unsigned long long* qthr) {
   const int nA = counters[CNT_QA];
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * (blockDim.x >> 5);
@@ -789,17 +865,43 @@ __global__ void tc_scatter(const int32_t* __restrict__ queues, const int32_t* __
       pos = atomicAdd(&bucket[b], 1);
     }
     pos = __shfl_sync(kFull, pos, 0);
-    float ss = 0.f;
-    for (int c = lane; c < dpq; c += 32) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(c < d ? q[(int64_t)qi * d + c] : 0.f);
-      qb[(int64_t)pos * dpq + c] = h;
-      const float f = __bfloat162float(h);
-      ss = fmaf(f, f, ss);
+    const float* qrow = q + (int64_t)qi * d;
+    float ss = 0.f, sq = 1.f;
+    if constexpr (F == kFmtBF16) {
+      __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(qb) + (int64_t)pos * dpq;
+      for (int c = lane; c < dpq; c += 32) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(c < d ? qrow[c] : 0.f);
+        dst[c] = h;
+        const float f = __bfloat162float(h);
+        ss = fmaf(f, f, ss);
+      }
+    } else if constexpr (F == kFmtTF32) {
+      float* dst = reinterpret_cast<float*>(qb) + (int64_t)pos * dpq;
+      for (int c = lane; c < dpq; c += 32) {
+        const float f = c < d ? qrow[c] : 0.f;
+        dst[c] = f;
+        ss = fmaf(f, f, ss);
+      }
+    } else {
+      float mx = 0.f;
+      for (int c = lane; c < d; c += 32) mx = fmaxf(mx, fabsf(qrow[c]));
+      for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, off));
+      sq = mx > 0.f ? mx / 448.f : 1.f;
+      unsigned char* dst = reinterpret_cast<unsigned char*>(qb) + (int64_t)pos * dpq;
+      for (int c = lane; c < dpq; c += 32) {
+        const __nv_fp8_storage_t code =
+            __nv_cvt_float_to_fp8(c < d ? qrow[c] / sq : 0.f, __NV_SATFINITE, __NV_E4M3);
+        dst[c] = (unsigned char)code;
+        const __half_raw hr = __nv_cvt_fp8_to_halfraw(code, __NV_E4M3);
+        const float f = sq * __half2float(*reinterpret_cast<const __half*>(&hr));
+        ss = fmaf(f, f, ss);
+      }
     }
     for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(kFull, ss, off);
     if (lane == 0) {
       aq[pos] = qi;
       aqn[pos] = ss;
+      if (aqs) aqs[pos] = sq;
       qthr[pos] = kKeyMax;
     }
   }
@@ -818,62 +920,68 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D bfloat16 tensor map: rows of `cols` elements, `row_bytes` apart, boxes of
-// box_cols x box_rows with 128-byte swizzle; reads outside the tensor return 0.
-bool encode_2d_bf16(CUtensorMap* tm, const void* base, uint64_t cols, uint64_t rows, uint64_t row_bytes,
-                    uint32_t box_cols, uint32_t box_rows) {
+// 2D tensor map of the scan's format: rows of `cols` elements, `row_bytes` apart,
+// boxes of box_cols x box_rows (box_cols elements = 128 bytes) with 128-byte swizzle;
+// reads outside the tensor return 0.
+bool encode_2d(CUtensorMap* tm, CUtensorMapDataType dt, const void* base, uint64_t cols, uint64_t rows,
+               uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {cols, rows};
   const cuuint64_t strides[1] = {row_bytes};
   const cuuint32_t box[2] = {box_cols, box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  return fn(tm, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
-}  // namespace
 
-bool tc_scan_available(const DeviceIndex& ix, const Params& p) {
-  return p.dtype == UNIFY_BF16 && p.tc_scan && (ix.dp % 8) == 0 && rerank_count(p) <= kTcRMax &&
-         ix.d <= 1024 && encode_fn() != nullptr;
-}
-
-cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
-                          const Outputs& o, cudaStream_t st) {
-  const int dpq = ((ix.d + kTcKc - 1) / kTcKc) * kTcKc;
+template <int F>
+cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
+                      const Outputs& o, cudaStream_t st) {
+  constexpr int eb = TcTraits<F>::kElemBytes;
+  constexpr int kKc = kTcKb / eb;  // K elements per stage
+  const int dpq = ((ix.d + kKc - 1) / kKc) * kKc;
   cudaError_t e = cudaMemsetAsync(sc.tc_bucket, 0, kBuckets * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   tc_bucket_count<<<ix.num_sms * 2, 256, 0, st>>>(sc.queues, sc.pa, sc.counters, sc.tc_bucket, ix.n);
   tc_bucket_scan<<<1, kBuckets, 0, st>>>(sc.tc_bucket);
-  tc_scatter<<<ix.num_sms * 4, 256, 0, st>>>(sc.queues, sc.pa, q, ix.d, dpq, sc.counters, sc.tc_bucket, ix.n,
-                                             sc.tc_aq, sc.tc_aqn, reinterpret_cast<__nv_bfloat16*>(sc.tc_qb),
-                                             sc.tc_thr);
+  tc_scatter<F><<<ix.num_sms * 4, 256, 0, st>>>(sc.queues, sc.pa, q, ix.d, dpq, sc.counters, sc.tc_bucket, ix.n,
+                                                sc.tc_aq, sc.tc_aqn, F == kFmtFP8 ? sc.tc_aqs : nullptr, sc.tc_qb,
+                                                sc.tc_thr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const CUtensorMapDataType dt = F == kFmtBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : F == kFmtTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const void* rows = F == kFmtBF16 ? (const void*)ix.vts_bf16
+                     : F == kFmtTF32 ? (const void*)ix.vec_sorted : (const void*)ix.vts_fp8;
   CUtensorMap tmX, tmQ;
-  if (!encode_2d_bf16(&tmX, ix.vts_bf16, (uint64_t)ix.dp, (uint64_t)ix.n, (uint64_t)ix.dp * 2, kTcKc, kTcRows) ||
-      !encode_2d_bf16(&tmQ, sc.tc_qb, (uint64_t)dpq, (uint64_t)sc.tc_rows, (uint64_t)dpq * 2, kTcKc, kTcQ))
+  if (!encode_2d(&tmX, dt, rows, (uint64_t)ix.dp, (uint64_t)ix.n, (uint64_t)ix.dp * eb, kKc, kTcRows) ||
+      !encode_2d(&tmQ, dt, sc.tc_qb, (uint64_t)dpq, (uint64_t)sc.tc_rows, (uint64_t)dpq * eb, kKc, kTcQ))
     return cudaErrorInvalidValue;
   const int tiles = (int)(sc.tc_rows / kTcQ);
   TcArgs a;
   a.sorted_ids = ix.sorted_ids;
-  a.xn = ix.xn_bf16_sorted;
+  a.xn = F == kFmtBF16 ? ix.xn_bf16_sorted : F == kFmtTF32 ? ix.xn_f32_sorted : ix.xn_fp8_sorted;
+  a.xs = F == kFmtFP8 ? ix.scale_fp8_sorted : nullptr;
   a.vec = ix.vec;
-  a.vt_bf16 = ix.vt_bf16;
+  a.vt = F == kFmtBF16 ? ix.vt_bf16 : F == kFmtTF32 ? reinterpret_cast<const unsigned char*>(ix.vec) : ix.vt_fp8;
+  a.vscale = F == kFmtFP8 ? ix.scale_fp8 : nullptr;
   a.q = q;
   a.dp4 = ix.dp / 4;
   a.d = ix.d;
-  a.KC = dpq / kTcKc;
+  a.KC = dpq / kKc;
   a.num_sms = ix.num_sms;
   a.n = ix.n;
   a.pa = sc.pa;
   a.pb = sc.pb;
   a.aq = sc.tc_aq;
   a.aqn = sc.tc_aqn;
+  a.aqs = F == kFmtFP8 ? sc.tc_aqs : nullptr;
   a.tile_lo = sc.tc_tile;
   a.tile_nb = sc.tc_tile + tiles;
   a.tile_units = sc.tc_tile + 2 * tiles;
@@ -883,7 +991,7 @@ cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float*
   a.pcnt = sc.tc_pcnt;
   a.counters = sc.counters;
   a.k = p.k;
-  a.R = rerank_count(p);
+  a.R = p.rerank_mult * p.k;
   a.stall = p.tc_scan == 2 ? 1 : 0;
   a.wait_ns = p.tc_scan == 2 ? kTestWaitNs : kWaitNs;
   a.o = o;
@@ -892,28 +1000,52 @@ cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float*
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = tc_smem_bytes();
-  e = cudaFuncSetAttribute(tc_scan_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(tc_scan_kernel<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tc_scan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(tc_scan_kernel<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // bounding pass (each query's bound), then the collecting pass
-  tc_scan_kernel<true><<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
+  tc_scan_kernel<F, true><<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  tc_scan_kernel<false><<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
+  tc_scan_kernel<F, false><<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // FP32 re-rank with the row-width variants of the search kernel
+  // FP32 re-rank with the row-width variants of the search kernel; an overflowed
+  // query scans the stored rows of its format
+  using T = typename std::conditional<F == kFmtBF16, StoreBF16,
+                                      typename std::conditional<F == kFmtTF32, StoreF32, StoreFP8>::type>::type;
   const int ch = (a.dp4 + 31) / 32;
   if (ch <= 1)
-    tc_finish<1, 16><<<ix.num_sms * 4, 128, 0, st>>>(a);
+    tc_finish<T, 1, 16><<<ix.num_sms * 4, 128, 0, st>>>(a);
   else if (ch <= 2)
-    tc_finish<2, 8><<<ix.num_sms * 4, 128, 0, st>>>(a);
+    tc_finish<T, 2, 8><<<ix.num_sms * 4, 128, 0, st>>>(a);
   else if (ch <= 4)
-    tc_finish<4, 4><<<ix.num_sms * 4, 128, 0, st>>>(a);
+    tc_finish<T, 4, 4><<<ix.num_sms * 4, 128, 0, st>>>(a);
   else
-    tc_finish<8, 2><<<ix.num_sms * 4, 128, 0, st>>>(a);
+    tc_finish<T, 8, 2><<<ix.num_sms * 4, 128, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_scan_available(const DeviceIndex& ix, const Params& p) {
+  if (!p.tc_scan || ix.d > 1024 || encode_fn() == nullptr) return false;
+  const long R = (long)p.rerank_mult * p.k;
+  if (R < p.k || R > kTcRMax) return false;
+  // the rows' TMA stride must be a multiple of 16 bytes
+  if (p.dtype == UNIFY_BF16) return ix.dp % 8 == 0;
+  if (p.dtype == UNIFY_FP32) return true;  // dp is a multiple of 4
+  return ix.dp % 16 == 0;                  // FP8: one byte per element
+}
+
+size_t tc_query_row_bytes(int d) { return (size_t)((d + kTcKb - 1) / kTcKb) * kTcKb * 4; }
+
+cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
+                          const Outputs& o, cudaStream_t st) {
+  if (p.dtype == UNIFY_BF16) return launch_tc<kFmtBF16>(ix, sc, q, p, o, st);
+  if (p.dtype == UNIFY_FP32) return launch_tc<kFmtTF32>(ix, sc, q, p, o, st);
+  return launch_tc<kFmtFP8>(ix, sc, q, p, o, st);
 }
 
 }  // namespace unify
