@@ -63,6 +63,41 @@ __device__ __forceinline__ void warp_sort_asc_payload(uint64_t& x, uint32_t& f) 
   }
 }
 
+// The keys of the lanes in kb (a ballot; the other lanes hold kKeyMax), distinct,
+// sorted ascending into lanes 0 .. popc(kb) - 1 with their payloads; the other lanes
+// end with kKeyMax and payload 0. Up to four keys take their rank among the kept keys
+// by broadcast comparisons and move in one shuffle; more go through the bitonic
+// network. Both give the same lanes.
+__device__ __forceinline__ void warp_sort_kept(uint64_t& x, uint32_t& f, unsigned kb) {
+  const int nk = __popc(kb);
+  if (nk > 4) {
+    warp_sort_asc_payload(x, f);
+    return;
+  }
+  const int lane = lane_id();
+  const bool mine = (kb >> lane) & 1u;
+  int rank = 0;
+  for (unsigned rest = kb; rest; rest &= rest - 1) {
+    const uint64_t y = __shfl_sync(kFull, x, __ffs(rest) - 1);
+    rank += y < x;
+  }
+  int src = lane;
+  for (int r = 0; r < nk; ++r) {
+    const unsigned b = __ballot_sync(kFull, mine && rank == r);
+    if (lane == r) src = __ffs(b) - 1;
+  }
+  const uint64_t y = __shfl_sync(kFull, x, src);
+  const uint32_t g = __shfl_sync(kFull, f, src);
+  x = lane < nk ? y : kKeyMax;
+  f = lane < nk ? g : 0u;
+}
+
+__device__ __forceinline__ uint64_t warp_sort_kept(uint64_t x, unsigned kb) {
+  uint32_t f = 0;
+  warp_sort_kept(x, f, kb);
+  return x;
+}
+
 // First index i in a[0, n) with a[i] >= x (per lane).
 __device__ __forceinline__ int lower_bound_u64(const uint64_t* a, int n, uint64_t x) {
   int lo = 0, hi = n;
@@ -92,13 +127,14 @@ __device__ __forceinline__ bool contains_u64(const uint64_t* a, int n, uint64_t 
 // Every lane of the warp calls it. Lane i < nb holds the i-th smallest batch key
 // (distinct from every arr entry); the other lanes hold kKeyMax. Entries that fall
 // beyond cap are dropped (the largest ones). flags (may be null) move with their
-// keys; new entries get flag 0. R is 32 ints of per-warp shared scratch.
+// keys; new entries get flag 0. R is 32 ints of per-warp shared scratch. rank, when
+// given (>= 0 on the lanes < nb), is lower_bound(arr, n, bk), already known.
 // Returns the new size; *r0 = rank of the smallest batch key in the old array
 // (entries below r0 did not move); *dropped = some entry fell beyond cap.
 __device__ __forceinline__ int warp_merge(uint64_t* arr, uint8_t* flags, int n, int cap, uint64_t bk,
-                                          int nb, int* R, int* r0_out, bool* dropped) {
+                                          int nb, int* R, int* r0_out, bool* dropped, int rank = -1) {
   const int lane = lane_id();
-  int r = (lane < nb) ? lower_bound_u64(arr, n, bk) : n;
+  int r = (lane < nb) ? (rank >= 0 ? rank : lower_bound_u64(arr, n, bk)) : n;
   R[lane] = r;
   __syncwarp();
   const int r0 = __shfl_sync(kFull, r, 0);
@@ -233,14 +269,9 @@ struct StoreFP8 {
   }
 };
 
-// A chunk as a distance group holds it (raw, or decoded at load) and back.
+// A chunk as a distance group holds it (raw, or decoded at load) and its value.
 template <class T>
 using Held = typename std::conditional<T::kHoldRaw, typename T::Raw, float4>::type;
-template <class T>
-__device__ __forceinline__ Held<T> hold(const typename T::Raw& r) {
-  if constexpr (T::kHoldRaw) return r;
-  else return T::decode(r);
-}
 template <class T>
 __device__ __forceinline__ float4 unhold(const Held<T>& h) {
   if constexpr (T::kHoldRaw) return T::decode(h);

@@ -318,20 +318,34 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
       n_dist += __popc(__ballot_sync(kFull, cid >= 0));
       const uint64_t key = cid >= 0 ? make_key(dist, cid) : kKeyMax;
       const uint64_t thr = nA >= efl ? (hybrid ? w.ann[efl - 1] : E[efl - 1]) : kKeyMax;
-      bool keep = cid >= 0 && key < thr;
-      // a visited object the filter forgot is still in E (or, after an overflow of
-      // E, possibly only in ann): drop it
-      if (keep && contains_u64(E, nE, key)) keep = false;
-      if (keep && hybrid && truncated && contains_u64(w.ann, nA, key)) keep = false;
+      const bool keep = cid >= 0 && key < thr;
       const unsigned kb = __ballot_sync(kFull, keep);
       if (kb == 0) continue;
       int r0;
       bool dropped;
       uint64_t sk = keep ? key : kKeyMax;
       uint32_t fl = (keep && inr) ? 1u : 0u;
-      warp_sort_asc_payload(sk, fl);
-      const int nk = __popc(kb);
-      nE = warp_merge(E, w.Ef, nE, capE, sk, nk, w.R, &r0, &dropped);
+      warp_sort_kept(sk, fl, kb);
+      int nk = __popc(kb);
+      // a visited object the filter forgot is still in E (or, after an overflow of E,
+      // possibly only in ann): drop it. Its rank in E is the merge's rank, found once.
+      int rk = lane < nk ? lower_bound_u64(E, nE, sk) : nE;
+      bool dup = lane < nk && rk < nE && E[rk] == sk;
+      if (hybrid && truncated && lane < nk && !dup) dup = contains_u64(w.ann, nA, sk);
+      if (__any_sync(kFull, dup)) {
+        const unsigned kept = __ballot_sync(kFull, lane < nk && !dup);
+        nk = __popc(kept);
+        const int src = lane < nk ? (int)__fns(kept, 0, lane + 1) : lane;
+        sk = __shfl_sync(kFull, sk, src);
+        fl = __shfl_sync(kFull, fl, src);
+        rk = __shfl_sync(kFull, rk, src);
+        if (lane >= nk) {
+          sk = kKeyMax;
+          fl = 0u;
+        }
+        if (nk == 0) continue;
+      }
+      nE = warp_merge(E, w.Ef, nE, capE, sk, nk, w.R, &r0, &dropped, rk);
       if (r0 < cursor) cursor = r0;
       if (!hybrid) {
         nA = nE;  // cand and ann share the buffer; dropping beyond ef is ann's pop
@@ -529,7 +543,8 @@ __device__ void scan_item(const BatchArgs& a, const WarpMem& w, int it) {
 #pragma unroll
         for (int t = 0; t < CH; ++t) {
           const int c = lane + 32 * t;
-          x[r][t] = hold<T>(c < a.dp4 ? T::load_raw(src, c) : T::zero_raw());
+          if constexpr (T::kHoldRaw) x[r][t] = c < a.dp4 ? T::load_raw(src, c) : T::zero_raw();
+          else x[r][t] = c < a.dp4 ? T::load(src, c, sc[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
 #pragma unroll

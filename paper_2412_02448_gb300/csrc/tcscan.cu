@@ -534,7 +534,8 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
               const float xv = __shfl_sync(kFull, h ? x1 : x0, j);
               float w = 2.f;  // weight of the dot product
               if constexpr (kSc) w = 2.f * qs * __shfl_sync(kFull, h ? s1 : s0, j);
-              const float dist = fmaxf(xv + qn - w * v[j], 0.f);
+              // clamped at 0 once, on the bound (the clamp commutes with min and rank)
+              const float dist = xv + qn - w * v[j];
               const bool in = col >= c0 && col < c1;
               if (h) gm1[j] = in ? fminf(gm1[j], dist) : gm1[j];
               else gm0[j] = in ? fminf(gm0[j], dist) : gm0[j];
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       for (int i = 0; i < 64; ++i)
         if (i == a.R - 1) T = v64[i];
       if (qv && T < __int_as_float(0x7f800000))
-        atomicMin(a.qthr + qpos, (unsigned long long)make_key(T, 0x7fffffff));
+        atomicMin(a.qthr + qpos, (unsigned long long)make_key(fmaxf(T, 0.f), 0x7fffffff));
     }
     if (failed) atomicExch(err, 1);
   } else {
@@ -598,6 +599,8 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         if constexpr (kSc) qs = a.aqs[qpos];
         thr = *reinterpret_cast<volatile unsigned long long*>(a.qthr + qpos);
       }
+      // the bound's distance (+inf without a bound: every row qualifies)
+      const float tdist = thr == kKeyMax ? __int_as_float(0x7f800000) : key_dist(thr);
       uint64_t* list = a.part + ((int64_t)x * kTcQ + tq) * kTcCap;
       int cnt = 0;
       for (int row0 = r0; row0 < r1; row0 += kTcRows, ++g) {
@@ -634,16 +637,19 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
           if (!__any_sync(kFull, need)) continue;
           float v[32];
           tmem_ld32(taddr + (uint32_t)(c * 32), v);
+          // this query's columns of the chunk: [jlo, jhi)
+          const int jlo = c0 - c * 32, jhi = c1 - c * 32;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int col = c * 32 + j;
             const float xv = __shfl_sync(kFull, xc, j);
             const int32_t idj = __shfl_sync(kFull, ic, j);
             float w = 2.f;  // weight of the dot product
             if constexpr (kSc) w = 2.f * qs * __shfl_sync(kFull, sc, j);
-            const uint64_t key = make_key(fmaxf(xv + qn - w * v[j], 0.f), idj);
-            if (col >= c0 && col < c1 && key < thr) {
-              if (cnt < kTcCap) list[cnt] = key;
+            const float dist = fmaxf(xv + qn - w * v[j], 0.f);
+            // the bound is the key (tdist, INT_MAX): a row's key is below it exactly
+            // when its distance is at most tdist
+            if (j >= jlo && j < jhi && dist <= tdist) {
+              if (cnt < kTcCap) list[cnt] = make_key(dist, idj);
               ++cnt;
             }
           }

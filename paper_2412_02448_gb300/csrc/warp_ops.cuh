@@ -50,7 +50,8 @@ __device__ __forceinline__ float batch_dist(const float4 (&q)[CH], int cid, cons
 #pragma unroll
       for (int t = 0; t < CH; ++t) {
         const int c = lane + 32 * t;
-        x[u][t] = hold<T>(c < dp4 ? T::load_raw(row, c) : T::zero_raw());
+        if constexpr (T::kHoldRaw) x[u][t] = c < dp4 ? T::load_raw(row, c) : T::zero_raw();
+        else x[u][t] = c < dp4 ? T::load(row, c, sc[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     float part[G];
@@ -84,7 +85,7 @@ __device__ __forceinline__ int topk_offer(uint64_t* topk, int nt, int k, uint64_
   const bool pass = key < thr;
   const unsigned bal = __ballot_sync(kFull, pass);
   if (bal == 0) return nt;
-  uint64_t s = warp_sort_asc(pass ? key : kKeyMax);
+  uint64_t s = warp_sort_kept(pass ? key : kKeyMax, bal);
   int r0;
   bool dropped;
   return warp_merge(topk, nullptr, nt, k, s, __popc(bal), R, &r0, &dropped);
