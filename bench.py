@@ -363,7 +363,8 @@ def run(args):
     base = U.Params.defaults(tau_a=w.n // 100, tau_b=w.n // 2, scan_rows=args.scan_rows, ef=args.ef,
                              ef_post=args.ef_post or args.ef, m=args.m, cand_cap=args.cand_cap,
                              visited_cap=args.visited_cap, warps_per_block=args.warps_per_block,
-                             reg_budget=args.reg_budget, selection=args.selection)
+                             reg_budget=args.reg_budget, selection=args.selection, rerank_mult=args.rerank_mult,
+                             tc_scan=args.tc_scan)
     if args.tau_a >= 0:
         base.tau_a = args.tau_a
     if args.tau_b >= 0:
@@ -526,7 +527,7 @@ def run(args):
     # the tensor cores with tf32 operands and the FP32 re-rank of 4k candidates,
     # whichever tunes faster)
     clocks = Clocks(local)
-    params, report = tuned_both_scans({"rerank_mult": 4}, 10)
+    params, report = tuned_both_scans({}, 10)
     clocks.start()
     m32 = measure(params, args.steps, args.warmup)
     clk = clocks.stop()
@@ -565,7 +566,7 @@ def run(args):
         precision["bf16"] = precision_line(U.BF16, 10)
         precision["fp8e4m3"] = precision_line(U.FP8E4M3, 10)
         if 100 in ks:
-            p100, _ = tuned_both_scans({"rerank_mult": 4}, 100)
+            p100, _ = tuned_both_scans({}, 100)
             precision["k100"] = {"fp32": summary(measure(p100, max(3, args.steps // 2), args.warmup, 100), p100),
                                  "bf16": precision_line(U.BF16, 100),
                                  "fp8e4m3": precision_line(U.FP8E4M3, 100)}
@@ -841,6 +842,8 @@ def main():
     ap.add_argument("--scan-rows", type=int, default=8192)
     ap.add_argument("--reg-budget", type=int, default=128)
     ap.add_argument("--selection", type=int, default=2, choices=[1, 2], help="hybrid selection S1 or S2")
+    ap.add_argument("--rerank-mult", type=int, default=4)
+    ap.add_argument("--tc-scan", type=int, default=0, choices=[0, 1], help="starting / no-tune pre-filter scan")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the BF16/FP8 lines")
