@@ -40,7 +40,10 @@ sys.path.insert(0, ROOT)
 METRIC = "QPS at recall@10>=0.95 by range fraction; FP32 vs BF16/FP8 path; % HBM peak"
 UNIT = "queries/s"
 WORKLOADS = {
+    "c1": "c1: n=10,000 d=64 N(0,1), attribute a permutation, 200 queries, ranges 1/10/50%, k=10, auto-routed",
     "c2": "c2: n=1,000,000 d=128 int-valued mixture, 10,000 queries, ranges 0.1/1/10/50/100%, k=10, auto-routed",
+    "c3": "c3: n=1,000,000 d=96 unit-normalised 500-centroid mixture, 10,000 queries, range fractions log-uniform "
+          "in 0.01-100% (recall grouped by decade, labelled by its lower edge), k=10, auto-routed",
     "c4": "c4: n=10,000,000 d=96 unit-normalised mixture, 10,000 queries, ranges 1/10/50%, k=10 and 100, "
           "auto-routed; FP32 vs BF16 / FP8 E4M3 storage with FP32 re-rank of 4k",
 }
@@ -96,9 +99,19 @@ def get_index(w, rank, world, barrier, gpu=False):
 def config_dict(name, w, world, nq):
     """The workload description shared by both arms' JSON lines."""
     return {"workload": WORKLOADS[name], "n": w.n, "d": w.d, "queries_per_step": nq,
-            "k": 10 if name == "c2" else [10, 100], "S": w.S, "M": w.M, "efc": w.efc,
+            "k": [10, 100] if name == "c4" else 10, "S": w.S, "M": w.M, "efc": w.efc,
             "parallelism": f"replicas x{world}",
-            "l2": "flushed between steps (256 MiB write); the index is larger than L2"}
+            "l2": "flushed between steps (256 MiB write); " + ("the c1 index (a few MB) fits in L2" if name == "c1"
+                                                               else "the index is larger than L2")}
+
+
+def fraction_groups(name, fractions):
+    """The groups recall is reported by: the range fractions themselves, or for the
+    log-uniform fractions of c3 their decade, labelled by its lower edge."""
+    fractions = np.asarray(fractions, dtype=np.float64)
+    if name != "c3":
+        return fractions
+    return 10.0 ** np.clip(np.floor(np.log10(fractions)), -4, 0)
 
 
 def stratified_rows(fractions, per_fraction):
@@ -146,7 +159,7 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -256,6 +269,7 @@ def reference_arm(args, rank, world):
         return
     over = {k_: v for k_, v in (("n", args.n), ("nq", args.nq)) if v}
     w = make_workload(args.config, seed=args.seed, **over)
+    w.fractions = fraction_groups(args.config, w.fractions)
     path = get_index(w, 0, 1, lambda: None)
     oi = oracle.OracleIndex(path)
     cores = oracle.default_threads()
@@ -330,17 +344,18 @@ def run(args):
     path = get_index(w, rank, world, barrier, gpu=True)
     # the held-out tuning batch: the same recipe from an independent query stream
     tq, tlo, thi, tfr = query_batch(w, args.seed + TUNE_SEED_OFFSET)
+    w.fractions, tfr = fraction_groups(name, w.fractions), fraction_groups(name, tfr)
     # weak scaling: every rank searches its own batch of the same shape
     w.queries, w.lo, w.hi, w.fractions = replicas.rank_batch(w.queries, w.lo, w.hi, w.fractions, rank, args.seed)
     ix = U.Index(path, device=local)
     dev = torch.device("cuda", local)
     nq = len(w.lo)
-    ks = (10,) if name == "c2" else (10, 100)
+    ks = (10, 100) if name == "c4" else (10,)
     # scored rows: every row of the c2 batches; 200 per range fraction of the c4 batches
     # (an exact answer there scans up to 5M rows), with a wider tuning margin for the
     # smaller sample
-    per_f = args.truth_per_fraction if args.truth_per_fraction >= 0 else (0 if name == "c2" else 200)
-    tune_margin = args.tune_margin if args.tune_margin >= 0 else (0.005 if name == "c2" else 0.01)
+    per_f = args.truth_per_fraction if args.truth_per_fraction >= 0 else (200 if name == "c4" else 0)
+    tune_margin = args.tune_margin if args.tune_margin >= 0 else (0.01 if name == "c4" else 0.005)
 
     def on_dev(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -375,6 +390,12 @@ def run(args):
     Sp = np.array([bin(int(m_)).count("1") for m_ in mask])
     Y = pb - pa
     hbm, peak_kind = peaks()
+    bf16_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        pass
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     d = w.d
@@ -457,13 +478,30 @@ def run(args):
         ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in evs]))
         ms_max = replicas.max_over_ranks(ms, world, dev)
         search_ms = phases["search"][0] / max(1, phases["search"][1])
+        tc_used = phases["tcscan"][1] > 0
         parts = algorithmic_bytes(params, counters, k)
+        tc_roof = None
+        if tc_used:
+            # the pre-filter queries ran on the tensor cores, not in the search kernel:
+            # the scan leaves the search kernel's bytes and is rated by its useful work,
+            # 2 d FLOP per (query, in-range row), against the format's dense peak (the
+            # measured bf16 peak times the nominal ratio: tf32 1/2, E4M3 2)
+            del parts["scan"]
+            tc_ms = phases["tcscan"][0] / max(1, phases["tcscan"][1])
+            flops = float(2.0 * d * (pb - pa)[isA].sum())
+            ratio = {U.FP32: 0.5, U.BF16: 1.0, U.FP8E4M3: 2.0}[params.dtype]
+            tf = flops / (tc_ms / 1000.0) / 1e12 if tc_ms > 0 else 0.0
+            tc_roof = {"bound": "tensor", "kernel": "tc_scan_kernel (both passes) + tc_finish", "unit": "TFLOP/s",
+                       "achieved": tf, "peak": ratio * bf16_peak if bf16_peak else None,
+                       "frac": tf / (ratio * bf16_peak) if bf16_peak else None, "ms_per_step": tc_ms,
+                       "useful_flops_per_step": flops,
+                       "peak_source": "measured bf16_tflops x nominal format ratio" if bf16_peak else None}
         alg = sum(parts.values())
         achieved = alg / (search_ms / 1000.0) / 1e9 if search_ms > 0 else 0.0
         nflag, flag_by = flagged(status)
         return dict(ms=ms_max, value=replicas.aggregate_qps(nq, world, ms_max), out=out, wall=wall,
                     timeline=timeline, routed=(int(isA.sum()), int(isC.sum()), int(isB.sum())), recall=gr,
-                    flagged=nflag, flagged_by=flag_by, tc_used=phases["tcscan"][1] > 0,
+                    flagged=nflag, flagged_by=flag_by, tc_used=tc_used, tc_roofline=tc_roof,
                     phases={ph: (v[0] / v[1] if v[1] else 0.0) for ph, v in phases.items()},
                     achieved=achieved, alg=alg, parts=parts)
 
@@ -487,7 +525,7 @@ def run(args):
     def summary(r_, p_):
         return {"value": r_["value"], "ms_per_step": r_["ms"], "recall_by_fraction": fmt_recall(r_["recall"]),
                 "status_flagged": r_["flagged"], "roofline_frac": r_["achieved"] / hbm,
-                "achieved_gbs": r_["achieved"],
+                "achieved_gbs": r_["achieved"], "tensor_core_scan_roofline": r_["tc_roofline"],
                 "routed": {"pre": r_["routed"][0], "hybrid": r_["routed"][1], "post": r_["routed"][2]},
                 "phase_ms_per_step": {ph: round(v, 4) for ph, v in r_["phases"].items() if not ph.startswith("unused")},
                 "params": params_dict(p_)}
@@ -528,7 +566,7 @@ def run(args):
     # whichever tunes faster)
     clocks = Clocks(local)
     params, report = tuned_both_scans({}, 10)
-    clocks.start()
+    clocks.start()  # the measurement's warm-up and timed steps
     m32 = measure(params, args.steps, args.warmup)
     clk = clocks.stop()
     value, ms_max, out = m32["value"], m32["ms"], m32["out"]
@@ -539,7 +577,8 @@ def run(args):
                 "traffic_frac": (traffic / (m32["phases"]["search"] / 1000.0) / 1e9 / hbm)
                 if traffic and m32["phases"]["search"] > 0 else None,
                 "kernel": "batch_kernel (route excluded)", "peak_source": f"{peak_kind} hbm_gbs",
-                "algorithmic_bytes_per_launch": m32["alg"], "algorithmic_bytes_by_strategy": m32["parts"]}
+                "algorithmic_bytes_per_launch": m32["alg"], "algorithmic_bytes_by_strategy": m32["parts"],
+                "tensor_core_scan": m32["tc_roofline"]}
     if traffic is None:
         roofline["traffic_capture"] = ({"bytes": capture["bytes"], "params": capture["params"],
                                         "note": "captured with other parameters"} if capture else None)
@@ -823,7 +862,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS),
-                    help="c2: the default workload; c4: the 10M-row precision shape (its own JSON line)")
+                    help="c2: the default workload; c1, c3 and c4 (the 10M-row precision shape) print their own "
+                         "JSON line")
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--target", type=float, default=0.95)
     ap.add_argument("--tune-margin", type=float, default=-1,
