@@ -37,7 +37,8 @@
 // in lane r; keys beating the current k-th are merged into a sorted top-k.
 //
 // Bounds (checked by reading, against the buffers the launch receives):
-// E[< cand_cap], ann[< ann_cap], vis[< 2^vis_log2], clist[< 32], slots[< 64];
+// E[< cand_cap], ann[< ann_cap], vis[< 2^vis_log2], clist[< 32], slots[< 64] as
+// uint64 (S1 keys) or as ints (post-filter slots; the hybrid S2 table, < kSlotTable);
 // ids come from validated adjacency (0 <= id < n); upper-layer rows exist for
 // every object reached on that layer (validated levels); scan rows lie in
 // [pa, pb) and loads clamp to the last valid row.
@@ -98,6 +99,8 @@ struct WarpMem {
 __host__ __device__ inline int flag_cap(int cand_cap, int ann_cap) {
   return ((cand_cap > ann_cap ? cand_cap : ann_cap) + 15) & ~15;
 }
+
+constexpr int kSlotTable = 128;  // ints of the per-warp slots array (64 uint64)
 
 __host__ __device__ inline int batch_warp_bytes(int cand_cap, int ann_cap, int vis_log2) {
   int b = cand_cap * 8 + ann_cap * 8 + (4 << vis_log2);
@@ -182,6 +185,18 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
   bool truncated = false;
   const int Sp = __popc(mask);
   const int SM = a.S * a.M;
+  // Hybrid S2 selects the same slots in every expansion of the query: the slot and
+  // segment of each selection index are tabled once (up to kSlotTable of them) in
+  // the slots array, which S2 does not otherwise use.
+  const bool tabled = hybrid && !a.s1 && Sp * per <= kSlotTable;
+  if (tabled) {
+    for (int ci = lane; ci < Sp * per; ci += 32) {
+      int sg;
+      const int slot = hybrid_slot(ci, per, mask, a.M, &sg);
+      w.slots[ci] = slot | (sg << 16);
+    }
+    __syncwarp();
+  }
   for (;;) {
     // the nearest unexpanded candidate
     while (cursor < nE) {
@@ -272,7 +287,7 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
         if (hybrid && !a.s1) {
           if (lane < ncand) {
             int sg;
-            prefetch_l2(adj2 + hybrid_slot(lane, per, mask, a.M, &sg));
+            prefetch_l2(adj2 + (tabled ? (w.slots[lane] & 0xffff) : hybrid_slot(lane, per, mask, a.M, &sg)));
           }
         } else if (hybrid) {
           if (lane * 32 < SM) prefetch_l2(adj2 + lane * 32);
@@ -290,11 +305,14 @@ __device__ int search_layer(const BatchArgs& a, const WarpMem& w, const float4 (
         cseg = -1;  // the range test below uses the position
       } else if (ci < ncand) {
         int slot;
-        if (hybrid) {
+        if (tabled) {
+          const int e = w.slots[ci];
+          slot = e & 0xffff;
+          cseg = e >> 16;
+        } else if (hybrid) {
           slot = hybrid_slot(ci, per, mask, a.M, &cseg);
         } else {
-          slot = w.slots[ci];
-          cseg = slot / a.M;
+          slot = w.slots[ci];  // the post-filter tests no range while it traverses
         }
         if (slot < SM) cid = __ldg(adj + slot);
       }
