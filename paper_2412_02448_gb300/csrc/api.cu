@@ -134,7 +134,7 @@ cudaError_t ensure_tc_scratch(Scratch& sc, int64_t nq, int d) {
   if (e == cudaSuccess) e = alloc(sc.tc_tile, 4 * (rows / kTcQueryTile) + 1);
   // at most kTcUnitsPerTile units per tile, one list of kTcCandCap keys per query and unit
   if (e == cudaSuccess) e = alloc(sc.tc_part, (size_t)rows * kTcUnitsPerTile * kTcCandCap);
-  if (e == cudaSuccess) e = alloc(sc.tc_pcnt, (size_t)rows * kTcUnitsPerTile);
+  if (e == cudaSuccess) e = alloc(sc.tc_pcnt, (size_t)rows * kTcUnitsPerTile * 2);
   if (e == cudaSuccess) e = alloc(sc.tc_thr, rows);
   if (e != cudaSuccess) {
     free_tc(sc);

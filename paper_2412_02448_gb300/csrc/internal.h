@@ -75,7 +75,7 @@ struct Scratch {
   void* tc_qb = nullptr;         // their vectors in the scan's format, tc_rows x tc_qrow_bytes
   int32_t* tc_tile = nullptr;    // per tile: first row, row blocks, units, unit offsets (4 x tiles + 1)
   uint64_t* tc_part = nullptr;   // per work unit: kTcQueryTile lists of up to kTcCandCap candidate keys
-  int32_t* tc_pcnt = nullptr;    // per work unit and query: candidates found
+  int32_t* tc_pcnt = nullptr;    // per work unit and query, two column halves: candidates found
   unsigned long long* tc_thr = nullptr;  // per pre-filter query: threshold key shared by its units
   int64_t tc_rows = 0;
   size_t tc_qrow_bytes = 0;

@@ -2,16 +2,16 @@
 // generation tensor cores: queries x in-range vectors is a dense contraction.
 //
 // The pre-filter queries of a batch are bucketed by the first position pa of
-// their range in the attribute order and converted to bfloat16, so that 128
-// consecutive queries (a tile) cover neighbouring rows. The rows of the union of
-// a tile's ranges are split into work units of whole 256-row blocks. For a block,
-// TMA stages 64-column slices of the tile's queries and of the block's
-// attribute-ordered bfloat16 rows (128-byte swizzled), and tcgen05.mma forms
-// D = Q X^T (M = 128 queries, N = 256 rows, K = 16 per instruction, float32
+// their range in the attribute order and converted to the scan's operand format
+// (below), so that 128 consecutive queries (a tile) cover neighbouring rows. The
+// rows of the union of a tile's ranges are split into work units of whole 256-row
+// blocks. For a block, TMA stages 128-byte slices of K of the tile's queries and of
+// the block's attribute-ordered rows (128-byte swizzled), and tcgen05.mma forms
+// D = Q X^T (M = 128 queries, N = 256 rows, 32 bytes of K per instruction, float32
 // accumulation in tensor memory, two accumulators so that the epilogue of one
 // block overlaps the products of the next). Tensor-memory lane q is query q of
-// the tile: thread q turns its query's dot products into squared distances
-// ||x||^2 + ||q||^2 - 2 x.q (norms of the bfloat16 values) and keeps the rows of
+// the tile: its epilogue threads turn its dot products into squared distances
+// ||x||^2 + ||q||^2 - 2 x.q (norms of the operand values) and keep the rows of
 // its range [pa, pb).
 //
 // Two passes over the same tiles select, for every query, the R = rerank_mult * k
@@ -22,8 +22,9 @@
 //      the query's R-th smallest key (R <= 64). The smallest bound over the units
 //      is published with atomicMin as the query's threshold;
 //   2. collecting pass: every in-range row whose key is below the threshold is
-//      appended to the (unit, query) list in global memory (a predicated store,
-//      thread-private count). Typically only about R rows per query qualify.
+//      appended to the (unit, query) list in global memory (a predicated store;
+//      the two column halves fill it from either end with their own counts).
+//      Typically only about R rows per query qualify.
 // A finishing kernel merges each query's lists into the R smallest keys and
 // re-ranks them with exact float32 direct-difference distances against the
 // float32 vectors, as the other reduced-precision paths do. A list that overflowed
@@ -32,17 +33,25 @@
 // d <= 128 every term is an exact integer below 2^24, so the result equals the
 // exact float32 scan.
 //
-// Roles in a CTA of 6 warps: warps 0-3 epilogue (warp w reads tensor-memory
-// lanes 32w..32w+31), warp 4 lane 0 issues TMA loads, warp 5 lane 0 issues the
-// MMAs and owns the tensor-memory allocation. Work units are claimed dynamically:
-// the producer takes the next unit from a global counter and hands its index to the
-// MMA issuer and the epilogue through a small ring in shared memory (index -1 ends
-// the kernel), so CTAs that drew cheap units take more of them. Stages of shared
-// memory (query slice 16 KB + row slice 32 KB per 64 columns of K) are handed over
-// with mbarriers. Every wait is bounded (a number of polls and an elapsed time); a
-// timeout sets an error flag instead of hanging, the waiting warp stops, and the
-// copies and products in flight are drained before the CTA releases its tensor
-// memory and exits.
+// Roles in a CTA of 10 warps: warps 0-7 epilogue (warp w reads tensor-memory
+// lanes 32 (w % 4).. 32 (w % 4) + 31, the queries it owns, over column half w / 4 of
+// each 256-column block, so that two warps share every scheduler's epilogue work),
+// warp 8 lane 0 issues TMA loads, warp 9 lane 0 issues the MMAs and owns the
+// tensor-memory allocation. Work units are claimed dynamically: the producer takes
+// the next unit from a global counter and hands its index to the MMA issuer and the
+// epilogue through a small ring in shared memory (index -1 ends the kernel), so CTAs
+// that drew cheap units take more of them. Stages of shared memory (query slice
+// 16 KB + row slice 32 KB per 128 bytes of K) are handed over with mbarriers. Every
+// wait is bounded (a number of polls and an elapsed time); a timeout sets an error
+// flag instead of hanging, the waiting warp stops, and the copies and products in
+// flight are drained before the CTA releases its tensor memory and exits.
+//
+// The epilogues read a chunk of 32 columns at a time. When every lane of the warp
+// takes either all 32 columns of the chunk or none of them, the chunk runs without a
+// per-column range test: a lane without columns adds NaN to its distances, which
+// neither fminf nor the bound's comparison lets through; the rows' norms and ids come
+// as broadcast vector loads. Only chunks that hold the end of some lane's range take
+// the per-column test.
 //
 // Bounds (checked against the buffers each launch receives): a unit's rows lie
 // in [tile_lo, tile_lo + 256 nb) and loads past n are zero-filled by TMA (rows)
@@ -68,6 +77,10 @@ constexpr int kTcKb = 128;          // bytes of K per stage (one 128-byte swizzl
 constexpr int kTcStages = 4;
 constexpr int kTcCap = kTcCandCap;  // candidate slots per query and work unit
 constexpr int kUnitRing = 4;        // claimed work units handed from the producer to the other roles
+constexpr int kEpiWarps = 8;        // epilogue warps: warp w reads lanes 32 (w % 4).. and column half w / 4
+constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
+constexpr int kTcThreads = 32 * (kEpiWarps + 2);
+constexpr int kHalfCols = kTcRows / 2;  // columns of a block per epilogue warp
 constexpr int kTcRMax = 64;         // candidates kept per query for the re-rank
 constexpr int kBuckets = 1024;
 constexpr int kStageA = kTcQ * kTcKb;     // 16 KB of queries
@@ -117,6 +130,10 @@ struct TcSmem {
   uint64_t full[kTcStages], empty[kTcStages], accf[2], acce[2], drain;
   uint64_t never;  // no thread arrives on it (the timeout test waits on it)
   uint64_t ufull[kUnitRing], uempty[kUnitRing];
+  // bounding pass: the column half 1 warps hand 32 group minima per query at a time
+  // to the half 0 warps of the same tensor-memory lanes (one pair per lane quarter)
+  uint64_t xfull[4], xempty[4];
+  float xch[32][kTcQ];
   int uring[kUnitRing];  // claimed unit (-1: no more units)
   uint32_t tmem;
 };
@@ -245,6 +262,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Element i (a constant after unrolling) of a vector of four.
+__device__ __forceinline__ float f4_at(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+__device__ __forceinline__ int i4_at(const int4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+
 // Ascending bitonic sort of 64 values held in registers (static indices only).
 __device__ __forceinline__ void sort64(float (&v)[64]) {
 #pragma unroll
@@ -286,7 +307,8 @@ struct TcArgs {
   int32_t* tile_units;  // work units the range is split into
   int32_t* unit_off;    // exclusive prefix of tile_units (ntiles + 1)
   uint64_t* part;       // per unit and query of its tile: kTcCap candidate slots
-  int32_t* pcnt;        // per unit and query: candidates found (above kTcCap: overflow)
+  int32_t* pcnt;        // per unit and query, per column half: candidates found (the two
+                        // together above kTcCap: overflow)
   unsigned long long* qthr;  // per query (bucketed order): smallest key known to have R keys at or below it
   int32_t* counters;
   int k, R;
@@ -321,7 +343,7 @@ __device__ __forceinline__ void tile_unit_rows(const TcArgs& a, int t, int u, in
 // key(T, INT_MAX) is above every key of the query's top R (R <= 64): it is published
 // into the shared threshold with atomicMin before the scan pass starts.
 template <int F, bool kBound>
-__global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__ CUtensorMap tmX,
+__global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_constant__ CUtensorMap tmX,
                                                           const __grid_constant__ CUtensorMap tmQ, TcArgs a) {
   constexpr bool kSc = TcTraits<F>::kScaled;
   constexpr int kKc = kTcKb / TcTraits<F>::kElemBytes;  // K elements per stage
@@ -340,17 +362,21 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&s.accf[i], 1);
-      mbar_init(&s.acce[i], 4 * 32);
+      mbar_init(&s.acce[i], kEpiWarps * 32);
     }
     mbar_init(&s.drain, 1);
     mbar_init(&s.never, 1);
     for (int i = 0; i < kUnitRing; ++i) {
       mbar_init(&s.ufull[i], 1);
-      mbar_init(&s.uempty[i], 1 + 4 * 32);  // the MMA issuer and the 128 epilogue threads
+      mbar_init(&s.uempty[i], 1 + kEpiWarps * 32);  // the MMA issuer and the epilogue threads
+    }
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(&s.xfull[i], 32);
+      mbar_init(&s.xempty[i], 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 5) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem)),
                  "r"(2 * kTcRows)
                  : "memory");
@@ -361,7 +387,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s.tmem;
 
-  if (warp == 4) {
+  if (warp == kTmaWarp) {
     // ---- TMA producer (lane 0 issues; the warp stays converged)
     if (lane == 0) {
       bool ok = true;
@@ -405,7 +431,7 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
       if (!ok) atomicExch(err, 1);
     }
     __syncwarp();
-  } else if (warp == 5) {
+  } else if (warp == kMmaWarp) {
     // ---- MMA issuer (lane 0 issues; the warp stays converged)
     if (lane == 0) {
       bool ok = true;
@@ -457,10 +483,17 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
     }
     __syncwarp();
   } else if (kBound) {
-    // ---- bounding epilogue (warps 0-3): group minima per query
-    const int tq = threadIdx.x;
+    // ---- bounding epilogue (warps 0-7): group minima per query. Warp w holds the
+    // queries of tensor-memory lanes 32 (w % 4).. over columns 128 (w / 4).. of each
+    // block; group = column mod 64 (chunk parity x column within the chunk). At the
+    // end of a unit the column-half-1 warp hands its 64 minima to the half-0 warp of
+    // the same lanes, which merges them (a group's minimum over the block is the
+    // smaller of its two halves' minima) and publishes the bound.
+    const int lq = warp & 3, hh = warp >> 2;
+    const int tq = lq * 32 + lane;
+    const int cbase = hh * kHalfCols;
     bool failed = false;
-    long long g = 0;
+    long long g = 0, xuse = 0;
     for (long long useq = 0; !failed; ++useq) {
       const int us = (int)(useq % kUnitRing);
       if (!__all_sync(kFull, mbar_wait(&s.ufull[us], (uint32_t)((useq / kUnitRing) & 1), a.wait_ns))) {
@@ -484,61 +517,63 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         qn = a.aqn[qpos];
         if constexpr (kSc) qs = a.aqs[qpos];
       }
+      const float w2 = 2.f * qs;  // weight of the dot product (times the row's scale for FP8)
       float gm0[32], gm1[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) gm0[j] = gm1[j] = __int_as_float(0x7f800000);
       for (int row0 = r0; row0 < r1; row0 += kTcRows, ++g) {
         const int ab = (int)(g & 1);
-        // norms of the block's rows, two 32-row chunks at a time (lane j holds row
-        // row0 + 32c + j of chunk c); the chunk-pair loop stays rolled, the two chunks
-        // of a pair feed the two halves of the group minima
-        const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);
-        float x0n, x1n, s0n = 1.f, s1n = 1.f;
-        {
-          const int64_t row = (int64_t)row0 + lane;
-          x0n = row < a.n ? __ldg(a.xn + row) : 0.f;
-          x1n = row + 32 < a.n ? __ldg(a.xn + row + 32) : 0.f;
-          if constexpr (kSc) {
-            s0n = row < a.n ? __ldg(a.xs + row) : 0.f;
-            s1n = row + 32 < a.n ? __ldg(a.xs + row + 32) : 0.f;
-          }
-        }
+        const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);  // this query's columns
+        const bool inside = (int64_t)row0 + kTcRows <= a.n;
         if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1), a.wait_ns))) {
           failed = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * kTcRows);
+        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ab * kTcRows + cbase);
 #pragma unroll 1
-        for (int cp = 0; cp < kTcRows / 64; ++cp) {
-          const float x0 = x0n, x1 = x1n, s0 = s0n, s1 = s1n;
-          if (cp + 1 < kTcRows / 64) {
-            const int64_t row = (int64_t)row0 + (cp + 1) * 64 + lane;
-            x0n = row < a.n ? __ldg(a.xn + row) : 0.f;
-            x1n = row + 32 < a.n ? __ldg(a.xn + row + 32) : 0.f;
-            if constexpr (kSc) {
-              s0n = row < a.n ? __ldg(a.xs + row) : 0.f;
-              s1n = row + 32 < a.n ? __ldg(a.xs + row + 32) : 0.f;
-            }
-          }
+        for (int cp = 0; cp < kHalfCols / 64; ++cp) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const int c = 2 * cp + h;
-            const bool need = c1 > c * 32 && c0 < c * 32 + 32;
+            const int lc = 2 * cp + h;          // chunk of this warp's half
+            const int cb = cbase + 32 * lc;     // its first column in the block
+            const bool need = c1 > cb && c0 < cb + 32;
             if (!__any_sync(kFull, need)) continue;
+            const bool full = c0 <= cb && c1 >= cb + 32;
             float v[32];
-            tmem_ld32(taddr + (uint32_t)(c * 32), v);
+            if (__all_sync(kFull, full || !need) && inside) {
+              // every lane takes all 32 columns or none: a lane without columns adds
+              // NaN, which fminf ignores
+              const float qe = need ? qn : __int_as_float(0x7fc00000);
+              float4 x4[8], s4[8];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int col = c * 32 + j;
-              const float xv = __shfl_sync(kFull, h ? x1 : x0, j);
-              float w = 2.f;  // weight of the dot product
-              if constexpr (kSc) w = 2.f * qs * __shfl_sync(kFull, h ? s1 : s0, j);
-              // clamped at 0 once, on the bound (the clamp commutes with min and rank)
-              const float dist = xv + qn - w * v[j];
-              const bool in = col >= c0 && col < c1;
-              if (h) gm1[j] = in ? fminf(gm1[j], dist) : gm1[j];
-              else gm0[j] = in ? fminf(gm0[j], dist) : gm0[j];
+              for (int i = 0; i < 8; ++i) {
+                x4[i] = __ldg(reinterpret_cast<const float4*>(a.xn + row0 + cb) + i);
+                if constexpr (kSc) s4[i] = __ldg(reinterpret_cast<const float4*>(a.xs + row0 + cb) + i);
+              }
+              tmem_ld32(taddr + (uint32_t)(32 * lc), v);
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const float xv = f4_at(x4[j >> 2], j & 3);
+                float w = 2.f;
+                if constexpr (kSc) w = w2 * f4_at(s4[j >> 2], j & 3);
+                const float dist = fmaf(-w, v[j], xv + qe);
+                if (h) gm1[j] = fminf(gm1[j], dist);
+                else gm0[j] = fminf(gm0[j], dist);
+              }
+            } else {
+              tmem_ld32(taddr + (uint32_t)(32 * lc), v);
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const int64_t row = (int64_t)row0 + cb + j;
+                const float xv = row < a.n ? __ldg(a.xn + row) : 0.f;
+                float w = 2.f;
+                if constexpr (kSc) w = w2 * (row < a.n ? __ldg(a.xs + row) : 0.f);
+                const float dist = fmaf(-w, v[j], xv + qn);
+                const bool in = cb + j >= c0 && cb + j < c1;
+                if (h) gm1[j] = in ? fminf(gm1[j], dist) : gm1[j];
+                else gm0[j] = in ? fminf(gm0[j], dist) : gm0[j];
+              }
             }
           }
         }
@@ -546,29 +581,64 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         mbar_arrive(&s.acce[ab]);
       }
       if (failed) break;
-      // the R-th smallest of the 64 group minima: R distinct rows lie at or below it
-      float v64[64];
+      // the half-1 warp hands its minima over, 32 at a time
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        v64[j] = gm0[j];
-        v64[32 + j] = gm1[j];
+      for (int r = 0; r < 2; ++r, ++xuse) {
+        if (hh) {
+          if (xuse > 0 &&
+              !__all_sync(kFull, mbar_wait(&s.xempty[lq], (uint32_t)((xuse - 1) & 1), a.wait_ns))) {
+            failed = true;
+            break;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) s.xch[j][tq] = r ? gm1[j] : gm0[j];
+          mbar_arrive(&s.xfull[lq]);
+        } else {
+          if (!__all_sync(kFull, mbar_wait(&s.xfull[lq], (uint32_t)(xuse & 1), a.wait_ns))) {
+            failed = true;
+            break;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float o = s.xch[j][tq];
+            if (r) gm1[j] = fminf(gm1[j], o);
+            else gm0[j] = fminf(gm0[j], o);
+          }
+          mbar_arrive(&s.xempty[lq]);
+        }
       }
-      sort64(v64);
-      float T = __int_as_float(0x7f800000);
+      if (failed) break;
+      if (hh == 0) {
+        // the R-th smallest of the 64 group minima: R distinct rows lie at or below it
+        float v64[64];
 #pragma unroll
-      for (int i = 0; i < 64; ++i)
-        if (i == a.R - 1) T = v64[i];
-      if (qv && T < __int_as_float(0x7f800000))
-        atomicMin(a.qthr + qpos, (unsigned long long)make_key(fmaxf(T, 0.f), 0x7fffffff));
+        for (int j = 0; j < 32; ++j) {
+          v64[j] = gm0[j];
+          v64[32 + j] = gm1[j];
+        }
+        sort64(v64);
+        float T = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int i = 0; i < 64; ++i)
+          if (i == a.R - 1) T = v64[i];
+        // clamped at 0 once, on the bound (the clamp commutes with min and rank)
+        if (qv && T < __int_as_float(0x7f800000))
+          atomicMin(a.qthr + qpos, (unsigned long long)make_key(fmaxf(T, 0.f), 0x7fffffff));
+      }
     }
     if (failed) atomicExch(err, 1);
   } else {
-    // ---- collecting epilogue (warps 0-3): thread q = query q of the tile =
-    // tensor-memory lane q. Every in-range row whose key is below the query's bound
-    // is appended to the (unit, query) list in global memory; the count goes on past
-    // kTcCap so that the finishing kernel can see an overflow. The warps run
-    // independently; a timed-out wait ends the warp's loop (decided warp-wide).
-    const int tq = threadIdx.x;
+    // ---- collecting epilogue (warps 0-7): lane q of warp w is query 32 (w % 4) + q
+    // of the tile (its tensor-memory lane) over columns 128 (w / 4).. of each block.
+    // Every in-range row whose key is below the query's bound is appended to the
+    // (unit, query) list in global memory: the column-half-0 thread fills it from the
+    // front, the half-1 thread from the back, each with its own count, which goes on
+    // past the list's end so that the finishing kernel can see an overflow (the two
+    // counts together above kTcCap). The warps run independently; a timed-out wait
+    // ends the warp's loop (decided warp-wide).
+    const int lq = warp & 3, hh = warp >> 2;
+    const int tq = lq * 32 + lane;
+    const int cbase = hh * kHalfCols;
     bool failed = false;
     long long g = 0;
     // timeout test: this wait runs out after wait_ns; the producer's and the MMA
@@ -599,58 +669,75 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         if constexpr (kSc) qs = a.aqs[qpos];
         thr = *reinterpret_cast<volatile unsigned long long*>(a.qthr + qpos);
       }
-      // the bound's distance (+inf without a bound: every row qualifies)
+      const float w2 = 2.f * qs;
+      // the bound's distance (+inf without a bound: every row qualifies); the bound is
+      // the key (tdist, INT_MAX), so a row's key is below it exactly when its
+      // distance is at most tdist
       const float tdist = thr == kKeyMax ? __int_as_float(0x7f800000) : key_dist(thr);
-      uint64_t* list = a.part + ((int64_t)x * kTcQ + tq) * kTcCap;
-      int cnt = 0;
+      uint64_t* const list = a.part + ((int64_t)x * kTcQ + tq) * kTcCap;
+      uint64_t* wp = hh ? list + (kTcCap - 1) : list;  // next slot
+      const int step = hh ? -1 : 1;
+      int cnt = 0;  // keys found (may pass kTcCap; wp stops at the list's end)
       for (int row0 = r0; row0 < r1; row0 += kTcRows, ++g) {
         const int ab = (int)(g & 1);
-        // squared norms and ids of the block's rows, one 32-row chunk at a time: lane j
-        // holds row row0 + 32c + j of chunk c; the next chunk's loads are issued before
-        // the current chunk is processed (the chunk loop stays rolled: a compact body)
         const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);  // this query's columns
-        float xnext, snext = 1.f;
-        int32_t inext;
-        {
-          const int64_t row = (int64_t)row0 + lane;
-          xnext = row < a.n ? __ldg(a.xn + row) : 0.f;
-          inext = row < a.n ? __ldg(a.sorted_ids + row) : 0;
-          if constexpr (kSc) snext = row < a.n ? __ldg(a.xs + row) : 0.f;
-        }
+        const bool inside = (int64_t)row0 + kTcRows <= a.n;
         if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1), a.wait_ns))) {
           failed = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * kTcRows);
+        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ab * kTcRows + cbase);
 #pragma unroll 1
-        for (int c = 0; c < kTcRows / 32; ++c) {
-          const float xc = xnext, sc = snext;
-          const int32_t ic = inext;
-          if (c + 1 < kTcRows / 32) {
-            const int64_t row = (int64_t)row0 + (c + 1) * 32 + lane;
-            xnext = row < a.n ? __ldg(a.xn + row) : 0.f;
-            inext = row < a.n ? __ldg(a.sorted_ids + row) : 0;
-            if constexpr (kSc) snext = row < a.n ? __ldg(a.xs + row) : 0.f;
-          }
-          const bool need = c1 > c * 32 && c0 < c * 32 + 32;
+        for (int lc = 0; lc < kHalfCols / 32; ++lc) {
+          const int cb = cbase + 32 * lc;
+          const bool need = c1 > cb && c0 < cb + 32;
           if (!__any_sync(kFull, need)) continue;
+          const bool full = c0 <= cb && c1 >= cb + 32;
           float v[32];
-          tmem_ld32(taddr + (uint32_t)(c * 32), v);
-          // this query's columns of the chunk: [jlo, jhi)
-          const int jlo = c0 - c * 32, jhi = c1 - c * 32;
+          if (__all_sync(kFull, (full || !need) && cnt + 32 <= kTcCap) && inside) {
+            // every lane takes all 32 columns or none (NaN compares false), and has
+            // room for 32 more keys
+            const float qe = need ? qn : __int_as_float(0x7fc00000);
+            float4 x4[8], s4[8];
+            int4 i4[8];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float xv = __shfl_sync(kFull, xc, j);
-            const int32_t idj = __shfl_sync(kFull, ic, j);
-            float w = 2.f;  // weight of the dot product
-            if constexpr (kSc) w = 2.f * qs * __shfl_sync(kFull, sc, j);
-            const float dist = fmaxf(xv + qn - w * v[j], 0.f);
-            // the bound is the key (tdist, INT_MAX): a row's key is below it exactly
-            // when its distance is at most tdist
-            if (j >= jlo && j < jhi && dist <= tdist) {
-              if (cnt < kTcCap) list[cnt] = make_key(dist, idj);
-              ++cnt;
+            for (int i = 0; i < 8; ++i) {
+              x4[i] = __ldg(reinterpret_cast<const float4*>(a.xn + row0 + cb) + i);
+              i4[i] = __ldg(reinterpret_cast<const int4*>(a.sorted_ids + row0 + cb) + i);
+              if constexpr (kSc) s4[i] = __ldg(reinterpret_cast<const float4*>(a.xs + row0 + cb) + i);
+            }
+            tmem_ld32(taddr + (uint32_t)(32 * lc), v);
+            uint64_t* const w0 = wp;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float xv = f4_at(x4[j >> 2], j & 3);
+              float w = 2.f;
+              if constexpr (kSc) w = w2 * f4_at(s4[j >> 2], j & 3);
+              const float dist = fmaf(-w, v[j], xv + qe);
+              const bool hit = dist <= tdist;
+              if (hit) *wp = make_key(fmaxf(dist, 0.f), i4_at(i4[j >> 2], j & 3));
+              wp += hit ? step : 0;
+            }
+            cnt += (int)(hh ? w0 - wp : wp - w0);
+          } else {
+            tmem_ld32(taddr + (uint32_t)(32 * lc), v);
+            // this query's columns of the chunk: [jlo, jhi)
+            const int jlo = c0 - cb, jhi = c1 - cb;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int64_t row = (int64_t)row0 + cb + j;
+              const float xv = row < a.n ? __ldg(a.xn + row) : 0.f;
+              float w = 2.f;
+              if constexpr (kSc) w = w2 * (row < a.n ? __ldg(a.xs + row) : 0.f);
+              const float dist = fmaf(-w, v[j], xv + qn);
+              if (j >= jlo && j < jhi && dist <= tdist) {
+                if (cnt < kTcCap) {
+                  *wp = make_key(fmaxf(dist, 0.f), row < a.n ? __ldg(a.sorted_ids + row) : 0);
+                  wp += step;
+                }
+                ++cnt;
+              }
             }
           }
         }
@@ -658,13 +745,13 @@ __global__ void __launch_bounds__(192, 1) tc_scan_kernel(const __grid_constant__
         mbar_arrive(&s.acce[ab]);
       }
       if (failed) break;
-      a.pcnt[(int64_t)x * kTcQ + tq] = cnt;
+      a.pcnt[2 * ((int64_t)x * kTcQ + tq) + hh] = cnt;
     }
     if (failed) atomicExch(err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 5) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcRows)
                  : "memory");
@@ -692,9 +779,13 @@ __global__ void tc_tile_prep(TcArgs a) {
       lo = min(lo, __shfl_xor_sync(kFull, lo, off));
       hi = max(hi, __shfl_xor_sync(kFull, hi, off));
     }
+    // the union starts on a multiple of 4 rows, so that the epilogues read the
+    // blocks' norms and ids as aligned vectors of four
+    const bool none = lo == INT_MAX;
+    lo &= ~3;
     if (lane == 0) {
-      a.tile_lo[t] = lo == INT_MAX ? 0 : lo;
-      a.tile_nb[t] = lo == INT_MAX ? 0 : (hi - lo + kTcRows - 1) / kTcRows;
+      a.tile_lo[t] = none ? 0 : lo;
+      a.tile_nb[t] = none ? 0 : (hi - lo + kTcRows - 1) / kTcRows;
     }
   }
 }
@@ -779,7 +870,8 @@ __global__ void __launch_bounds__(128) tc_finish(TcArgs a) {
       int r0, r1;
       tile_unit_rows(a, t, u, &r0, &r1);
       if (r1 <= pa || r0 >= pb) continue;
-      overflow = overflow || a.pcnt[(int64_t)(u0 + u) * kTcQ + j] > kTcCap;
+      const int64_t li = (int64_t)(u0 + u) * kTcQ + j;
+      overflow = overflow || a.pcnt[2 * li] + a.pcnt[2 * li + 1] > kTcCap;
     }
     int nt = 0;
     if (failed || pb <= pa) {
@@ -790,10 +882,12 @@ __global__ void __launch_bounds__(128) tc_finish(TcArgs a) {
         tile_unit_rows(a, t, u, &r0, &r1);
         if (r1 <= pa || r0 >= pb) continue;
         const int64_t li = (int64_t)(u0 + u) * kTcQ + j;
-        const int c = a.pcnt[li];
+        // keys from the front (column half 0) and from the back (half 1)
+        const int cf = a.pcnt[2 * li], c = cf + a.pcnt[2 * li + 1];
         const uint64_t* src = a.part + li * kTcCap;
         for (int off = 0; off < c; off += 32) {
-          const uint64_t key = off + lane < c ? src[off + lane] : kKeyMax;
+          const int i = off + lane;
+          const uint64_t key = i < cf ? src[i] : i < c ? src[kTcCap - 1 - (i - cf)] : kKeyMax;
           nt = topk_offer(top[warp], nt, a.R, key, R[warp]);
         }
       }
@@ -1011,10 +1105,10 @@ cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, 
     e = cudaFuncSetAttribute(tc_scan_kernel<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // bounding pass (each query's bound), then the collecting pass
-  tc_scan_kernel<F, true><<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
+  tc_scan_kernel<F, true><<<ix.num_sms, kTcThreads, smem, st>>>(tmX, tmQ, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  tc_scan_kernel<F, false><<<ix.num_sms, 192, smem, st>>>(tmX, tmQ, a);
+  tc_scan_kernel<F, false><<<ix.num_sms, kTcThreads, smem, st>>>(tmX, tmQ, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // FP32 re-rank with the row-width variants of the search kernel; an overflowed

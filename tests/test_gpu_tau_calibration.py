@@ -40,6 +40,7 @@ def test_tau_calibration_turning_points(U, c1_index):
         assert a["y_hi"] < b["y_lo"]
     # c1's attributes are a permutation of the domain: every range holds an object (Y >= 1)
     assert sum(r["queries"] for r in table) == 1024
+    assert all(r["timed_rows"] >= 8192 for r in table)
     assert (ta, tb) == autotune.turning_points(table, ix.n)
     assert 0 < ta < tb <= ix.n + 1
     assert table[0]["ms_pre"] <= table[0]["ms_hybrid"]
