@@ -190,6 +190,14 @@ cudaError_t upload(T** dst, const T* src, uint64_t elems) {
   return e;
 }
 
+// An attribute-ordered per-row array with kTcRowPad zero entries past the last row.
+template <class T>
+cudaError_t alloc_rows(T** dst, uint64_t n) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), (n + kTcRowPad) * sizeof(T));
+  if (e == cudaSuccess) e = cudaMemset(*dst, 0, (n + kTcRowPad) * sizeof(T));
+  return e;
+}
+
 }  // namespace
 
 void free_scratch(Scratch& sc);
@@ -341,7 +349,8 @@ extern "C" int unify_load_index(const char* path, int device, unify_index_t** ou
   int64_t* d_attr = nullptr;
   cudaError_t e = upload(&ix.vec, vsrc, n * ix.dp);
   if (e == cudaSuccess) e = upload(&d_attr, attr, n);
-  if (e == cudaSuccess) e = upload(&ix.sorted_ids, sorted_ids, n);
+  if (e == cudaSuccess) e = alloc_rows(&ix.sorted_ids, n);
+  if (e == cudaSuccess) e = cudaMemcpy(ix.sorted_ids, sorted_ids, n * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = upload(&ix.upper_base, upper_base, n);
   if (e == cudaSuccess) e = upload(&ix.adj0, adj0, n * SM);
   if (e == cudaSuccess) e = upload(&ix.gmask0, gmask0, n * ix.W);
@@ -358,10 +367,10 @@ extern "C" int unify_load_index(const char* path, int device, unify_index_t** ou
   if (e == cudaSuccess) e = cudaMalloc(&ix.vt_fp8, n * dp4 * 4);
   if (e == cudaSuccess) e = cudaMalloc(&ix.vts_fp8, n * dp4 * 4);
   if (e == cudaSuccess) e = cudaMalloc(&ix.scale_fp8, n * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&ix.scale_fp8_sorted, n * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&ix.xn_bf16_sorted, n * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&ix.xn_f32_sorted, n * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&ix.xn_fp8_sorted, n * sizeof(float));
+  if (e == cudaSuccess) e = alloc_rows(&ix.scale_fp8_sorted, n);
+  if (e == cudaSuccess) e = alloc_rows(&ix.xn_bf16_sorted, n);
+  if (e == cudaSuccess) e = alloc_rows(&ix.xn_f32_sorted, n);
+  if (e == cudaSuccess) e = alloc_rows(&ix.xn_fp8_sorted, n);
   if (e == cudaSuccess) {
     derive_kernel<<<1024, 256>>>(ix.vec, ix.sorted_ids, d_attr, ix.n, ix.dp, ix.vec_sorted, ix.sorted_attr, ix.pos);
     e = cudaGetLastError();

@@ -127,7 +127,12 @@ struct TcSmem {
   // 1024-byte aligned stages first
   uint8_t a[kTcStages][kStageA];
   uint8_t b[kTcStages][kStageB];
-  uint64_t full[kTcStages], empty[kTcStages], accf[2], acce[2], drain;
+  // per accumulator: the block's squared norms, ids and (FP8) scales, copied by the
+  // producer when it starts the block's loads; mfull[i] completes when they landed
+  float mxn[2][kTcRows];
+  int32_t mid[2][kTcRows];
+  float mxs[2][kTcRows];
+  uint64_t full[kTcStages], empty[kTcStages], accf[2], acce[2], drain, mfull[2];
   uint64_t never;  // no thread arrives on it (the timeout test waits on it)
   uint64_t ufull[kUnitRing], uempty[kUnitRing];
   // bounding pass: the column half 1 warps hand 32 group minima per query at a time
@@ -189,6 +194,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
     if ((i & 63) == 63 && global_ns() - t0 > limit_ns) return false;
   }
   return false;
+}
+
+// Untiled bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// into shared memory, completing on the mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
@@ -347,6 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
                                                           const __grid_constant__ CUtensorMap tmQ, TcArgs a) {
   constexpr bool kSc = TcTraits<F>::kScaled;
   constexpr int kKc = kTcKb / TcTraits<F>::kElemBytes;  // K elements per stage
+  constexpr uint32_t kMetaBytes = kTcRows * 4 * (1 + (kBound ? 0 : 1) + (kSc ? 1 : 0));
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023));
   const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -366,6 +381,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
     }
     mbar_init(&s.drain, 1);
     mbar_init(&s.never, 1);
+    for (int i = 0; i < 2; ++i) mbar_init(&s.mfull[i], 1);
     for (int i = 0; i < kUnitRing; ++i) {
       mbar_init(&s.ufull[i], 1);
       mbar_init(&s.uempty[i], 1 + kEpiWarps * 32);  // the MMA issuer and the epilogue threads
@@ -391,7 +407,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
     // ---- TMA producer (lane 0 issues; the warp stays converged)
     if (lane == 0) {
       bool ok = true;
-      long long it = 0;
+      long long it = 0, gb = 0;
       for (long long useq = 0; ok; ++useq) {
         // claim the next unit and hand it to the other roles
         const int us = (int)(useq % kUnitRing);
@@ -408,7 +424,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
         const int t = unit_tile(a, ntiles, x);
         int r0, r1;
         tile_unit_rows(a, t, x - a.unit_off[t], &r0, &r1);
-        for (int row0 = r0; row0 < r1 && ok; row0 += kTcRows)
+        for (int row0 = r0; row0 < r1 && ok; row0 += kTcRows, ++gb) {
+          // the block's norms, ids and scales, once the epilogue is done with the
+          // block that used this accumulator before (rows below n + kTcRowPad: the
+          // arrays' zero padding covers the last block)
+          const int mb = (int)(gb & 1);
+          if (gb >= 2 && !mbar_wait(&s.acce[mb], (uint32_t)(((gb >> 1) - 1) & 1), a.wait_ns)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&s.mfull[mb], kMetaBytes);
+          bulk_load(s.mxn[mb], a.xn + row0, kTcRows * 4, &s.mfull[mb]);
+          if constexpr (!kBound) bulk_load(s.mid[mb], a.sorted_ids + row0, kTcRows * 4, &s.mfull[mb]);
+          if constexpr (kSc) bulk_load(s.mxs[mb], a.xs + row0, kTcRows * 4, &s.mfull[mb]);
           for (int kc = 0; kc < a.KC; ++kc, ++it) {
             const int st = (int)(it % kTcStages);
             const long long u = it / kTcStages;
@@ -420,6 +448,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
             tma_load_2d(s.a[st], &tmQ, kc * kKc, t * kTcQ, &s.full[st]);
             tma_load_2d(s.b[st], &tmX, kc * kKc, row0, &s.full[st]);
           }
+        }
       }
       // no copy may still be landing in shared memory when the CTA leaves: wait
       // (bounded) for the last load issued into every stage
@@ -427,6 +456,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
         if (it <= st) continue;
         const long long last_use = (it - 1 - st) / kTcStages;
         if (!mbar_wait(&s.full[st], (uint32_t)(last_use & 1), kWaitNs)) ok = false;
+      }
+      for (int mb = 0; mb < 2; ++mb) {
+        if (gb <= mb) continue;
+        const long long last_use = (gb - 1 - mb) / 2;
+        if (!mbar_wait(&s.mfull[mb], (uint32_t)(last_use & 1), kWaitNs)) ok = false;
       }
       if (!ok) atomicExch(err, 1);
     }
@@ -524,13 +558,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
       for (int row0 = r0; row0 < r1; row0 += kTcRows, ++g) {
         const int ab = (int)(g & 1);
         const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);  // this query's columns
-        const bool inside = (int64_t)row0 + kTcRows <= a.n;
-        if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1), a.wait_ns))) {
+        if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1), a.wait_ns) &&
+                                   mbar_wait(&s.mfull[ab], (uint32_t)((g >> 1) & 1), a.wait_ns))) {
           failed = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ab * kTcRows + cbase);
+        const float* mxn = s.mxn[ab];
+        const float* mxs = s.mxs[ab];
 #pragma unroll 1
         for (int cp = 0; cp < kHalfCols / 64; ++cp) {
 #pragma unroll
@@ -541,15 +577,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
             if (!__any_sync(kFull, need)) continue;
             const bool full = c0 <= cb && c1 >= cb + 32;
             float v[32];
-            if (__all_sync(kFull, full || !need) && inside) {
+            if (__all_sync(kFull, full || !need)) {
               // every lane takes all 32 columns or none: a lane without columns adds
               // NaN, which fminf ignores
               const float qe = need ? qn : __int_as_float(0x7fc00000);
               float4 x4[8], s4[8];
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                x4[i] = __ldg(reinterpret_cast<const float4*>(a.xn + row0 + cb) + i);
-                if constexpr (kSc) s4[i] = __ldg(reinterpret_cast<const float4*>(a.xs + row0 + cb) + i);
+                x4[i] = reinterpret_cast<const float4*>(mxn + cb)[i];
+                if constexpr (kSc) s4[i] = reinterpret_cast<const float4*>(mxs + cb)[i];
               }
               tmem_ld32(taddr + (uint32_t)(32 * lc), v);
 #pragma unroll
@@ -565,10 +601,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
               tmem_ld32(taddr + (uint32_t)(32 * lc), v);
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
-                const int64_t row = (int64_t)row0 + cb + j;
-                const float xv = row < a.n ? __ldg(a.xn + row) : 0.f;
+                const float xv = mxn[cb + j];
                 float w = 2.f;
-                if constexpr (kSc) w = w2 * (row < a.n ? __ldg(a.xs + row) : 0.f);
+                if constexpr (kSc) w = w2 * mxs[cb + j];
                 const float dist = fmaf(-w, v[j], xv + qn);
                 const bool in = cb + j >= c0 && cb + j < c1;
                 if (h) gm1[j] = in ? fminf(gm1[j], dist) : gm1[j];
@@ -681,13 +716,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
       for (int row0 = r0; row0 < r1; row0 += kTcRows, ++g) {
         const int ab = (int)(g & 1);
         const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);  // this query's columns
-        const bool inside = (int64_t)row0 + kTcRows <= a.n;
-        if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1), a.wait_ns))) {
+        if (!__all_sync(kFull, mbar_wait(&s.accf[ab], (uint32_t)((g >> 1) & 1), a.wait_ns) &&
+                                   mbar_wait(&s.mfull[ab], (uint32_t)((g >> 1) & 1), a.wait_ns))) {
           failed = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ab * kTcRows + cbase);
+        const float* mxn = s.mxn[ab];
+        const int32_t* mid = s.mid[ab];
+        const float* mxs = s.mxs[ab];
 #pragma unroll 1
         for (int lc = 0; lc < kHalfCols / 32; ++lc) {
           const int cb = cbase + 32 * lc;
@@ -695,7 +733,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
           if (!__any_sync(kFull, need)) continue;
           const bool full = c0 <= cb && c1 >= cb + 32;
           float v[32];
-          if (__all_sync(kFull, (full || !need) && cnt + 32 <= kTcCap) && inside) {
+          if (__all_sync(kFull, (full || !need) && cnt + 32 <= kTcCap)) {
             // every lane takes all 32 columns or none (NaN compares false), and has
             // room for 32 more keys
             const float qe = need ? qn : __int_as_float(0x7fc00000);
@@ -703,9 +741,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
             int4 i4[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              x4[i] = __ldg(reinterpret_cast<const float4*>(a.xn + row0 + cb) + i);
-              i4[i] = __ldg(reinterpret_cast<const int4*>(a.sorted_ids + row0 + cb) + i);
-              if constexpr (kSc) s4[i] = __ldg(reinterpret_cast<const float4*>(a.xs + row0 + cb) + i);
+              x4[i] = reinterpret_cast<const float4*>(mxn + cb)[i];
+              i4[i] = reinterpret_cast<const int4*>(mid + cb)[i];
+              if constexpr (kSc) s4[i] = reinterpret_cast<const float4*>(mxs + cb)[i];
             }
             tmem_ld32(taddr + (uint32_t)(32 * lc), v);
             uint64_t* const w0 = wp;
@@ -726,14 +764,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
             const int jlo = c0 - cb, jhi = c1 - cb;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              const int64_t row = (int64_t)row0 + cb + j;
-              const float xv = row < a.n ? __ldg(a.xn + row) : 0.f;
+              const float xv = mxn[cb + j];
               float w = 2.f;
-              if constexpr (kSc) w = w2 * (row < a.n ? __ldg(a.xs + row) : 0.f);
+              if constexpr (kSc) w = w2 * mxs[cb + j];
               const float dist = fmaf(-w, v[j], xv + qn);
               if (j >= jlo && j < jhi && dist <= tdist) {
                 if (cnt < kTcCap) {
-                  *wp = make_key(fmaxf(dist, 0.f), row < a.n ? __ldg(a.sorted_ids + row) : 0);
+                  *wp = make_key(fmaxf(dist, 0.f), mid[cb + j]);
                   wp += step;
                 }
                 ++cnt;
