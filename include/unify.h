@@ -86,7 +86,8 @@ typedef struct {
   int m;               /* hybrid neighbours visited per expanded object, default 16 (S2:
                           ceil(m / S') per intersected chunk; S1: the m nearest) */
   int ef_post;         /* Algorithm 1 layer-0 beam of Strategy B; <= 0 means ef */
-  int rerank_mult;     /* BF16/FP8: re-rank rerank_mult * k candidates in FP32, default 4 */
+  int rerank_mult;     /* BF16/FP8 storage: re-rank rerank_mult * k candidates in FP32 (the
+                          tensor-core scan: see tc_scan), default 4 */
   unify_dtype_t dtype; /* storage read by traversal and scan, default UNIFY_FP32 */
   int64_t tau_a;       /* Strategy A when Y <= tau_a; < 0 means floor(0.01 n) */
   int64_t tau_b;       /* Strategy B when Y >= tau_b; < 0 means floor(0.5 n) */
@@ -99,11 +100,14 @@ typedef struct {
                           80 (24 warps) or 64 (32 warps, smaller distance groups); default 128.
                           More resident warps hide more memory latency when shared memory
                           (cand_cap, visited_cap, ef) also fits. */
-  int tc_scan;         /* 1: with UNIFY_BF16 storage, Strategy A queries are scanned on the
-                          tensor cores (tcgen05 MMA over TMA-staged row tiles shared by 128
-                          queries, top rerank_mult * k by bf16 distance, FP32 re-rank) when
-                          d is a multiple of 8, d <= 1024 and rerank_mult * k <= 64;
-                          0 (default): warp scan. 2: test of the scan's failure path only:
+  int tc_scan;         /* 1: Strategy A queries are scanned on the tensor cores (tcgen05 MMA
+                          over TMA-staged row tiles shared by 128 queries; bf16 operands for
+                          UNIFY_BF16 storage, tf32 for UNIFY_FP32, E4M3 for UNIFY_FP8E4M3; the
+                          top R by that distance re-ranked in FP32, R = rerank_mult * k up
+                          to 64 and R = k past that) when d <= 1024, k <= 128 and the rows
+                          suit TMA (the padded
+                          d a multiple of 8 for BF16, of 16 for FP8); otherwise, and with
+                          0 (default), the warp scan. 2: test of the scan's failure path only:
                           the scan's collecting pass waits on a barrier that nothing arrives
                           at, every wait between its roles is limited to 50 ms, the waits run
                           out, and the pre-filter rows come back empty with UNIFY_Q_LIMIT

@@ -95,7 +95,7 @@ constexpr int kTcQueryTile = 128;   // pre-filter queries per tensor-core tile
 constexpr int kTcRowPad = 256;      // zero entries past row n of the attribute-ordered norms, scales
                                     // and ids (the tensor-core scan copies whole 256-row blocks)
 constexpr int kTcUnitsPerTile = 16;  // at most this many work units per tile
-constexpr int kTcCandCap = 128;      // candidate slots per query and work unit
+constexpr int kTcCandCap = 256;      // candidate slots per query and work unit
 
 // counters[] layout
 enum {

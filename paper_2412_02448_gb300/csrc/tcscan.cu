@@ -14,13 +14,15 @@
 // ||x||^2 + ||q||^2 - 2 x.q (norms of the operand values) and keep the rows of
 // its range [pa, pb).
 //
-// Two passes over the same tiles select, for every query, the R = rerank_mult * k
-// smallest keys (distance, id) without any per-query heap:
-//   1. bounding pass: per query and unit, the minimum distance of each of 64
-//      disjoint row groups (group = chunk parity x column, in registers); the R-th
-//      smallest of those 64 minima has R distinct rows at or below it, so it bounds
-//      the query's R-th smallest key (R <= 64). The smallest bound over the units
-//      is published with atomicMin as the query's threshold;
+// Two passes over the same tiles select, for every query, the R smallest keys
+// (distance, id), R = rerank_mult * k up to 64 and k past that (k <= 128), without any
+// per-query heap:
+//   1. bounding pass: per query and unit, the minimum distance of each of 128
+//      disjoint row groups (column half x chunk parity x column, in registers of
+//      the two threads that hold the query); the R-th smallest of those 128 minima
+//      has R distinct rows at or below it, so it bounds the query's R-th smallest
+//      key (R <= 128). The smallest bound over the units is published with
+//      atomicMin as the query's threshold;
 //   2. collecting pass: every in-range row whose key is below the threshold is
 //      appended to the (unit, query) list in global memory (a predicated store;
 //      the two column halves fill it from either end with their own counts).
@@ -61,6 +63,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -81,7 +84,8 @@ constexpr int kEpiWarps = 8;        // epilogue warps: warp w reads lanes 32 (w 
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kTcThreads = 32 * (kEpiWarps + 2);
 constexpr int kHalfCols = kTcRows / 2;  // columns of a block per epilogue warp
-constexpr int kTcRMax = 64;         // candidates kept per query for the re-rank
+constexpr int kTcRMax = 128;        // candidates kept per query for the re-rank, at most
+constexpr int kTcRTight = 64;       // up to here the bound stays near R rows; past it the scan keeps k
 constexpr int kBuckets = 1024;
 constexpr int kStageA = kTcQ * kTcKb;     // 16 KB of queries
 constexpr int kStageB = kTcRows * kTcKb;  // 32 KB of rows
@@ -351,11 +355,12 @@ __device__ __forceinline__ void tile_unit_rows(const TcArgs& a, int t, int u, in
 }
 
 // kBound = true: the bounding pass. Its epilogue keeps, per query, the minimum
-// distance of 64 disjoint groups of the query's rows in the unit (group = chunk
-// parity x column within the chunk, registers with static indices). The largest of
-// those 64 minima is at least the query's 64th-smallest distance in the unit, so
-// key(T, INT_MAX) is above every key of the query's top R (R <= 64): it is published
-// into the shared threshold with atomicMin before the scan pass starts.
+// distance of 128 disjoint groups of the query's rows in the unit (column half x
+// chunk parity x column within the chunk; each of the query's two threads holds its
+// half's 64 in registers with static indices). The R-th smallest T of the 128
+// minima has R distinct rows at or below it, so key(T, INT_MAX) is above every key
+// of the query's top R (R <= 128): it is published into the query's threshold with
+// atomicMin before the collecting pass starts.
 template <int F, bool kBound>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_constant__ CUtensorMap tmX,
                                                           const __grid_constant__ CUtensorMap tmQ, TcArgs a) {
@@ -616,8 +621,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
         mbar_arrive(&s.acce[ab]);
       }
       if (failed) break;
-      // the half-1 warp hands its minima over, 32 at a time
+      // 128 disjoint groups: 64 per column half. Both halves sort their minima; the
+      // half-1 warp hands its sorted minima to the half-0 warp, 32 at a time, which
+      // takes the R-th smallest of the 128 as the bound: over the splits that take i
+      // of its own smallest and R - i of the other half's, the smallest of the larger
+      // of the two last values taken. R distinct rows lie at or below it.
+      float v64[64];
 #pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        v64[j] = gm0[j];
+        v64[32 + j] = gm1[j];
+      }
+      sort64(v64);
+      float T = __int_as_float(0x7f800000);
+#pragma unroll 1
       for (int r = 0; r < 2; ++r, ++xuse) {
         if (hh) {
           if (xuse > 0 &&
@@ -625,37 +642,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
             failed = true;
             break;
           }
+          if (r == 0) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) s.xch[j][tq] = r ? gm1[j] : gm0[j];
+            for (int j = 0; j < 32; ++j) s.xch[j][tq] = v64[j];
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) s.xch[j][tq] = v64[32 + j];
+          }
           mbar_arrive(&s.xfull[lq]);
         } else {
           if (!__all_sync(kFull, mbar_wait(&s.xfull[lq], (uint32_t)(xuse & 1), a.wait_ns))) {
             failed = true;
             break;
           }
+          // the splits whose last value of the other half is in this round's 32
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float o = s.xch[j][tq];
-            if (r) gm1[j] = fminf(gm1[j], o);
-            else gm0[j] = fminf(gm0[j], o);
+          for (int i = 0; i <= 64; ++i) {
+            const int j = a.R - i - 1 - 32 * r;
+            if (j >= 0 && j < 32) {
+              const float own = i == 0 ? -__int_as_float(0x7f800000) : v64[i > 0 ? i - 1 : 0];
+              T = fminf(T, fmaxf(own, s.xch[j][tq]));
+            }
           }
           mbar_arrive(&s.xempty[lq]);
         }
       }
       if (failed) break;
       if (hh == 0) {
-        // the R-th smallest of the 64 group minima: R distinct rows lie at or below it
-        float v64[64];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          v64[j] = gm0[j];
-          v64[32 + j] = gm1[j];
-        }
-        sort64(v64);
-        float T = __int_as_float(0x7f800000);
+        // the split that takes R of its own (R <= 64)
 #pragma unroll
         for (int i = 0; i < 64; ++i)
-          if (i == a.R - 1) T = v64[i];
+          if (i == a.R - 1) T = fminf(T, v64[i]);
         // clamped at 0 once, on the bound (the clamp commutes with min and rank)
         if (qv && T < __int_as_float(0x7f800000))
           atomicMin(a.qthr + qpos, (unsigned long long)make_key(fmaxf(T, 0.f), 0x7fffffff));
@@ -1076,6 +1093,14 @@ bool encode_2d(CUtensorMap* tm, CUtensorMapDataType dt, const void* base, uint64
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
 
+// Candidates the scan keeps per query for the FP32 re-rank: rerank_mult * k up to
+// kTcRTight, and k itself past that (k <= kTcRMax). The bound is the R-th smallest of
+// 128 group minima: about -128 ln(1 - R / 128) rows lie below it, 48 at R = 40 and
+// 195 at R = 100, while at R = 128 it is the largest minimum and most rows pass.
+int tc_rerank_width(const Params& p) {
+  return (int)std::max<long>(p.k, std::min<long>((long)p.rerank_mult * p.k, kTcRTight));
+}
+
 template <int F>
 cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
                       const Outputs& o, cudaStream_t st) {
@@ -1128,7 +1153,7 @@ cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, 
   a.pcnt = sc.tc_pcnt;
   a.counters = sc.counters;
   a.k = p.k;
-  a.R = p.rerank_mult * p.k;
+  a.R = tc_rerank_width(p);
   a.stall = p.tc_scan == 2 ? 1 : 0;
   a.wait_ns = p.tc_scan == 2 ? kTestWaitNs : kWaitNs;
   a.o = o;
@@ -1168,8 +1193,7 @@ cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, 
 
 bool tc_scan_available(const DeviceIndex& ix, const Params& p) {
   if (!p.tc_scan || ix.d > 1024 || encode_fn() == nullptr) return false;
-  const long R = (long)p.rerank_mult * p.k;
-  if (R < p.k || R > kTcRMax) return false;
+  if (p.rerank_mult < 1 || p.k > kTcRMax) return false;
   // the rows' TMA stride must be a multiple of 16 bytes
   if (p.dtype == UNIFY_BF16) return ix.dp % 8 == 0;
   if (p.dtype == UNIFY_FP32) return true;  // dp is a multiple of 4

@@ -423,7 +423,7 @@ def test_tensor_core_scan_equals_exact_answer(U, c2_small_index, dtype):
     oracle's exact answer (Definition 1, FP64) id for id and distance for distance on
     integer data, whose values are exact in both operand formats: ragged tiles (300,
     129, 65 and 1 queries), several work units per tile, and re-rank widths R = k, 4k,
-    6k. In a routed batch the tensor-core phase takes the pre-filter queries and the
+    6k, and the widest sets (R = 64 at k = 32 and 64, R = k = 100 and 128). In a routed batch the tensor-core phase takes the pre-filter queries and the
     search kernel the others, and every row equals the oracle's HSIG search."""
     w, path = c2_small_index
     ix = U.Index(path)
@@ -439,6 +439,17 @@ def test_tensor_core_scan_equals_exact_answer(U, c2_small_index, dtype):
             assert np.array_equal(tc["count"], ex_c), (dtype, nq, rm)
             assert np.array_equal(tc["dist"][fin].astype(np.float64), ex_d[fin]), (dtype, nq, rm)
             assert np.all(np.isinf(tc["dist"][~fin])) and np.all(tc["status"] == 0)
+    # the widest candidate sets the scan keeps (R = rerank_mult * k up to 64, else k,
+    # up to 128: there the bound is the largest group minimum, and lists overflow into
+    # the exact warp scan of the query's range)
+    for k, rm in ((100, 1), (100, 4), (64, 2), (32, 4), (128, 1)):
+        Q, lo, hi = w.queries[:129], w.lo[:129], w.hi[:129]
+        ex_ids, ex_d, ex_c = oracle.exact_knn(w.vectors, w.attrs, Q, lo, hi, k)
+        fin = np.isfinite(ex_d)
+        tc = _np(ix.search(Q, lo, hi, k, strategy="pre", params=U.Params.defaults(dtype=dt, rerank_mult=rm, tc_scan=1)))
+        assert np.array_equal(tc["ids"], ex_ids), (dtype, k, rm)
+        assert np.array_equal(tc["count"], ex_c), (dtype, k, rm)
+        assert np.array_equal(tc["dist"][fin].astype(np.float64), ex_d[fin]), (dtype, k, rm)
     ta, tb = w.n // 20, w.n // 2
     p1 = U.Params.defaults(dtype=dt, rerank_mult=4, tau_a=ta, tau_b=tb, cand_cap=CAND, tc_scan=1)
     r1 = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy="auto", params=p1))
