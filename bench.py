@@ -57,10 +57,10 @@ PAPER_EF, PAPER_M = 100, 16
 # the search parameters the capture ran with. A run whose digest, workload or
 # parameters differ reports traffic null, beside the nearest capture's parameters.
 NCU_TRAFFIC = [
-    {"digest": "2dfb4cd9d943", "workload": "c2", "bytes": 6_782_889_728 + 9_362_432,
-     "params": {"ef": 16, "ef_post": 96, "m": 64, "tau_a": 10000, "tau_b": 300000, "dtype": 0, "selection": 2,
-                "cand_cap": 256, "visited_cap": 2048, "warps_per_block": 4, "scan_rows": 8192, "reg_budget": 128,
-                "tc_scan": 0},
+    {"digest": "4a97db7ee83d", "workload": "c2", "bytes": 1_946_751_488 + 12_246_528,
+     "params": {"ef": 16, "ef_post": 96, "m": 64, "tau_a": 20000, "tau_b": 600000, "dtype": 0, "selection": 2,
+                "cand_cap": 256, "visited_cap": 1024, "warps_per_block": 4, "scan_rows": 8192, "reg_budget": 80,
+                "tc_scan": 1},
      "profile": "profiles/batch_kernel_c2_1m_launches.md"},
 ]
 TRAFFIC_KEYS = ("ef", "ef_post", "m", "tau_a", "tau_b", "dtype", "selection", "cand_cap", "visited_cap",
