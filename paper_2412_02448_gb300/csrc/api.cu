@@ -292,7 +292,7 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
   if (tc) {
     NvtxRange r("unify:tensor-core scan");
     PhaseTimer t(idx->tm, 2, st);
-    e = launch_tcscan(idx->ix, sc, q, p, o, st);
+    e = launch_tcscan(idx->ix, sc, q, nq, p, o, st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core pre-filter scan");
   }
   {

@@ -142,7 +142,7 @@ cudaError_t launch_batch(const DeviceIndex& ix, const Scratch& sc, const float* 
                          const Outputs& o, cudaStream_t st, bool skip_scan = false, const Conj* cj = nullptr);
 bool tc_scan_available(const DeviceIndex& ix, const Params& p);
 size_t tc_query_row_bytes(int d);  // bytes of one query row of the tensor-core scan, any format
-cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
+cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float* q, int64_t nq, const Params& p,
                           const Outputs& o, cudaStream_t st);
 int batch_smem_per_warp(const Params& p);
 int rerank_count(const Params& p);  // candidates re-ranked in FP32 (0 for FP32 storage)

@@ -670,11 +670,16 @@ static cudaError_t launch_t(const BatchArgs& a, int wpb, int num_sms, cudaStream
 template <class T>
 static cudaError_t launch_dt(const BatchArgs& a, int wpb, int regs, int num_sms, cudaStream_t st) {
   // G rows per distance group: G * CH = 16 row chunks in flight (8 under the
-  // 64-register budget); a group of 32 raw bfloat16 or FP8 rows measured no faster on
-  // GB300. GF rows per group of the float32 re-rank, which runs after the traversal.
+  // 64-register budget, and for FP8 rows, decoded when they load, under the 80-register
+  // one: 16 decoded rows crowd its registers and measured 13 % slower on GB300); a group
+  // of 32 raw bfloat16 or FP8 rows measured no faster. GF rows per group of the float32
+  // re-rank, which runs after the traversal.
   const int ch = (a.dp4 + 31) / 32;
   if (ch <= 1) {
-    if (regs == 80) return launch_t<T, 1, 16, 16, 6>(a, wpb, num_sms, st);
+    if (regs == 80) {
+      if constexpr (T::kHoldRaw) return launch_t<T, 1, 16, 16, 6>(a, wpb, num_sms, st);
+      else return launch_t<T, 1, 8, 8, 6>(a, wpb, num_sms, st);
+    }
     if (regs == 64) return launch_t<T, 1, 8, 8, 8>(a, wpb, num_sms, st);
     return launch_t<T, 1, 16, 16, 4>(a, wpb, num_sms, st);
   }

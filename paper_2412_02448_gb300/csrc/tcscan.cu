@@ -1102,7 +1102,7 @@ int tc_rerank_width(const Params& p) {
 }
 
 template <int F>
-cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
+cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, int64_t nq, const Params& p,
                       const Outputs& o, cudaStream_t st) {
   constexpr int eb = TcTraits<F>::kElemBytes;
   constexpr int kKc = kTcKb / eb;  // K elements per stage
@@ -1177,15 +1177,18 @@ cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, 
   // query scans the stored rows of its format
   using T = typename std::conditional<F == kFmtBF16, StoreBF16,
                                       typename std::conditional<F == kFmtTF32, StoreF32, StoreFP8>::type>::type;
+  // one warp per query of the batch (the pre-filter queries are a part of it), so that
+  // every query's list merge and re-rank gathers are in flight at once
   const int ch = (a.dp4 + 31) / 32;
+  const int fgrid = (int)std::max<int64_t>(ix.num_sms * 4, (nq + 3) / 4);
   if (ch <= 1)
-    tc_finish<T, 1, 16><<<ix.num_sms * 4, 128, 0, st>>>(a);
+    tc_finish<T, 1, 16><<<fgrid, 128, 0, st>>>(a);
   else if (ch <= 2)
-    tc_finish<T, 2, 8><<<ix.num_sms * 4, 128, 0, st>>>(a);
+    tc_finish<T, 2, 8><<<fgrid, 128, 0, st>>>(a);
   else if (ch <= 4)
-    tc_finish<T, 4, 4><<<ix.num_sms * 4, 128, 0, st>>>(a);
+    tc_finish<T, 4, 4><<<fgrid, 128, 0, st>>>(a);
   else
-    tc_finish<T, 8, 2><<<ix.num_sms * 4, 128, 0, st>>>(a);
+    tc_finish<T, 8, 2><<<fgrid, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1202,11 +1205,11 @@ bool tc_scan_available(const DeviceIndex& ix, const Params& p) {
 
 size_t tc_query_row_bytes(int d) { return (size_t)((d + kTcKb - 1) / kTcKb) * kTcKb * 4; }
 
-cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float* q, const Params& p,
+cudaError_t launch_tcscan(const DeviceIndex& ix, const Scratch& sc, const float* q, int64_t nq, const Params& p,
                           const Outputs& o, cudaStream_t st) {
-  if (p.dtype == UNIFY_BF16) return launch_tc<kFmtBF16>(ix, sc, q, p, o, st);
-  if (p.dtype == UNIFY_FP32) return launch_tc<kFmtTF32>(ix, sc, q, p, o, st);
-  return launch_tc<kFmtFP8>(ix, sc, q, p, o, st);
+  if (p.dtype == UNIFY_BF16) return launch_tc<kFmtBF16>(ix, sc, q, nq, p, o, st);
+  if (p.dtype == UNIFY_FP32) return launch_tc<kFmtTF32>(ix, sc, q, nq, p, o, st);
+  return launch_tc<kFmtFP8>(ix, sc, q, nq, p, o, st);
 }
 
 }  // namespace unify
