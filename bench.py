@@ -57,8 +57,8 @@ PAPER_EF, PAPER_M = 100, 16
 # the search parameters the capture ran with. A run whose digest, workload or
 # parameters differ reports traffic null, beside the nearest capture's parameters.
 NCU_TRAFFIC = [
-    {"digest": "4a97db7ee83d", "workload": "c2", "bytes": 1_946_751_488 + 12_246_528,
-     "params": {"ef": 16, "ef_post": 96, "m": 64, "tau_a": 20000, "tau_b": 600000, "dtype": 0, "selection": 2,
+    {"digest": "1820668a002a", "workload": "c2", "bytes": 1_946_045_696 + 11_967_744,
+     "params": {"ef": 16, "ef_post": 96, "m": 64, "tau_a": 20000, "tau_b": 750000, "dtype": 0, "selection": 2,
                 "cand_cap": 256, "visited_cap": 1024, "warps_per_block": 4, "scan_rows": 8192, "reg_budget": 80,
                 "tc_scan": 1},
      "profile": "profiles/batch_kernel_c2_1m_launches.md"},
