@@ -62,6 +62,11 @@ NCU_TRAFFIC = [
                 "cand_cap": 256, "visited_cap": 1024, "warps_per_block": 4, "scan_rows": 8192, "reg_budget": 80,
                 "tc_scan": 1},
      "profile": "profiles/batch_kernel_c2_1m_launches.md"},
+    {"digest": "1820668a002a", "workload": "c2", "bytes": 1_948_573_440 + 12_239_616,
+     "params": {"ef": 16, "ef_post": 96, "m": 64, "tau_a": 20000, "tau_b": 600000, "dtype": 0, "selection": 2,
+                "cand_cap": 256, "visited_cap": 1024, "warps_per_block": 4, "scan_rows": 8192, "reg_budget": 80,
+                "tc_scan": 1},
+     "profile": "profiles/batch_kernel_c2_1m_launches.md"},
 ]
 TRAFFIC_KEYS = ("ef", "ef_post", "m", "tau_a", "tau_b", "dtype", "selection", "cand_cap", "visited_cap",
                 "warps_per_block", "scan_rows", "reg_budget", "tc_scan")
