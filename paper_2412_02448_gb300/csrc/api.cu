@@ -54,17 +54,26 @@ void free_core(Scratch& sc) {
 }
 
 void free_tc(Scratch& sc) {
-  release(sc.tc_bucket);
   release(sc.tc_aq);
   release(sc.tc_aqn);
   release(sc.tc_aqs);
   if (sc.tc_qb) cudaFree(sc.tc_qb);
   sc.tc_qb = nullptr;
-  release(sc.tc_tile);
-  release(sc.tc_part);
+  if (sc.tc_qg) cudaFree(sc.tc_qg);
+  sc.tc_qg = nullptr;
+  release(sc.tc_slotpos);
+  release(sc.tc_tiles);
+  release(sc.tc_spans);
+  release(sc.tc_gmin);
+  release(sc.tc_qlist);
+  release(sc.tc_qcnt);
   release(sc.tc_thr);
-  release(sc.tc_pcnt);
+  release(sc.tc_sumy);
+  release(sc.tc_stage);
+  sc.tc_stage_sms = 0;
   sc.tc_rows = 0;
+  sc.tc_slots = 0;
+  sc.tc_spans_cap = 0;
   sc.tc_qrow_bytes = 0;
 }
 
@@ -114,33 +123,44 @@ cudaError_t ensure_scratch(Scratch& sc, int64_t nq, int k) {
   return cudaSuccess;
 }
 
-// Tensor-core scan buffers for nq queries of d columns, allocated only when a search
-// uses that scan (about 16 KB of candidate lists per query of capacity).
-bool tc_scratch_fits(const Scratch& sc, int64_t nq, int d) {
-  return sc.tc_part && nq <= sc.tc_rows && tc_query_row_bytes(d) <= sc.tc_qrow_bytes;
+// Tensor-core scan buffers for nq queries of d columns over n rows, allocated only
+// when a search uses that scan: per query position its operand row, 16 tile slots
+// (each with a gathered operand row), 128 group minima and a list of kTcQCap keys.
+bool tc_scratch_fits(const Scratch& sc, int64_t nq, int d, int64_t n, int sms) {
+  return sc.tc_qlist && nq <= sc.tc_rows && tc_query_row_bytes(d) <= sc.tc_qrow_bytes &&
+         (n + 4095) / 4096 + 1 <= sc.tc_spans_cap && sms <= sc.tc_stage_sms;
 }
 
-cudaError_t ensure_tc_scratch(Scratch& sc, int64_t nq, int d) {
-  if (tc_scratch_fits(sc, nq, d)) return cudaSuccess;
+cudaError_t ensure_tc_scratch(Scratch& sc, int64_t nq, int d, int64_t n, int sms) {
+  if (tc_scratch_fits(sc, nq, d, n, sms)) return cudaSuccess;
   const size_t qrow = tc_query_row_bytes(d);  // query rows of any of the scan's formats, K padded
   int64_t cap = nq > sc.tc_rows ? nq : sc.tc_rows;
   const int64_t rows = ((cap + kTcQueryTile - 1) / kTcQueryTile) * kTcQueryTile;
+  const int64_t slots = 2 * kTcPairsPerQuery * rows;  // a multiple of 128
+  const int64_t spans = (n + 4095) / 4096 + 1;
   free_tc(sc);
-  cudaError_t e = alloc(sc.tc_bucket, 1024);
-  if (e == cudaSuccess) e = alloc(sc.tc_aq, rows);
+  cudaError_t e = alloc(sc.tc_aq, rows);
   if (e == cudaSuccess) e = alloc(sc.tc_aqn, rows);
   if (e == cudaSuccess) e = alloc(sc.tc_aqs, rows);
   if (e == cudaSuccess) e = cudaMalloc(&sc.tc_qb, (size_t)rows * qrow);
-  if (e == cudaSuccess) e = alloc(sc.tc_tile, 4 * (rows / kTcQueryTile) + 1);
-  // at most kTcUnitsPerTile units per tile, one list of kTcCandCap keys per query and unit
-  if (e == cudaSuccess) e = alloc(sc.tc_part, (size_t)rows * kTcUnitsPerTile * kTcCandCap);
-  if (e == cudaSuccess) e = alloc(sc.tc_pcnt, (size_t)rows * kTcUnitsPerTile * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&sc.tc_qg, (size_t)slots * qrow);
+  if (e == cudaSuccess) e = alloc(sc.tc_slotpos, slots);
+  if (e == cudaSuccess) e = alloc(sc.tc_tiles, 2 * (slots / kTcQueryTile) + 1);
+  if (e == cudaSuccess) e = alloc(sc.tc_spans, 3 * spans + 1);
+  if (e == cudaSuccess) e = alloc(sc.tc_gmin, (size_t)rows * 128);
+  if (e == cudaSuccess) e = alloc(sc.tc_qlist, (size_t)rows * kTcQCap);
+  if (e == cudaSuccess) e = alloc(sc.tc_qcnt, rows);
   if (e == cudaSuccess) e = alloc(sc.tc_thr, rows);
+  if (e == cudaSuccess) e = alloc(sc.tc_sumy, 1);
+  if (e == cudaSuccess) e = alloc(sc.tc_stage, (size_t)sms * kTcEpiThreads * kTcStage);
   if (e != cudaSuccess) {
     free_tc(sc);
     return e;
   }
+  sc.tc_stage_sms = sms;
   sc.tc_rows = rows;
+  sc.tc_slots = slots;
+  sc.tc_spans_cap = spans;
   sc.tc_qrow_bytes = qrow;
   return cudaSuccess;
 }
@@ -272,9 +292,9 @@ int run_search(unify_index_t* idx, const float* q, const int64_t* lo, const int6
   // the tensor-core scan has no second-attribute predicate: conjunctive queries use the warp scan
   const bool tc = !cj && (strategy == UNIFY_PRE || strategy == UNIFY_AUTO) && tc_scan_available(idx->ix, p);
   if (tc) {
-    if (idx->live_plans > 0 && !tc_scratch_fits(idx->sc, nq, idx->ix.d))
+    if (idx->live_plans > 0 && !tc_scratch_fits(idx->sc, nq, idx->ix.d, (int64_t)idx->ix.n, idx->ix.num_sms))
       return fail(UNIFY_E_LIMIT, "search larger than the scratch held by a live plan; destroy the plans first");
-    e = ensure_tc_scratch(idx->sc, nq, idx->ix.d);
+    e = ensure_tc_scratch(idx->sc, nq, idx->ix.d, (int64_t)idx->ix.n, idx->ix.num_sms);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core scan scratch allocation");
   }
   Scratch& sc = idx->sc;

@@ -67,17 +67,26 @@ struct Scratch {
   int2* items = nullptr;       // cap_nq * kMaxScanBlocks scan work items (query, block)
   uint64_t* part = nullptr;    // cap_nq * kMaxScanBlocks * cap_k partial top-k keys
   int32_t* counters = nullptr; // kNumCounters ints, zeroed per call
-  // tensor-core pre-filter scan
-  int32_t* tc_bucket = nullptr;  // 1024 bucket counters / cursors
-  int32_t* tc_aq = nullptr;      // pre-filter query ids in bucketed order
+  // tensor-core pre-filter scan: queries by position (their queue order), tiles of
+  // 128 slots per span of the attribute order, per-query bound and candidate list
+  int32_t* tc_aq = nullptr;      // pre-filter query ids by position
   float* tc_aqn = nullptr;       // squared norms of their vectors in the scan's format
   float* tc_aqs = nullptr;       // their FP8 scales
   void* tc_qb = nullptr;         // their vectors in the scan's format, tc_rows x tc_qrow_bytes
-  int32_t* tc_tile = nullptr;    // per tile: first row, row blocks, units, unit offsets (4 x tiles + 1)
-  uint64_t* tc_part = nullptr;   // per work unit: kTcQueryTile lists of up to kTcCandCap candidate keys
-  int32_t* tc_pcnt = nullptr;    // per work unit and query, two column halves: candidates found
-  unsigned long long* tc_thr = nullptr;  // per pre-filter query: threshold key shared by its units
-  int64_t tc_rows = 0;
+  void* tc_qg = nullptr;         // the rows gathered per tile slot, tc_slots x tc_qrow_bytes
+  int32_t* tc_slotpos = nullptr;  // per tile slot: query position (-1: none), tc_slots
+  int32_t* tc_tiles = nullptr;   // per tile: span, then unit offsets (2 x tc_slots / 128 + 1)
+  int32_t* tc_spans = nullptr;   // per span: count, fill cursor, first tile (3 x tc_spans_cap + 1)
+  unsigned* tc_gmin = nullptr;   // per query: 128 group minima (float bits)
+  uint64_t* tc_qlist = nullptr;  // per query: kTcQCap candidate keys
+  int32_t* tc_qcnt = nullptr;    // per query: candidates found
+  unsigned long long* tc_thr = nullptr;   // per query: bound key
+  unsigned long long* tc_sumy = nullptr;  // total in-range rows of the pre-filter queries
+  uint64_t* tc_stage = nullptr;  // per scan CTA and epilogue thread: kTcStage keys of the current unit
+  int tc_stage_sms = 0;
+  int64_t tc_rows = 0;        // query positions (a multiple of 128)
+  int64_t tc_slots = 0;       // tile slots: 16 per query position
+  int64_t tc_spans_cap = 0;   // spans: ceil(n / 4096) + 1
   size_t tc_qrow_bytes = 0;
   // host-buffer staging
   int64_t stage_nq = 0;
@@ -94,8 +103,10 @@ struct Scratch {
 constexpr int kTcQueryTile = 128;   // pre-filter queries per tensor-core tile
 constexpr int kTcRowPad = 256;      // zero entries past row n of the attribute-ordered norms, scales
                                     // and ids (the tensor-core scan copies whole 256-row blocks)
-constexpr int kTcUnitsPerTile = 16;  // at most this many work units per tile
-constexpr int kTcCandCap = 256;      // candidate slots per query and work unit
+constexpr int kTcQCap = 512;        // candidate keys per query below its bound
+constexpr int kTcStage = 96;        // keys an epilogue thread stages per work unit
+constexpr int kTcEpiThreads = 256;  // epilogue threads of a tensor-core scan CTA
+constexpr int kTcPairsPerQuery = 8;  // (query, span) pairs the scratch holds per query position
 
 // counters[] layout
 enum {
@@ -107,6 +118,8 @@ enum {
   CNT_TC_UNITS = 11,                   // work units of the tensor-core scan
   CNT_TC_TAKE = 12,                    // next work unit to claim (tensor-core scan pass)
   CNT_TC_TAKE_B = 13,                  // next work unit to claim (tensor-core bounding pass)
+  CNT_TC_L = 14,                       // span length of the tensor-core scan's tiles (rows)
+  CNT_TC_TILES = 15,                   // tiles of the tensor-core scan
   kNumCounters = 16
 };
 

@@ -1,39 +1,40 @@
 // Strategy A (pre-filtering, Section 4.2) for many queries at once on the 5th-
 // generation tensor cores: queries x in-range vectors is a dense contraction.
 //
-// The pre-filter queries of a batch are bucketed by the first position pa of
-// their range in the attribute order and converted to the scan's operand format
-// (below), so that 128 consecutive queries (a tile) cover neighbouring rows. The
-// rows of the union of a tile's ranges are split into work units of whole 256-row
-// blocks. For a block, TMA stages 128-byte slices of K of the tile's queries and of
-// the block's attribute-ordered rows (128-byte swizzled), and tcgen05.mma forms
-// D = Q X^T (M = 128 queries, N = 256 rows, 32 bytes of K per instruction, float32
-// accumulation in tensor memory, two accumulators so that the epilogue of one
-// block overlaps the products of the next). Tensor-memory lane q is query q of
-// the tile: its epilogue threads turn its dot products into squared distances
-// ||x||^2 + ||q||^2 - 2 x.q (norms of the operand values) and keep the rows of
-// its range [pa, pb).
+// Tiles per span. The attribute order is cut into spans of L rows (L a multiple of
+// 256, at least 4096, grown when the batch's ranges are long; see span_len). Every
+// pre-filter query takes one slot in a tile of every span its range [pa, pb) meets,
+// and its vector, converted to the scan's operand format (below), is copied into that
+// slot's row of a gathered buffer; a span's covering queries fill ceil(count / 128)
+// tiles. So each 256-row block is read by about count / 128 tiles, whatever the mix
+// of range widths, instead of by every tile of consecutive queries whose union of
+// ranges holds it. A tile's span is split into work units of at most 16 blocks. For a
+// block, TMA stages 128-byte slices of K of the tile's gathered query rows and of the
+// block's attribute-ordered rows (128-byte swizzled), and tcgen05.mma forms D = Q X^T
+// (M = 128 query slots, N = 256 rows, 32 bytes of K per instruction, float32
+// accumulation in tensor memory, two accumulators so that the epilogue of one block
+// overlaps the products of the next). Tensor-memory lane q is slot q of the tile: its
+// epilogue threads turn the slot's dot products into squared distances
+// ||x||^2 + ||q||^2 - 2 x.q (norms of the operand values) and keep the rows of the
+// query's range.
 //
 // Two passes over the same tiles select, for every query, the R smallest keys
 // (distance, id), R = rerank_mult * k up to 64 and k past that (k <= 128), without any
 // per-query heap:
-//   1. bounding pass: per query and unit, the minimum distance of each of 128
-//      disjoint row groups (column half x chunk parity x column, in registers of
-//      the two threads that hold the query); the R-th smallest of those 128 minima
-//      has R distinct rows at or below it, so it bounds the query's R-th smallest
-//      key (R <= 128). The smallest bound over the units is published with
-//      atomicMin as the query's threshold;
-//   2. collecting pass: every in-range row whose key is below the threshold is
-//      appended to the (unit, query) list in global memory (a predicated store;
-//      the two column halves fill it from either end with their own counts).
-//      Typically only about R rows per query qualify.
-// A finishing kernel merges each query's lists into the R smallest keys and
-// re-ranks them with exact float32 direct-difference distances against the
-// float32 vectors, as the other reduced-precision paths do. A list that overflowed
-// (more than kTcCap rows below the bound) sends that query through an exact warp
-// scan of its range instead. On integer-valued vectors of at most 8 bits and
-// d <= 128 every term is an exact integer below 2^24, so the result equals the
-// exact float32 scan.
+//   1. bounding pass: per query, the minimum distance of each of 128 disjoint row
+//      groups over its whole range (group = column half x column mod 64 of a 256-row
+//      block; every unit min-merges its minima into the query's 128 with atomicMin).
+//      A small kernel then takes the R-th smallest of the 128: R distinct rows lie at
+//      or below it, so it bounds the query's R-th smallest key (R <= 128);
+//   2. collecting pass: every in-range row whose key is below the bound is appended
+//      to the query's list in global memory (an atomic count; about 1.5 R rows per
+//      query qualify).
+// A finishing kernel takes the R smallest keys of each query's list and re-ranks
+// them with exact float32 direct-difference distances against the float32 vectors,
+// as the other reduced-precision paths do. A list that overflowed (more than kTcQCap
+// rows below the bound) sends that query through an exact warp scan of its range
+// instead. On integer-valued vectors of at most 8 bits and d <= 128 every term is an
+// exact integer below 2^24, so the result equals the exact float32 scan.
 //
 // Roles in a CTA of 10 warps: warps 0-7 epilogue (warp w reads tensor-memory
 // lanes 32 (w % 4).. 32 (w % 4) + 31, the queries it owns, over column half w / 4 of
@@ -55,11 +56,13 @@
 // as broadcast vector loads. Only chunks that hold the end of some lane's range take
 // the per-column test.
 //
-// Bounds (checked against the buffers each launch receives): a unit's rows lie
-// in [tile_lo, tile_lo + 256 nb) and loads past n are zero-filled by TMA (rows)
-// or guarded (norms, ids); the query tile's TMA rows end at tc_rows (a multiple
-// of 128); part holds at most kTcUnitsPerTile units per tile and kTcCap keys per
-// (unit, query) list, and stores stop at kTcCap while the count goes on.
+// Bounds (checked against the buffers each launch receives): the span length keeps
+// the (query, span) pairs within the scratch's pairs and the tiles within its slots
+// (span_len; the tile count is checked again, and an overflow raises the error flag);
+// a unit's rows start below n and the attribute-ordered norms, scales and ids hold
+// 256 zero entries past n, TMA zero-fills rows past n; the query tiles' TMA rows end
+// at the scratch's slots; list stores stop at kTcQCap while the count goes on.
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -78,15 +81,13 @@ constexpr int kTcQ = kTcQueryTile;  // queries per tile (MMA M = tensor-memory l
 constexpr int kTcRows = 256;        // rows per block (MMA N = tensor-memory columns per accumulator)
 constexpr int kTcKb = 128;          // bytes of K per stage (one 128-byte swizzle row)
 constexpr int kTcStages = 4;
-constexpr int kTcCap = kTcCandCap;  // candidate slots per query and work unit
 constexpr int kUnitRing = 4;        // claimed work units handed from the producer to the other roles
-constexpr int kEpiWarps = 8;        // epilogue warps: warp w reads lanes 32 (w % 4).. and column half w / 4
+constexpr int kEpiWarps = kTcEpiThreads / 32;  // 8 epilogue warps: warp w reads lanes 32 (w % 4).. and column half w / 4
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kTcThreads = 32 * (kEpiWarps + 2);
 constexpr int kHalfCols = kTcRows / 2;  // columns of a block per epilogue warp
 constexpr int kTcRMax = 128;        // candidates kept per query for the re-rank, at most
 constexpr int kTcRTight = 64;       // up to here the bound stays near R rows; past it the scan keeps k
-constexpr int kBuckets = 1024;
 constexpr int kStageA = kTcQ * kTcKb;     // 16 KB of queries
 constexpr int kStageB = kTcRows * kTcKb;  // 32 KB of rows
 
@@ -139,10 +140,6 @@ struct TcSmem {
   uint64_t full[kTcStages], empty[kTcStages], accf[2], acce[2], drain, mfull[2];
   uint64_t never;  // no thread arrives on it (the timeout test waits on it)
   uint64_t ufull[kUnitRing], uempty[kUnitRing];
-  // bounding pass: the column half 1 warps hand 32 group minima per query at a time
-  // to the half 0 warps of the same tensor-memory lanes (one pair per lane quarter)
-  uint64_t xfull[4], xempty[4];
-  float xch[32][kTcQ];
   int uring[kUnitRing];  // claimed unit (-1: no more units)
   uint32_t tmem;
 };
@@ -283,26 +280,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
 // Element i (a constant after unrolling) of a vector of four.
 __device__ __forceinline__ float f4_at(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
 __device__ __forceinline__ int i4_at(const int4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
-
-// Ascending bitonic sort of 64 values held in registers (static indices only).
-__device__ __forceinline__ void sort64(float (&v)[64]) {
-#pragma unroll
-  for (int k = 2; k <= 64; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-#pragma unroll
-      for (int i = 0; i < 64; ++i) {
-        const int l = i ^ j;
-        if (l > i) {
-          const bool up = (i & k) == 0;
-          const float x = v[i], y = v[l];
-          const bool sw = up ? (x > y) : (x < y);
-          v[i] = sw ? y : x;
-          v[l] = sw ? x : y;
-        }
-      }
-    }
-  }
+__device__ __forceinline__ unsigned u4_at(const uint4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
 struct TcArgs {
@@ -313,21 +292,28 @@ struct TcArgs {
   const unsigned char* vt;  // rows by id in the storage format (scan of an overflowed query)
   const float* vscale;      // FP8: per-row scales by id (else null)
   const float* q;      // float32 queries (re-rank)
-  int dp4, d, KC, num_sms;
+  int dp4, d, dpq, eb, KC, num_sms;
   int64_t n;
   const int32_t* pa;
   const int32_t* pb;
-  const int32_t* aq;    // pre-filter query ids in bucketed order
-  const float* aqn;     // squared norms of their vectors as the scan's format holds them, same order
-  const float* aqs;     // FP8: their scales (else null)
-  int32_t* tile_lo;     // first row of each tile's union range
-  int32_t* tile_nb;     // 256-row blocks of the union range
-  int32_t* tile_units;  // work units the range is split into
-  int32_t* unit_off;    // exclusive prefix of tile_units (ntiles + 1)
-  uint64_t* part;       // per unit and query of its tile: kTcCap candidate slots
-  int32_t* pcnt;        // per unit and query, per column half: candidates found (the two
-                        // together above kTcCap: overflow)
-  unsigned long long* qthr;  // per query (bucketed order): smallest key known to have R keys at or below it
+  int32_t* aq;          // pre-filter query ids by position (the order of their queue)
+  float* aqn;           // squared norms of their vectors as the scan's format holds them
+  float* aqs;           // FP8: their scales (else null)
+  void* qb;             // their vectors in the scan's format, dpq elements a row
+  void* qg;             // the same rows gathered per tile slot (TMA source of the query operand)
+  int32_t* slotpos;     // per tile slot: the query position it holds, -1 for none
+  int32_t* tile_span;   // per tile: its span
+  int32_t* unit_off;    // per tile: its first work unit (tiles + 1 entries)
+  int32_t* span_cnt;    // per span: queries whose range meets it
+  int32_t* span_tile;   // per span: its first tile (spans + 1 entries)
+  int32_t* span_fill;   // per span: next free slot (placement cursor)
+  unsigned* gmin;       // per query: 128 group minima over its whole range (float bits)
+  uint64_t* qlist;      // per query: kTcQCap candidate keys below its bound
+  uint64_t* stage;      // per CTA and epilogue thread: kTcStage keys found in the current unit
+  int32_t* qcnt;        // per query: candidates found (above kQCap: overflow)
+  unsigned long long* sumy;  // total in-range rows of the pre-filter queries
+  unsigned long long* qthr;  // per query: key(T, INT_MAX) of its bound T (kKeyMax: none)
+  int64_t slot_cap, span_cap, pcap;  // tile slots, spans and (query, span) pairs the scratch holds
   int32_t* counters;
   int k, R;
   uint64_t wait_ns;  // elapsed-time limit of every wait on another role
@@ -345,13 +331,31 @@ __device__ __forceinline__ int unit_tile(const TcArgs& a, int ntiles, int x) {
   return lo;
 }
 
-// Rows [r0, r1) of unit u of tile t: blocks [u nb / U, (u + 1) nb / U) of the
-// tile's range (r1 may pass the end of the data; those rows are not used).
+// Span length L (rows; a multiple of 256, at least 4096). It keeps the (query, span)
+// pairs P within pcap: a query meets at most (Y - 1) / L + 2 spans, so
+// L >= sum(Y) / (pcap - 2 nA) gives P <= pcap; and the tiles within slot_cap / 128 =
+// pcap / 64: there are at most P / 128 + ceil(n / L) of them, and
+// L >= 128 n / (pcap - 128) makes ceil(n / L) <= pcap / 128.
+__device__ __forceinline__ int64_t span_len(const TcArgs& a, int nA) {
+  const unsigned long long sy = *a.sumy;
+  const int64_t room = a.pcap - 2 * (int64_t)nA;  // > 0: pcap is 8 slots per query
+  int64_t L = (int64_t)((sy + room - 1) / room);
+  const int64_t L2 = (128 * a.n + a.pcap - 129) / (a.pcap - 128);  // pcap >= 1024
+  if (L2 > L) L = L2;
+  if (L < 4096) L = 4096;
+  return (L + kTcRows - 1) / kTcRows * kTcRows;
+}
+
+// Rows [r0, r1) of unit u of tile t: its share of the blocks of the tile's span
+// (r1 may pass the end of the data; those rows are not used).
 __device__ __forceinline__ void tile_unit_rows(const TcArgs& a, int t, int u, int* r0, int* r1) {
-  const int nb = a.tile_nb[t], U = a.tile_units[t];
+  const int64_t L = a.counters[CNT_TC_L];
+  const int64_t s0 = (int64_t)a.tile_span[t] * L;
+  const int64_t rows = (a.n - s0 < L) ? a.n - s0 : L;
+  const int nb = (int)((rows + kTcRows - 1) / kTcRows), U = a.unit_off[t + 1] - a.unit_off[t];
   const int b0 = (int)((int64_t)u * nb / U), b1 = (int)((int64_t)(u + 1) * nb / U);
-  *r0 = a.tile_lo[t] + b0 * kTcRows;
-  *r1 = a.tile_lo[t] + b1 * kTcRows;
+  *r0 = (int)(s0 + (int64_t)b0 * kTcRows);
+  *r1 = (int)(s0 + (int64_t)b1 * kTcRows);
 }
 
 // kBound = true: the bounding pass. Its epilogue keeps, per query, the minimum
@@ -370,8 +374,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023));
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  const int nA = a.counters[CNT_QA];
-  const int ntiles = (nA + kTcQ - 1) / kTcQ;
+  const int ntiles = a.counters[CNT_TC_TILES];
   const int nunits = a.counters[CNT_TC_UNITS];
   int* err = a.counters + CNT_TC_ERR;
 
@@ -390,10 +393,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
     for (int i = 0; i < kUnitRing; ++i) {
       mbar_init(&s.ufull[i], 1);
       mbar_init(&s.uempty[i], 1 + kEpiWarps * 32);  // the MMA issuer and the epilogue threads
-    }
-    for (int i = 0; i < 4; ++i) {
-      mbar_init(&s.xfull[i], 32);
-      mbar_init(&s.xempty[i], 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -532,7 +531,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
     const int tq = lq * 32 + lane;
     const int cbase = hh * kHalfCols;
     bool failed = false;
-    long long g = 0, xuse = 0;
+    long long g = 0;
     for (long long useq = 0; !failed; ++useq) {
       const int us = (int)(useq % kUnitRing);
       if (!__all_sync(kFull, mbar_wait(&s.ufull[us], (uint32_t)((useq / kUnitRing) & 1), a.wait_ns))) {
@@ -545,8 +544,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
       const int t = unit_tile(a, ntiles, x);
       int r0, r1;
       tile_unit_rows(a, t, x - a.unit_off[t], &r0, &r1);
-      const int qpos = t * kTcQ + tq;
-      const bool qv = qpos < nA;
+      const int qpos = a.slotpos[(int64_t)t * kTcQ + tq];  // query position of this slot, -1: none
+      const bool qv = qpos >= 0;
       int pa = 0, pb = 0;
       float qn = 0.f, qs = 1.f;
       if (qv) {
@@ -621,73 +620,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
         mbar_arrive(&s.acce[ab]);
       }
       if (failed) break;
-      // 128 disjoint groups: 64 per column half. Both halves sort their minima; the
-      // half-1 warp hands its sorted minima to the half-0 warp, 32 at a time, which
-      // takes the R-th smallest of the 128 as the bound: over the splits that take i
-      // of its own smallest and R - i of the other half's, the smallest of the larger
-      // of the two last values taken. R distinct rows lie at or below it.
-      float v64[64];
+      // the query's 128 group minima over its whole range: group hh * 64 + (column mod
+      // 64) of column half hh; every span and block starts on a multiple of 256 rows,
+      // so a group is the same set of row residues in every unit of the query, and the
+      // minimum over units is the group's minimum over the range. Clamped at 0 (the
+      // clamp commutes with min and rank); groups without rows stay +inf.
+      // Only minima below the query's current ones take an atomic (a plain read first;
+      // a stale read only costs an atomic that changes nothing).
+      if (qv) {
+        unsigned* gq = a.gmin + (int64_t)qpos * 128 + hh * 64;
+        uint4 cur[16];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        v64[j] = gm0[j];
-        v64[32 + j] = gm1[j];
-      }
-      sort64(v64);
-      float T = __int_as_float(0x7f800000);
-#pragma unroll 1
-      for (int r = 0; r < 2; ++r, ++xuse) {
-        if (hh) {
-          if (xuse > 0 &&
-              !__all_sync(kFull, mbar_wait(&s.xempty[lq], (uint32_t)((xuse - 1) & 1), a.wait_ns))) {
-            failed = true;
-            break;
-          }
-          if (r == 0) {
+        for (int i = 0; i < 16; ++i) cur[i] = __ldcg(reinterpret_cast<const uint4*>(gq) + i);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) s.xch[j][tq] = v64[j];
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) s.xch[j][tq] = v64[32 + j];
-          }
-          mbar_arrive(&s.xfull[lq]);
-        } else {
-          if (!__all_sync(kFull, mbar_wait(&s.xfull[lq], (uint32_t)(xuse & 1), a.wait_ns))) {
-            failed = true;
-            break;
-          }
-          // the splits whose last value of the other half is in this round's 32
-#pragma unroll
-          for (int i = 0; i <= 64; ++i) {
-            const int j = a.R - i - 1 - 32 * r;
-            if (j >= 0 && j < 32) {
-              const float own = i == 0 ? -__int_as_float(0x7f800000) : v64[i > 0 ? i - 1 : 0];
-              T = fminf(T, fmaxf(own, s.xch[j][tq]));
-            }
-          }
-          mbar_arrive(&s.xempty[lq]);
+        for (int j = 0; j < 32; ++j) {
+          const unsigned v0 = __float_as_uint(fmaxf(gm0[j], 0.f)), v1 = __float_as_uint(fmaxf(gm1[j], 0.f));
+          if (gm0[j] < __int_as_float(0x7f800000) && v0 < u4_at(cur[j >> 2], j & 3)) atomicMin(gq + j, v0);
+          if (gm1[j] < __int_as_float(0x7f800000) && v1 < u4_at(cur[8 + (j >> 2)], j & 3)) atomicMin(gq + 32 + j, v1);
         }
-      }
-      if (failed) break;
-      if (hh == 0) {
-        // the split that takes R of its own (R <= 64)
-#pragma unroll
-        for (int i = 0; i < 64; ++i)
-          if (i == a.R - 1) T = fminf(T, v64[i]);
-        // clamped at 0 once, on the bound (the clamp commutes with min and rank)
-        if (qv && T < __int_as_float(0x7f800000))
-          atomicMin(a.qthr + qpos, (unsigned long long)make_key(fmaxf(T, 0.f), 0x7fffffff));
       }
     }
     if (failed) atomicExch(err, 1);
   } else {
     // ---- collecting epilogue (warps 0-7): lane q of warp w is query 32 (w % 4) + q
     // of the tile (its tensor-memory lane) over columns 128 (w / 4).. of each block.
-    // Every in-range row whose key is below the query's bound is appended to the
-    // (unit, query) list in global memory: the column-half-0 thread fills it from the
-    // front, the half-1 thread from the back, each with its own count, which goes on
-    // past the list's end so that the finishing kernel can see an overflow (the two
-    // counts together above kTcCap). The warps run independently; a timed-out wait
-    // ends the warp's loop (decided warp-wide).
+    // Every in-range row whose key is below the query's bound is staged in this
+    // thread's area (a predicated store, thread-private count); at the end of the unit
+    // the thread reserves room in the query's list with one atomicAdd and copies its
+    // keys there. The query's count goes on past kTcQCap (a staging area that filled
+    // up adds more than kTcQCap), so that the finishing kernel can see an overflow. The
+    // warps run independently; a timed-out wait ends the warp's loop (decided
+    // warp-wide).
     const int lq = warp & 3, hh = warp >> 2;
     const int tq = lq * 32 + lane;
     const int cbase = hh * kHalfCols;
@@ -708,8 +671,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
       const int t = unit_tile(a, ntiles, x);
       int r0, r1;
       tile_unit_rows(a, t, x - a.unit_off[t], &r0, &r1);
-      const int qpos = t * kTcQ + tq;
-      const bool qv = qpos < nA;
+      const int qpos = a.slotpos[(int64_t)t * kTcQ + tq];  // query position of this slot, -1: none
+      const bool qv = qpos >= 0;
       int pa = 0, pb = 0;
       float qn = 0.f, qs = 1.f;
       uint64_t thr = kKeyMax;
@@ -726,10 +689,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
       // the key (tdist, INT_MAX), so a row's key is below it exactly when its
       // distance is at most tdist
       const float tdist = thr == kKeyMax ? __int_as_float(0x7f800000) : key_dist(thr);
-      uint64_t* const list = a.part + ((int64_t)x * kTcQ + tq) * kTcCap;
-      uint64_t* wp = hh ? list + (kTcCap - 1) : list;  // next slot
-      const int step = hh ? -1 : 1;
-      int cnt = 0;  // keys found (may pass kTcCap; wp stops at the list's end)
+      uint64_t* const stage = a.stage + ((int64_t)blockIdx.x * kTcEpiThreads + threadIdx.x) * kTcStage;
+      int cnt = 0;  // keys found in this unit (may pass kTcStage; stores stop there)
       for (int row0 = r0; row0 < r1; row0 += kTcRows, ++g) {
         const int ab = (int)(g & 1);
         const int c0 = max(pa - row0, 0), c1 = min(pb - row0, kTcRows);  // this query's columns
@@ -750,7 +711,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
           if (!__any_sync(kFull, need)) continue;
           const bool full = c0 <= cb && c1 >= cb + 32;
           float v[32];
-          if (__all_sync(kFull, (full || !need) && cnt + 32 <= kTcCap)) {
+          if (__all_sync(kFull, (full || !need) && cnt + 32 <= kTcStage)) {
             // every lane takes all 32 columns or none (NaN compares false), and has
             // room for 32 more keys
             const float qe = need ? qn : __int_as_float(0x7fc00000);
@@ -763,7 +724,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
               if constexpr (kSc) s4[i] = reinterpret_cast<const float4*>(mxs + cb)[i];
             }
             tmem_ld32(taddr + (uint32_t)(32 * lc), v);
-            uint64_t* const w0 = wp;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const float xv = f4_at(x4[j >> 2], j & 3);
@@ -771,10 +731,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
               if constexpr (kSc) w = w2 * f4_at(s4[j >> 2], j & 3);
               const float dist = fmaf(-w, v[j], xv + qe);
               const bool hit = dist <= tdist;
-              if (hit) *wp = make_key(fmaxf(dist, 0.f), i4_at(i4[j >> 2], j & 3));
-              wp += hit ? step : 0;
+              if (hit) stage[cnt] = make_key(fmaxf(dist, 0.f), i4_at(i4[j >> 2], j & 3));
+              cnt += hit;
             }
-            cnt += (int)(hh ? w0 - wp : wp - w0);
           } else {
             tmem_ld32(taddr + (uint32_t)(32 * lc), v);
             // this query's columns of the chunk: [jlo, jhi)
@@ -786,10 +745,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
               if constexpr (kSc) w = w2 * mxs[cb + j];
               const float dist = fmaf(-w, v[j], xv + qn);
               if (j >= jlo && j < jhi && dist <= tdist) {
-                if (cnt < kTcCap) {
-                  *wp = make_key(fmaxf(dist, 0.f), mid[cb + j]);
-                  wp += step;
-                }
+                if (cnt < kTcStage) stage[cnt] = make_key(fmaxf(dist, 0.f), mid[cb + j]);
                 ++cnt;
               }
             }
@@ -799,7 +755,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
         mbar_arrive(&s.acce[ab]);
       }
       if (failed) break;
-      a.pcnt[2 * ((int64_t)x * kTcQ + tq) + hh] = cnt;
+      // the unit's keys into the query's list (a staging area that filled up forces
+      // the query's overflow: its exact scan)
+      if (cnt > 0) {
+        const int o = atomicAdd(a.qcnt + qpos, cnt > kTcStage ? kTcQCap + 1 : cnt);
+        uint64_t* const list = a.qlist + (int64_t)qpos * kTcQCap;
+        if (cnt <= kTcStage)
+          for (int i = 0; i < cnt && o + i < kTcQCap; ++i) list[o + i] = stage[i];
+      }
     }
     if (failed) atomicExch(err, 1);
   }
@@ -812,93 +775,172 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const __grid_con
   }
 }
 
-// One warp per tile: the union of its queries' ranges in 256-row blocks.
-__global__ void tc_tile_prep(TcArgs a) {
+// Spans of the attribute order met by each pre-filter query: one thread per query
+// position counts itself into every span its range [pa, pb) meets.
+__global__ void tc_span_count(TcArgs a) {
   const int nA = a.counters[CNT_QA];
-  const int ntiles = (nA + kTcQ - 1) / kTcQ;
+  const int64_t L = span_len(a, nA);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[CNT_TC_L] = (int)L;
+  for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < nA; pos += gridDim.x * blockDim.x) {
+    const int qi = a.aq[pos];
+    const int pa = a.pa[qi], pb = a.pb[qi];
+    if (pb <= pa) continue;
+    for (int64_t sp = pa / L; sp <= (pb - 1) / L; ++sp) atomicAdd(&a.span_cnt[sp], 1);
+  }
+}
+
+// Exclusive prefix sum over the 1024 threads of a CTA; *total gets the sum.
+__device__ __forceinline__ int cta_exclusive_scan(int v, int* sm, int* total) {
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int w = threadIdx.x >= off ? sm[threadIdx.x - off] : 0;
+    __syncthreads();
+    sm[threadIdx.x] += w;
+    __syncthreads();
+  }
+  const int r = sm[threadIdx.x] - v;
+  *total = sm[1023];
+  __syncthreads();
+  return r;
+}
+
+// One CTA of 1024 threads: tiles of 128 slots per span (ceil(count / 128)), the first
+// tile of every span, the span of every tile, the work units of every tile and the
+// placement cursors (every slot was marked empty, -1, before). A unit holds bpu of its span's
+// 256-row blocks, bpu in [1, 16] chosen for about four units per SM over the batch
+// (all tiles of a span have the same units). Totals go to the counters; tiles past the
+// scratch's slots raise the error flag and are dropped.
+__global__ void tc_span_scan(TcArgs a) {
+  __shared__ int sm[1024];
+  __shared__ int carry;
+  __shared__ unsigned long long blocks;
+  const int64_t L = a.counters[CNT_TC_L];
+  const int nspan = (int)((a.n + L - 1) / L);
+  const int tile_cap = (int)(a.slot_cap / kTcQ);
+  auto span_blocks = [&](int sp) {
+    const int64_t rows = (a.n - sp * L < L) ? a.n - sp * L : L;
+    return (int)((rows + kTcRows - 1) / kTcRows);
+  };
+  if (threadIdx.x == 0) {
+    carry = 0;
+    blocks = 0;
+  }
+  __syncthreads();
+  // sweep 1: tiles per span and their first tile; tile-blocks of the batch
+  for (int base = 0; base < nspan; base += 1024) {
+    const int sp = base + threadIdx.x;
+    const int nt = sp < nspan ? (a.span_cnt[sp] + kTcQ - 1) / kTcQ : 0;
+    int tsum;
+    const int t0 = carry + cta_exclusive_scan(nt, sm, &tsum);
+    if (sp < nspan) {
+      a.span_tile[sp] = t0;
+      a.span_fill[sp] = t0 * kTcQ;
+      if (nt > 0) atomicAdd(&blocks, (unsigned long long)nt * span_blocks(sp));
+      for (int i = 0; i < nt && t0 + i < tile_cap; ++i) a.tile_span[t0 + i] = sp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tsum;
+    __syncthreads();
+  }
+  const int tiles = carry;
+  const unsigned long long want = 4ull * (unsigned long long)a.num_sms;
+  unsigned long long per = (blocks + want - 1) / want;
+  const int bpu = per < 1 ? 1 : per > 16 ? 16 : (int)per;
+  __syncthreads();
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  // sweep 2: units of every tile
+  for (int base = 0; base < nspan; base += 1024) {
+    const int sp = base + threadIdx.x;
+    int nt = 0, nu = 0;
+    if (sp < nspan) {
+      nt = (a.span_cnt[sp] + kTcQ - 1) / kTcQ;
+      nu = (span_blocks(sp) + bpu - 1) / bpu;
+    }
+    int usum;
+    const int u0 = carry + cta_exclusive_scan(nt * nu, sm, &usum);
+    if (sp < nspan) {
+      const int t0 = a.span_tile[sp];
+      for (int i = 0; i < nt && t0 + i < tile_cap; ++i) a.unit_off[t0 + i] = u0 + i * nu;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += usum;
+    __syncthreads();
+  }
+  int ntiles = tiles, units = carry;
+  if (ntiles > tile_cap) {  // cannot happen with the span length's bounds; kept safe
+    ntiles = 0;
+    units = 0;
+    if (threadIdx.x == 0) atomicExch(&a.counters[CNT_TC_ERR], 1);
+  }
+  if (threadIdx.x == 0) {
+    a.span_tile[nspan] = ntiles;
+    a.unit_off[ntiles] = units;
+    a.counters[CNT_TC_TILES] = ntiles;
+    a.counters[CNT_TC_UNITS] = units;
+  }
+}
+
+// One warp per pre-filter query position: a slot in one tile of every span its range
+// meets, and its operand row copied into that slot's row of the gathered buffer.
+__global__ void tc_place(TcArgs a) {
+  const int nA = a.counters[CNT_QA];
+  const int64_t L = a.counters[CNT_TC_L];
+  const int64_t slots = (int64_t)a.counters[CNT_TC_TILES] * kTcQ;
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * (blockDim.x >> 5);
-  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += warps) {
-    const int q0 = t * kTcQ, nq = min(kTcQ, nA - q0);
-    int lo = INT_MAX, hi = 0;
-    for (int i = lane; i < nq; i += 32) {
-      const int qi = a.aq[q0 + i];
-      const int p0 = a.pa[qi], p1 = a.pb[qi];
-      if (p1 > p0) {
-        lo = min(lo, p0);
-        hi = max(hi, p1);
-      }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      lo = min(lo, __shfl_xor_sync(kFull, lo, off));
-      hi = max(hi, __shfl_xor_sync(kFull, hi, off));
-    }
-    // the union starts on a multiple of 4 rows, so that the epilogues read the
-    // blocks' norms and ids as aligned vectors of four
-    const bool none = lo == INT_MAX;
-    lo &= ~3;
-    if (lane == 0) {
-      a.tile_lo[t] = none ? 0 : lo;
-      a.tile_nb[t] = none ? 0 : (hi - lo + kTcRows - 1) / kTcRows;
+  const int row16 = a.dpq * a.eb / 16;  // 16-byte words of an operand row
+  for (int pos = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pos < nA; pos += warps) {
+    const int qi = a.aq[pos];
+    const int pa = a.pa[qi], pb = a.pb[qi];
+    if (pb <= pa) continue;
+    const int4* src = reinterpret_cast<const int4*>(reinterpret_cast<const unsigned char*>(a.qb) +
+                                                    (int64_t)pos * a.dpq * a.eb);
+    for (int64_t sp = pa / L; sp <= (pb - 1) / L; ++sp) {
+      int gs = 0;
+      if (lane == 0) gs = atomicAdd(&a.span_fill[sp], 1);
+      gs = __shfl_sync(kFull, gs, 0);
+      if (gs >= slots) continue;  // only with dropped tiles (error flag set)
+      if (lane == 0) a.slotpos[gs] = pos;
+      int4* dst = reinterpret_cast<int4*>(reinterpret_cast<unsigned char*>(a.qg) + (int64_t)gs * a.dpq * a.eb);
+      for (int c = lane; c < row16; c += 32) dst[c] = src[c];
     }
   }
 }
 
-// One CTA of 1024 threads: splits every tile into work units of about equal
-// length, about four units per SM over the whole batch (at least one per tile
-// with rows, at most kTcUnitsPerTile and at most one per block), and writes the
-// exclusive prefix of the units per tile; the total goes to the counters.
-__global__ void tc_unit_plan(TcArgs a) {
-  __shared__ int sm[1024];
-  __shared__ unsigned long long tot;
-  __shared__ int carry;
+// One warp per pre-filter query position: its bound, the R-th smallest of its 128
+// group minima (the smallest value v with at least R minima <= v, by bisection over
+// the float bits, which order like the values for v >= 0). No bound (+inf) when fewer
+// than R groups hold rows.
+__global__ void tc_bound(TcArgs a) {
   const int nA = a.counters[CNT_QA];
-  const int ntiles = (nA + kTcQ - 1) / kTcQ;
-  unsigned long long mine = 0;
-  for (int t = threadIdx.x; t < ntiles; t += 1024) mine += (unsigned long long)a.tile_nb[t];
-  for (int off = 16; off > 0; off >>= 1) mine += __shfl_xor_sync(kFull, mine, off);
-  if (threadIdx.x == 0) {
-    tot = 0;
-    carry = 0;
-  }
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) atomicAdd(&tot, mine);
-  __syncthreads();
-  const long long total = tot > 0 ? (long long)tot : 1;
-  const long long target = 4ll * a.num_sms;
-  for (int base = 0; base < ntiles; base += 1024) {
-    const int t = base + threadIdx.x;
-    int v = 0;
-    if (t < ntiles) {
-      const int nb = a.tile_nb[t];
-      v = (int)((nb * target + total - 1) / total);
-      v = max(v, nb > 0 ? 1 : 0);
-      v = min(v, min(nb, kTcUnitsPerTile));
-      a.tile_units[t] = v;
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int pos = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pos < nA; pos += warps) {
+    const uint4 m = reinterpret_cast<const uint4*>(a.gmin + (int64_t)pos * 128)[lane];
+    auto count_le = [&](unsigned x) {
+      const int c = (m.x <= x) + (m.y <= x) + (m.z <= x) + (m.w <= x);
+      int t = c;
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(kFull, t, off);
+      return t;
+    };
+    const unsigned kInf = 0x7f800000u;
+    if (count_le(kInf - 1) < a.R) continue;  // the threshold stays kKeyMax
+    unsigned lo = 0, hi = kInf - 1;  // count_le(hi) >= R
+    while (lo < hi) {
+      const unsigned mid = lo + (hi - lo) / 2;
+      if (count_le(mid) >= a.R) hi = mid;
+      else lo = mid + 1;
     }
-    sm[threadIdx.x] = v;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-      const int w = threadIdx.x >= off ? sm[threadIdx.x - off] : 0;
-      __syncthreads();
-      sm[threadIdx.x] += w;
-      __syncthreads();
-    }
-    if (t < ntiles) a.unit_off[t] = carry + sm[threadIdx.x] - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry += sm[1023];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    a.unit_off[ntiles] = carry;
-    a.counters[CNT_TC_UNITS] = carry;
+    if (lane == 0) a.qthr[pos] = make_key(__uint_as_float(lo), 0x7fffffff);
   }
 }
 
-// One warp per pre-filter query: merges the candidate lists of the units of its
-// tile that overlap its range into the R smallest keys, re-ranks them with exact
-// float32 distances and writes the result row. A list that overflowed (more than
-// kTcCap candidates below the bound) sends the query through an exact warp scan of
+// One warp per pre-filter query: takes the R smallest keys of its candidate list,
+// re-ranks them with exact float32 distances and writes the result row. A list that
+// overflowed (more than kTcQCap candidates below the bound) sends the query through
+// an exact warp scan of
 // its range instead: the stored rows (format T) against the float32 query, direct
 // differences, the same selection as the warp scan of the search kernel. After a
 // timed-out wait the rows are empty and flagged.
@@ -913,37 +955,20 @@ __global__ void __launch_bounds__(128) tc_finish(TcArgs a) {
   const bool failed = a.counters[CNT_TC_ERR] != 0;
   const int warps = gridDim.x * 4;
   for (int pos = blockIdx.x * 4 + warp; pos < nA; pos += warps) {
-    const int t = pos / kTcQ, j = pos - t * kTcQ;
     const int qi = a.aq[pos];
     const int pa = a.pa[qi], pb = a.pb[qi];
-    const int u0 = a.unit_off[t], U = a.tile_units[t];
     float4 qv[CH];
     load_query<CH>(qv, a.q + (int64_t)qi * a.d, a.d);
-    bool overflow = false;
-    for (int u = 0; u < U && pb > pa && !failed; ++u) {
-      int r0, r1;
-      tile_unit_rows(a, t, u, &r0, &r1);
-      if (r1 <= pa || r0 >= pb) continue;
-      const int64_t li = (int64_t)(u0 + u) * kTcQ + j;
-      overflow = overflow || a.pcnt[2 * li] + a.pcnt[2 * li + 1] > kTcCap;
-    }
+    const int c = a.qcnt[pos];
+    const bool overflow = c > kTcQCap;
     int nt = 0;
     if (failed || pb <= pa) {
       nt = 0;
     } else if (!overflow) {
-      for (int u = 0; u < U; ++u) {
-        int r0, r1;
-        tile_unit_rows(a, t, u, &r0, &r1);
-        if (r1 <= pa || r0 >= pb) continue;
-        const int64_t li = (int64_t)(u0 + u) * kTcQ + j;
-        // keys from the front (column half 0) and from the back (half 1)
-        const int cf = a.pcnt[2 * li], c = cf + a.pcnt[2 * li + 1];
-        const uint64_t* src = a.part + li * kTcCap;
-        for (int off = 0; off < c; off += 32) {
-          const int i = off + lane;
-          const uint64_t key = i < cf ? src[i] : i < c ? src[kTcCap - 1 - (i - cf)] : kKeyMax;
-          nt = topk_offer(top[warp], nt, a.R, key, R[warp]);
-        }
+      const uint64_t* src = a.qlist + (int64_t)pos * kTcQCap;
+      for (int off = 0; off < c; off += 32) {
+        const uint64_t key = off + lane < c ? src[off + lane] : kKeyMax;
+        nt = topk_offer(top[warp], nt, a.R, key, R[warp]);
       }
     } else {
       for (int base = pa; base < pb; base += 32) {
@@ -973,52 +998,29 @@ __global__ void __launch_bounds__(128) tc_finish(TcArgs a) {
   }
 }
 
-// Pre-filter queries per bucket of pa.
-__global__ void tc_bucket_count(const int32_t* __restrict__ queues, const int32_t* __restrict__ pa,
-                                int32_t* counters, int32_t* bucket, int64_t n) {
-  const int nA = counters[CNT_QA];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nA; i += gridDim.x * blockDim.x) {
-    const int qi = queues[i];
-    const int b = (int)(((int64_t)pa[qi] * kBuckets) / (n + 1));
-    atomicAdd(&bucket[b], 1);
-  }
-}
-
-// Exclusive prefix sum of the bucket counts (one CTA of 1024 threads).
-__global__ void tc_bucket_scan(int32_t* bucket) {
-  __shared__ int sm[kBuckets];
-  const int t = threadIdx.x;
-  sm[t] = bucket[t];
-  __syncthreads();
-  for (int off = 1; off < kBuckets; off <<= 1) {
-    const int v = t >= off ? sm[t - off] : 0;
-    __syncthreads();
-    sm[t] += v;
-    __syncthreads();
-  }
-  bucket[t] = sm[t] - bucket[t];  // exclusive start, used as a fill cursor
-}
-
-// Places every pre-filter query in its bucket, writes its vector in the scan's
-// format (zero-padded to dpq elements: bfloat16 by round-to-nearest-even; float32 as
-// given for tf32; E4M3 codes of q / s_q with s_q = max|q| / 448, saturating) and the
-// squared norm of those values (for E4M3, of the decoded s_q * code), and resets its
-// shared threshold.
+// One warp per pre-filter query (position = its place in the queue): its vector in
+// the scan's format (zero-padded to dpq elements: bfloat16 by round-to-nearest-even;
+// float32 as given for tf32; E4M3 codes of q / s_q with s_q = max|q| / 448,
+// saturating), the squared norm of those values (for E4M3, of the decoded s_q * code),
+// and its bound, group minima and candidate count reset; its in-range row count is
+// added to the batch's total.
 template <int F>
 __global__ void tc_scatter(const int32_t* __restrict__ queues, const int32_t* __restrict__ pa,
-                           const float* __restrict__ q, int d, int dpq, int32_t* counters, int32_t* bucket,
-                           int64_t n, int32_t* aq, float* aqn, float* aqs, void* qb, unsigned long long* qthr) {
+                           const int32_t* __restrict__ pb, const float* __restrict__ q, int d, int dpq,
+                           int32_t* counters, int32_t* aq, float* aqn, float* aqs, void* qb,
+                           unsigned long long* qthr, unsigned* gmin, int32_t* qcnt, unsigned long long* sumy) {
   const int nA = counters[CNT_QA];
   const int lane = threadIdx.x & 31;
   const int warps = gridDim.x * (blockDim.x >> 5);
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nA; i += warps) {
-    const int qi = queues[i];
-    int pos = 0;
+  for (int pos = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pos < nA; pos += warps) {
+    const int qi = queues[pos];
+    reinterpret_cast<uint4*>(gmin + (int64_t)pos * 128)[lane] = make_uint4(0x7f800000u, 0x7f800000u, 0x7f800000u,
+                                                                          0x7f800000u);
     if (lane == 0) {
-      const int b = (int)(((int64_t)pa[qi] * kBuckets) / (n + 1));
-      pos = atomicAdd(&bucket[b], 1);
+      const int y = pb[qi] - pa[qi];
+      if (y > 0) atomicAdd(sumy, (unsigned long long)y);
+      qcnt[pos] = 0;
     }
-    pos = __shfl_sync(kFull, pos, 0);
     const float* qrow = q + (int64_t)qi * d;
     float ss = 0.f, sq = 1.f;
     if constexpr (F == kFmtBF16) {
@@ -1107,15 +1109,6 @@ cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, 
   constexpr int eb = TcTraits<F>::kElemBytes;
   constexpr int kKc = kTcKb / eb;  // K elements per stage
   const int dpq = ((ix.d + kKc - 1) / kKc) * kKc;
-  cudaError_t e = cudaMemsetAsync(sc.tc_bucket, 0, kBuckets * sizeof(int32_t), st);
-  if (e != cudaSuccess) return e;
-  tc_bucket_count<<<ix.num_sms * 2, 256, 0, st>>>(sc.queues, sc.pa, sc.counters, sc.tc_bucket, ix.n);
-  tc_bucket_scan<<<1, kBuckets, 0, st>>>(sc.tc_bucket);
-  tc_scatter<F><<<ix.num_sms * 4, 256, 0, st>>>(sc.queues, sc.pa, q, ix.d, dpq, sc.counters, sc.tc_bucket, ix.n,
-                                                sc.tc_aq, sc.tc_aqn, F == kFmtFP8 ? sc.tc_aqs : nullptr, sc.tc_qb,
-                                                sc.tc_thr);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   const CUtensorMapDataType dt = F == kFmtBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                  : F == kFmtTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                  : CU_TENSOR_MAP_DATA_TYPE_UINT8;
@@ -1123,9 +1116,9 @@ cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, 
                      : F == kFmtTF32 ? (const void*)ix.vec_sorted : (const void*)ix.vts_fp8;
   CUtensorMap tmX, tmQ;
   if (!encode_2d(&tmX, dt, rows, (uint64_t)ix.dp, (uint64_t)ix.n, (uint64_t)ix.dp * eb, kKc, kTcRows) ||
-      !encode_2d(&tmQ, dt, sc.tc_qb, (uint64_t)dpq, (uint64_t)sc.tc_rows, (uint64_t)dpq * eb, kKc, kTcQ))
+      !encode_2d(&tmQ, dt, sc.tc_qg, (uint64_t)dpq, (uint64_t)sc.tc_slots, (uint64_t)dpq * eb, kKc, kTcQ))
     return cudaErrorInvalidValue;
-  const int tiles = (int)(sc.tc_rows / kTcQ);
+  const int64_t tile_cap = sc.tc_slots / kTcQ;
   TcArgs a;
   a.sorted_ids = ix.sorted_ids;
   a.xn = F == kFmtBF16 ? ix.xn_bf16_sorted : F == kFmtTF32 ? ix.xn_f32_sorted : ix.xn_fp8_sorted;
@@ -1136,6 +1129,8 @@ cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, 
   a.q = q;
   a.dp4 = ix.dp / 4;
   a.d = ix.d;
+  a.dpq = dpq;
+  a.eb = eb;
   a.KC = dpq / kKc;
   a.num_sms = ix.num_sms;
   a.n = ix.n;
@@ -1144,21 +1139,41 @@ cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, 
   a.aq = sc.tc_aq;
   a.aqn = sc.tc_aqn;
   a.aqs = F == kFmtFP8 ? sc.tc_aqs : nullptr;
-  a.tile_lo = sc.tc_tile;
-  a.tile_nb = sc.tc_tile + tiles;
-  a.tile_units = sc.tc_tile + 2 * tiles;
-  a.unit_off = sc.tc_tile + 3 * tiles;
-  a.part = sc.tc_part;
+  a.qb = sc.tc_qb;
+  a.qg = sc.tc_qg;
+  a.slotpos = sc.tc_slotpos;
+  a.tile_span = sc.tc_tiles;
+  a.unit_off = sc.tc_tiles + tile_cap;
+  a.span_cnt = sc.tc_spans;
+  a.span_fill = sc.tc_spans + sc.tc_spans_cap;
+  a.span_tile = sc.tc_spans + 2 * sc.tc_spans_cap;
+  a.gmin = sc.tc_gmin;
+  a.qlist = sc.tc_qlist;
+  a.qcnt = sc.tc_qcnt;
+  a.stage = sc.tc_stage;
+  a.sumy = sc.tc_sumy;
   a.qthr = sc.tc_thr;
-  a.pcnt = sc.tc_pcnt;
+  a.slot_cap = sc.tc_slots;
+  a.span_cap = sc.tc_spans_cap;
+  a.pcap = kTcPairsPerQuery * sc.tc_rows;
   a.counters = sc.counters;
   a.k = p.k;
   a.R = tc_rerank_width(p);
   a.stall = p.tc_scan == 2 ? 1 : 0;
   a.wait_ns = p.tc_scan == 2 ? kTestWaitNs : kWaitNs;
   a.o = o;
-  tc_tile_prep<<<ix.num_sms, 256, 0, st>>>(a);
-  tc_unit_plan<<<1, 1024, 0, st>>>(a);
+  // queries by position, then spans, tiles, units and slots
+  cudaError_t e = cudaMemsetAsync(sc.tc_sumy, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc.tc_spans, 0, (size_t)sc.tc_spans_cap * sizeof(int32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc.tc_slotpos, 0xff, (size_t)sc.tc_slots * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  const int qgrid = (int)std::max<int64_t>(ix.num_sms, (nq + 7) / 8);  // a warp per query, 8 per CTA
+  tc_scatter<F><<<qgrid, 256, 0, st>>>(sc.queues, sc.pa, sc.pb, q, ix.d, dpq, sc.counters, sc.tc_aq, sc.tc_aqn,
+                                       F == kFmtFP8 ? sc.tc_aqs : nullptr, sc.tc_qb, sc.tc_thr, sc.tc_gmin,
+                                       sc.tc_qcnt, sc.tc_sumy);
+  tc_span_count<<<(int)std::max<int64_t>(1, (nq + 255) / 256), 256, 0, st>>>(a);
+  tc_span_scan<<<1, 1024, 0, st>>>(a);
+  tc_place<<<qgrid, 256, 0, st>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = tc_smem_bytes();
@@ -1168,6 +1183,7 @@ cudaError_t launch_tc(const DeviceIndex& ix, const Scratch& sc, const float* q, 
   if (e != cudaSuccess) return e;
   // bounding pass (each query's bound), then the collecting pass
   tc_scan_kernel<F, true><<<ix.num_sms, kTcThreads, smem, st>>>(tmX, tmQ, a);
+  tc_bound<<<qgrid, 256, 0, st>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   tc_scan_kernel<F, false><<<ix.num_sms, kTcThreads, smem, st>>>(tmX, tmQ, a);
