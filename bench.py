@@ -57,13 +57,18 @@ PAPER_EF, PAPER_M = 100, 16
 # the search parameters the capture ran with. A run whose digest, workload or
 # parameters differ reports traffic null, beside the nearest capture's parameters.
 NCU_TRAFFIC = [
-    {"digest": "1820668a002a", "workload": "c2", "bytes": 1_946_045_696 + 11_967_744,
-     "params": {"ef": 16, "ef_post": 96, "m": 64, "tau_a": 20000, "tau_b": 750000, "dtype": 0, "selection": 2,
+    {"digest": "641a67db8b15", "workload": "c2", "bytes": 1_947_512_576 + 12_342_272,
+     "params": {"ef": 16, "ef_post": 96, "m": 64, "tau_a": 50000, "tau_b": 600000, "dtype": 0, "selection": 2,
                 "cand_cap": 256, "visited_cap": 1024, "warps_per_block": 4, "scan_rows": 8192, "reg_budget": 80,
                 "tc_scan": 1},
      "profile": "profiles/batch_kernel_c2_1m_launches.md"},
-    {"digest": "1820668a002a", "workload": "c2", "bytes": 1_948_573_440 + 12_239_616,
+    {"digest": "641a67db8b15", "workload": "c2", "bytes": 1_948_306_432 + 12_202_240,
      "params": {"ef": 16, "ef_post": 96, "m": 64, "tau_a": 20000, "tau_b": 600000, "dtype": 0, "selection": 2,
+                "cand_cap": 256, "visited_cap": 1024, "warps_per_block": 4, "scan_rows": 8192, "reg_budget": 80,
+                "tc_scan": 1},
+     "profile": "profiles/batch_kernel_c2_1m_launches.md"},
+    {"digest": "641a67db8b15", "workload": "c2", "bytes": 1_947_282_944 + 11_829_248,
+     "params": {"ef": 16, "ef_post": 96, "m": 64, "tau_a": 20000, "tau_b": 750000, "dtype": 0, "selection": 2,
                 "cand_cap": 256, "visited_cap": 1024, "warps_per_block": 4, "scan_rows": 8192, "reg_budget": 80,
                 "tc_scan": 1},
      "profile": "profiles/batch_kernel_c2_1m_launches.md"},
@@ -366,7 +371,9 @@ def run(args):
     # (an exact answer there scans up to 5M rows), with a wider tuning margin for the
     # smaller sample
     per_f = args.truth_per_fraction if args.truth_per_fraction >= 0 else (200 if name == "c4" else 0)
-    tune_margin = args.tune_margin if args.tune_margin >= 0 else (0.01 if name == "c4" else 0.005)
+    # c4 scores recall on 200 queries per range fraction (sampling noise about 0.01):
+    # its tuner keeps a wider margin
+    tune_margin = args.tune_margin if args.tune_margin >= 0 else (0.02 if name == "c4" else 0.005)
 
     def on_dev(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -879,7 +886,7 @@ def main():
     ap.add_argument("--target", type=float, default=0.95)
     ap.add_argument("--tune-margin", type=float, default=-1,
                     help="the tuner aims this far above --target on the held-out batch (default 0.005 for "
-                         "c2, 0.01 for c4)")
+                         "c2 and the others, 0.02 for c4)")
     ap.add_argument("--truth-per-fraction", type=int, default=-1,
                     help="scored rows per range fraction (0: all; default all for c2, 200 for c4)")
     ap.add_argument("--ef", type=int, default=100, help="starting / no-tune beam width")
