@@ -65,8 +65,9 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
        queries run under the strategies): the (tau_A, tau_B) pair with the fastest
        batch whose recall meets the target in every group; then step 1 again under
        the new router.
-    3. CTA shape, buffer sizes, scan work-item size, register budget and the
-       tensor-core pre-filter scan."""
+    3. CTA shape, buffer sizes, scan work-item size, register budget, the hybrid
+       selection, the tensor-core pre-filter scan and (BF16/FP8 storage) twice the
+       FP32 re-rank."""
     import torch
 
     import paper_2412_02448_gb300 as U
@@ -173,6 +174,10 @@ def tune(index, q, lo, hi, k, truth_ids, truth_count, groups, target=0.95, base=
     if cur.m <= 64:
         # hybrid selection S1 instead of S2 (Section 5.6 compares the two)
         shapes.append({"selection": 1})
+    if cur.dtype != U.FP32 and 2 * cur.rerank_mult * k <= 4096:
+        # BF16/FP8 storage: twice the FP32 re-rank, for targets the coarser distances of
+        # the traversal cannot meet with the beams alone
+        shapes.append({"rerank_mult": 2 * cur.rerank_mult})
     # pre-filter queries on the tensor cores instead of the warp scan (or back): bfloat16,
     # tf32 or E4M3 operands by the storage format
     shapes.append({"tc_scan": 1 - cur.tc_scan})

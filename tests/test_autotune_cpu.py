@@ -136,3 +136,28 @@ def test_tuner_breaks_near_ties_by_listing_order(monkeypatch):
     p, _ = autotune.tune(FakeIndex(), None, None, None, K, truth, np.full(NQ, K), GROUPS, target=0.95,
                          efs=(16,), ms_=(16,), reps=3, calibrate_tau=False)
     assert p.cand_cap == 1024 and p.visited_cap == 2048
+
+
+def test_reduced_precision_line_can_widen_its_rerank(monkeypatch):
+    """With FP8 storage, when no beam or routing meets the target because the graph
+    rows' coarse distances lose neighbours unless the FP32 re-rank takes 8k candidates,
+    the tuner's shape step tries twice the re-rank and keeps it."""
+    def ids8(p):
+        ids = _ids(p)
+        s = FakeIndex().route(None, None, p.tau_a, p.tau_b)["strategy"].numpy()
+        if p.rerank_mult < 8:
+            ids[s != U.PRE, K - 2:] = -1
+        return ids
+
+    def time8(index, q, lo, hi, k, params, reps, torch_, strategy="auto"):
+        return _true_ms(params) + 0.05 * params.rerank_mult, {"ids": torch.from_numpy(ids8(params))}
+
+    monkeypatch.setattr(autotune, "_time_search", time8)
+    truth = np.tile(np.arange(K, dtype=np.int64), (NQ, 1))
+    count = np.full(NQ, K)
+    base = U.Params.defaults(dtype=U.FP8E4M3, rerank_mult=4)
+    p, rep = autotune.tune(FakeIndex(), None, None, None, K, truth, count, GROUPS, target=0.95, base=base,
+                           efs=(16, 24, 32, 48, 64), ms_=(16, 32), reps=3,
+                           tau_a_fracs=(0.01, 0.02, 0.05), tau_b_fracs=(0.3, 0.5))
+    assert p.rerank_mult == 8
+    assert min(rep["recall"].values()) >= 0.95
