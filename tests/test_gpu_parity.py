@@ -677,3 +677,30 @@ def test_c4_precision_shape_k10_k100(U, c4_small_index):
         assert rec[U.BF16]["pre"] >= 0.98 and rec[U.FP8E4M3]["pre"] >= 0.95, (k, rec)
     print("c4-shape recall by k, dtype, fraction:", json.dumps({str(k): {str(d): v for d, v in r_.items()}
                                                                  for k, r_ in report.items()}))
+
+
+@pytest.mark.parametrize("tc", [0, 1])
+@pytest.mark.parametrize("dtype", ["BF16", "FP8E4M3"])
+def test_wide_rerank_reduced_precision(U, tmp_path, dtype, tc):
+    """BF16 and FP8 storage with twice the usual FP32 re-rank (8k candidates, a shape
+    the autotuner tries), on either pre-filter scan, auto-routed: every row in range,
+    every returned distance the FP32 direct distance of its id, and recall against the
+    exact answer (Definition 1) at least 0.95."""
+    import hsig_build
+    from workloads import make_workload
+    w = make_workload("c2", seed=5, n=20000, nq=600)
+    path = str(tmp_path / "rr8.idx")
+    hsig_build.build_index(w.vectors, w.attrs, path, w.S, w.M, 60, seed=5)
+    ix = U.Index(path, device=0)
+    ex_ids, _, ex_c = oracle.exact_knn(w.vectors, w.attrs, w.queries, w.lo, w.hi, w.k)
+    X = w.vectors.astype(np.float64)
+    p = U.Params.defaults(dtype=getattr(U, dtype), rerank_mult=8, tc_scan=tc, tau_a=w.n // 50, tau_b=w.n // 2)
+    r = _np(ix.search(w.queries, w.lo, w.hi, w.k, ef=64, strategy="auto", params=p))
+    _valid(w, r, w.lo, w.hi)
+    for i in range(len(w.lo)):
+        c = r["count"][i]
+        ids = r["ids"][i, :c]
+        d64 = ((X[ids] - w.queries[i].astype(np.float64)) ** 2).sum(1)
+        assert np.all(np.abs(r["dist"][i, :c] - d64) <= 1e-5 * np.maximum(d64, 1e-30))
+    assert oracle.recall(r["ids"], ex_ids, ex_c, w.k).mean() >= 0.95
+    ix.close()
